@@ -1,0 +1,294 @@
+/*
+ * tsplat.h -- C ABI of libtsplat: latent-feature Gaussian splatting on one
+ * GB300 (sm_103a).
+ *
+ * The calls follow the statement of the problem in Tele-Aloha (arXiv
+ * 2405.14866), Sec. 4.2 "Neural Rasterization via 3DGS":
+ *   - each point is a Gaussian with position x_i, latent feature f_i
+ *     (d = C channels), scale s_i and opacity alpha_i (rotation identity in
+ *     the paper, an input here);
+ *   - positions are unprojected from the source depth maps with the camera
+ *     parameters Pi, and the foreground pixels become pixel-aligned
+ *     Gaussians                                           -> tsplat_build
+ *   - the Gaussians are differentiably rasterized to the target view,
+ *     F_novel = R_G({G}, Pi_novel), with the 3DGS rasterizer the paper
+ *     cites (EWA projection, 16x16 tiles, (tile, depth) order,
+ *     front-to-back alpha compositing of features)      -> tsplat_render
+ *   - gradients flow through R_G because the encoder and decoder around it
+ *     are trained end to end                             -> tsplat_backward
+ *   - the system renders the viewer's left and right eye views every frame
+ *     and is optimized with CUDA Graphs (Sec. 5.3)        -> tsplat_server_*
+ *
+ * General rules.
+ *   - Every pointer argument documented as "device" must point to memory of
+ *     the current CUDA device; "host" pointers to host memory.  The caller
+ *     owns all input and output buffers; the library owns the opaque
+ *     handles and their scratch memory.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *     are stream-ordered and asynchronous unless documented to synchronize.
+ *   - Every call returns a tsplat_status; on failure a thread-local message
+ *     is available from tsplat_last_error().  No C++ exception crosses the
+ *     ABI.  Errors found by the kernels themselves (buffer capacity,
+ *     invalid sizes) are written to a device status word of the context and
+ *     returned by the next call that synchronizes on it (tsplat_ctx_status).
+ *   - Sizes: N < 2^31 Gaussians, images up to 16383 x 16383 pixels,
+ *     1 <= C <= 64 feature channels.
+ */
+#ifndef TSPLAT_H
+#define TSPLAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TSPLAT_OK = 0,
+    TSPLAT_ERR_INVALID_ARG = 1,  /* a size, pointer or enum is out of range */
+    TSPLAT_ERR_OOM = 2,          /* device allocation failed */
+    TSPLAT_ERR_CAPACITY = 3,     /* a buffer bound was exceeded (see the call) */
+    TSPLAT_ERR_TIMEOUT = 4,      /* a bounded wait expired */
+    TSPLAT_ERR_CUDA = 5,         /* a CUDA runtime call failed */
+    TSPLAT_ERR_NOT_READY = 6,    /* asynchronous work has not finished yet */
+    TSPLAT_ERR_UNSUPPORTED = 7   /* feature combination not built */
+} tsplat_status;
+
+/* feature storage types */
+enum { TSPLAT_F32 = 0, TSPLAT_BF16 = 1 };
+
+/* Pinhole camera.  R, t map world to camera coordinates, p = R x + t
+ * (R row-major).  Camera frame: x right, y down, z forward.  Pixel (u, v) =
+ * (column, row) is centred at image coordinate (u, v).  Only Gaussians
+ * with z_near < p_z < z_far are rendered. */
+typedef struct {
+    float fx, fy, cx, cy;
+    int32_t width, height;
+    float R[9];
+    float t[3];
+    float z_near, z_far;
+} tsplat_camera;
+
+/* flags of tsplat_render_params */
+enum {
+    /* Do not synchronize to size the pair buffer: use the capacity set with
+     * tsplat_ctx_reserve and report an overflow through the context status
+     * (needed for CUDA-graph capture). */
+    TSPLAT_RENDER_ASYNC = 1u << 0,
+    /* Keep what tsplat_backward needs (final transmittance and last
+     * blended index per pixel). */
+    TSPLAT_RENDER_SAVE = 1u << 1
+};
+
+/* Rasterizer constants (the 3DGS rasterizer's; all parameters). */
+typedef struct {
+    float lowpass;        /* px^2 added to the diagonal of Sigma2D (0.3) */
+    float alpha_max;      /* opacity clamp (0.99) */
+    float alpha_min;      /* skip threshold (1/255) */
+    float t_min;          /* transmittance stop threshold (1e-4) */
+    float frustum_clamp;  /* Jacobian clamp in units of tan(fov/2) (1.3) */
+    uint32_t flags;       /* TSPLAT_RENDER_* */
+} tsplat_render_params;
+
+/* Fill `p` with the defaults listed above (flags = 0). */
+void tsplat_render_params_default(tsplat_render_params *p);
+
+/* One source view (Sec. 4.2: depth map plus the encoder's per-pixel maps).
+ * All map pointers are device pointers, row-major H x W (x channels):
+ *   depth    H*W   f32  camera-space z in metres
+ *   mask     H*W   u8   nonzero = foreground; NULL = every pixel
+ *   scale    H*W*3 f32  standard deviations along the Gaussian's axes (M_s)
+ *   quat     H*W*4 f32  (w,x,y,z) rotation of the axes in the source camera
+ *                       frame; NULL = identity (the paper's choice)
+ *   opacity  H*W   f32  (M_alpha)
+ *   feat     H*W*C      latent features (M_f), type feat_dtype */
+typedef struct {
+    const float *depth;
+    const uint8_t *mask;
+    const float *scale;
+    const float *quat;
+    const float *opacity;
+    const void *feat;
+    int32_t feat_dtype;
+    int32_t reserved;
+    tsplat_camera cam;
+} tsplat_src_view;
+
+/* ------------------------------------------------------------------------
+ * Gaussians (library-owned, device-resident)
+ *
+ * Layout: N Gaussians in id order; positions and opacities as float4
+ * (x, y, z, opacity), covariances as float4 (s00, s01, s02, s11) plus
+ * float2 (s12, s22), features N x C of the storage type.  N lives in device
+ * memory (so that building can be captured in a CUDA graph).
+ * ---------------------------------------------------------------------- */
+typedef struct tsplat_gaussians tsplat_gaussians;
+
+/* Allocate room for `capacity` Gaussians with C channels of type
+ * feat_dtype.  N starts at 0. */
+tsplat_status tsplat_gaussians_create(int64_t capacity, int32_t C, int32_t feat_dtype,
+                                      tsplat_gaussians **out);
+tsplat_status tsplat_gaussians_destroy(tsplat_gaussians *g);
+
+/* Load N Gaussians from caller device arrays: mean N*3 f32, cov N*6 f32
+ * (s00 s01 s02 s11 s12 s22), opac N f32, feat N*C of type feat_dtype_in
+ * (converted to the storage type with round-to-nearest-even).  N must not
+ * exceed the capacity. */
+tsplat_status tsplat_gaussians_set(tsplat_gaussians *g, int64_t n, const float *mean,
+                                   const float *cov, const float *opac, const void *feat,
+                                   int32_t feat_dtype_in, void *stream);
+
+/* Copy the current Gaussians to caller device arrays (layouts as in _set;
+ * feat in the storage type).  Synchronizes `stream` to learn N first. */
+tsplat_status tsplat_gaussians_get(const tsplat_gaussians *g, float *mean, float *cov,
+                                   float *opac, void *feat, void *stream);
+
+/* Current N (synchronizes on the stream that last wrote it). */
+tsplat_status tsplat_gaussians_count(const tsplat_gaussians *g, int64_t *n);
+tsplat_status tsplat_gaussians_shape(const tsplat_gaussians *g, int64_t *capacity,
+                                     int32_t *C, int32_t *feat_dtype);
+
+/* ------------------------------------------------------------------------
+ * A1 -- lifting (Sec. 4.2: foreground pixels of the source views are lifted
+ * to pixel-aligned Gaussians; positions unprojected with Pi).
+ *
+ * For pixel (u,v) of view s with depth z:
+ *   x_world = R_s^T (z ((u - cx)/fx, (v - cy)/fy, 1) - t_s)
+ *   Sigma3D = R_g diag(scale)^2 R_g^T,  R_g = R_s^T R(quat)
+ * Gaussian ids follow (view, row, column) order of the foreground pixels.
+ * Arithmetic is single precision in a fixed operation order (no fused
+ * multiply-add), identical to the oracle's key mode.
+ *
+ * tsplat_build allocates a new handle with capacity = sum of H*W (the
+ * upper bound of N); tsplat_build_into reuses `g`, whose capacity must be at
+ * least the total pixel count of the views and whose C must match.  Both
+ * are asynchronous; N stays on the device.  1 <= n_views <= 16.
+ * ---------------------------------------------------------------------- */
+tsplat_status tsplat_build(const tsplat_src_view *views, int32_t n_views, int32_t C,
+                           int32_t feat_dtype, tsplat_gaussians **out, void *stream);
+tsplat_status tsplat_build_into(tsplat_gaussians *g, const tsplat_src_view *views,
+                                int32_t n_views, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Render context: scratch memory of one render stream plus the state saved
+ * for the backward pass.  One context must not be used by two streams at
+ * once.  Buffers grow on demand (device allocation); tsplat_ctx_reserve
+ * pre-sizes them so that later calls allocate nothing.
+ * ---------------------------------------------------------------------- */
+typedef struct tsplat_ctx tsplat_ctx;
+
+tsplat_status tsplat_ctx_create(tsplat_ctx **out);
+tsplat_status tsplat_ctx_destroy(tsplat_ctx *ctx);
+tsplat_status tsplat_ctx_reserve(tsplat_ctx *ctx, int64_t max_gaussians, int64_t max_pairs,
+                                 int32_t max_width, int32_t max_height, int32_t C);
+
+typedef struct {
+    int64_t n_gaussians;   /* N of the last render */
+    int64_t n_visible;     /* Gaussians with at least one tile */
+    int64_t n_pairs;       /* P: (Gaussian, tile) pairs */
+    int64_t pair_capacity; /* current size of the pair buffers */
+    int32_t tiles_x, tiles_y;
+    int32_t width, height, C;
+    int32_t device_status; /* tsplat_status written by kernels (0 = OK) */
+} tsplat_ctx_stats;
+
+/* Statistics of the last render on `ctx` (synchronizes the context's last
+ * stream). */
+tsplat_status tsplat_ctx_stats_get(tsplat_ctx *ctx, tsplat_ctx_stats *out);
+
+/* Device status of the last render (synchronizes); TSPLAT_ERR_CAPACITY if
+ * the pair buffer overflowed in TSPLAT_RENDER_ASYNC mode. */
+tsplat_status tsplat_ctx_status(tsplat_ctx *ctx);
+
+/* Intermediate results of the last render, copied to a caller device
+ * buffer of `bytes` bytes (for tests and tools):
+ *   TSPLAT_EXPORT_RECT     N x 4 int32 tile rect (x0 y0 x1 y1), culled = 0
+ *   TSPLAT_EXPORT_DEPTHKEY N uint32 depth key (bits of camera z), culled = 0xFFFFFFFF
+ *   TSPLAT_EXPORT_MEAN2D   N x 2 f32
+ *   TSPLAT_EXPORT_CONIC    N x 3 f32
+ *   TSPLAT_EXPORT_RADIUS   N f32
+ *   TSPLAT_EXPORT_PAIRS    P uint32 Gaussian ids in (tile, depth, id) order
+ *   TSPLAT_EXPORT_RANGES   tiles x 2 uint32 [first, last) per tile
+ *   TSPLAT_EXPORT_TFINAL   H x W f32 (needs TSPLAT_RENDER_SAVE)
+ *   TSPLAT_EXPORT_LAST     H x W uint32 (needs TSPLAT_RENDER_SAVE) */
+enum {
+    TSPLAT_EXPORT_RECT = 0, TSPLAT_EXPORT_DEPTHKEY = 1, TSPLAT_EXPORT_MEAN2D = 2,
+    TSPLAT_EXPORT_CONIC = 3, TSPLAT_EXPORT_RADIUS = 4, TSPLAT_EXPORT_PAIRS = 5,
+    TSPLAT_EXPORT_RANGES = 6, TSPLAT_EXPORT_TFINAL = 7, TSPLAT_EXPORT_LAST = 8
+};
+tsplat_status tsplat_ctx_export(tsplat_ctx *ctx, int32_t what, void *dst, size_t bytes, void *stream);
+
+/* ------------------------------------------------------------------------
+ * A2..A7 -- render (Sec. 4.2: F_novel = R_G({G}, Pi_novel)).
+ *
+ * A2 project: p = R x + t; visible iff z_near < p_z < z_far;
+ *   J = [[fx/p_z, 0, -fx t_x/p_z^2], [0, fy/p_z, -fy t_y/p_z^2]] with
+ *   t_x/p_z, t_y/p_z clamped to +-frustum_clamp * 0.5 W/fx (0.5 H/fy);
+ *   Sigma2D = (J R) Sigma3D (J R)^T + lowpass I, det <= 0 or non-finite
+ *   culls; conic = (c, -b, a)/det; r = ceil(3 sqrt(m + sqrt(max(0.1,
+ *   m^2 - det)))), m = (a+c)/2; mean2D = (fx p_x/p_z + cx, fy p_y/p_z + cy);
+ *   tile rect [floor((mu-r)/16), floor((mu+r+15)/16)) clamped to the grid.
+ * A3-A6: one (Gaussian, tile) pair per tile of the rect, ordered by
+ *   (tile, bits of p_z, Gaussian id) -- identical to a stable sort of the
+ *   64-bit key tile << 32 | bits(p_z) -- and per-tile ranges.
+ * A7 composite, per pixel p, front to back over its tile's list:
+ *   q = -1/2 (a dx^2 + c dy^2) - b dx dy, d = p - mean2D; q > 0 skips;
+ *   alpha = min(alpha_max, o e^q); alpha < alpha_min skips;
+ *   T' = T (1 - alpha); T' < t_min stops (that Gaussian is not blended);
+ *   F += f alpha T; T = T'.   A = 1 - T at the end.
+ *
+ * out_feat:  device, C x H x W f32 (H, W of the camera), overwritten.
+ * out_alpha: device, H x W f32, overwritten; may be NULL.
+ * Without TSPLAT_RENDER_ASYNC the call synchronizes once (to size the pair
+ * buffer); with it the call never synchronizes and writes
+ * TSPLAT_ERR_CAPACITY to the context status if P exceeds the reserved
+ * capacity (outputs are then incomplete).
+ * `g` must stay alive and unmodified until tsplat_backward has used `ctx`.
+ * ---------------------------------------------------------------------- */
+tsplat_status tsplat_render(const tsplat_gaussians *g, const tsplat_camera *cam,
+                            const tsplat_render_params *params, float *out_feat,
+                            float *out_alpha, tsplat_ctx *ctx, void *stream);
+
+/* A3..A7 from already projected 2D Gaussians (device arrays):
+ *   mean2d N*2 f32, conic N*3 f32 (a, b, c), opac N f32,
+ *   depth N f32 (sort key; must be > 0 for rendered Gaussians),
+ *   radius N int32 (0 = not rendered), feat N*C of type feat_dtype.
+ * The tile rect is derived from mean2d and radius as in A2.  Outputs as in
+ * tsplat_render.  This is the forward of the differentiable rasterizer. */
+tsplat_status tsplat_rasterize(int64_t n, const float *mean2d, const float *conic,
+                               const float *opac, const float *depth, const int32_t *radius,
+                               const void *feat, int32_t C, int32_t feat_dtype, int32_t width,
+                               int32_t height, const tsplat_render_params *params,
+                               float *out_feat, float *out_alpha, tsplat_ctx *ctx, void *stream);
+
+/* ------------------------------------------------------------------------
+ * A8 -- backward of A7 (Sec. 4.2: R_G is differentiable; the encoder and
+ * decoder are trained through it).  Needs a render or rasterize on `ctx`
+ * with TSPLAT_RENDER_SAVE.  With g = dL/dF(p), gA = dL/dA(p), T_j the
+ * transmittance before blended Gaussian j (recomputed from the saved final
+ * transmittance by division, not stored) and S_j the blended features
+ * behind j:
+ *   dL/df_j     += alpha_j T_j g
+ *   dL/dalpha_j  = T_j <f_j, g> - <S_j, g>/(1 - alpha_j) + gA T_final/(1 - alpha_j)
+ * chained through alpha = o e^q (no gradient where alpha was clamped) to
+ * the opacity, the conic (a, b, c) and the 2D mean.
+ *   dL_dfeat  device C x H x W f32;  dL_dalpha device H x W f32 or NULL
+ *   d_mean2d N*2, d_conic N*3, d_opac N, d_feat N*C: device f32 outputs,
+ *   overwritten, indexed by Gaussian id.  Any output may be NULL.
+ * Accumulation order across pixels is not deterministic (FP32 atomics).
+ * ---------------------------------------------------------------------- */
+tsplat_status tsplat_backward(tsplat_ctx *ctx, const float *dL_dfeat, const float *dL_dalpha,
+                              float *d_mean2d, float *d_conic, float *d_opac, float *d_feat,
+                              void *stream);
+
+/* Thread-local message of the last failed call on this thread. */
+const char *tsplat_last_error(void);
+
+/* Library version string. */
+const char *tsplat_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TSPLAT_H */

@@ -1,0 +1,253 @@
+"""Python surface of libtsplat: the C-ABI calls with torch tensors.
+
+Every function marshals arguments (device pointers, sizes, the current CUDA
+stream) and calls the library; all computation runs in its CUDA kernels.
+PyTorch provides device memory and streams only.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Dict, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+F32, BF16 = L.F32, L.BF16
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("tsplat: tensors must live on the CUDA device")
+    if not t.is_contiguous():
+        raise ValueError("tsplat: tensors must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def ccamera(cam) -> L.CCamera:
+    """tsplat_camera from any object with fx, fy, cx, cy, width, height, R, t,
+    z_near, z_far (e.g. gen.Camera)."""
+    c = L.CCamera()
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.width, c.height = int(cam.width), int(cam.height)
+    R = np.asarray(cam.R, np.float32).reshape(9)
+    t = np.asarray(cam.t, np.float32).reshape(3)
+    for i in range(9):
+        c.R[i] = float(R[i])
+    for i in range(3):
+        c.t[i] = float(t[i])
+    c.z_near, c.z_far = float(getattr(cam, "z_near", 0.2)), float(getattr(cam, "z_far", 1e4))
+    return c
+
+
+def cparams(lowpass=0.3, alpha_max=0.99, alpha_min=1.0 / 255.0, t_min=1e-4, frustum_clamp=1.3,
+            save=False, async_=False) -> L.CParams:
+    p = L.CParams()
+    p.lowpass, p.alpha_max, p.alpha_min, p.t_min, p.frustum_clamp = lowpass, alpha_max, alpha_min, t_min, frustum_clamp
+    p.flags = (L.RENDER_SAVE if save else 0) | (L.RENDER_ASYNC if async_ else 0)
+    return p
+
+
+def _with_flags(params: Optional[L.CParams], save: bool, async_: bool) -> L.CParams:
+    if params is None:
+        return cparams(save=save, async_=async_)
+    p = L.CParams.from_buffer_copy(params)
+    if save:
+        p.flags |= L.RENDER_SAVE
+    if async_:
+        p.flags |= L.RENDER_ASYNC
+    return p
+
+
+def source_view(depth, mask, scale, quat, opacity, feat, cam, feat_dtype=F32) -> L.CSrcView:
+    """tsplat_src_view from CUDA tensors (H,W), (H,W) u8 or None, (H,W,3),
+    (H,W,4) or None, (H,W), (H,W,C).  The tensors must stay alive until the
+    build has run."""
+    v = L.CSrcView()
+    v.depth, v.mask, v.scale, v.quat = _ptr(depth), _ptr(mask), _ptr(scale), _ptr(quat)
+    v.opacity, v.feat = _ptr(opacity), _ptr(feat)
+    v.feat_dtype = feat_dtype
+    v.cam = ccamera(cam)
+    return v
+
+
+def upload_scene(scene, device="cuda") -> Dict:
+    """Copy a gen.Scene's per-view maps to the device (features as FP32)."""
+    views = []
+    for v in scene.views:
+        views.append(dict(
+            depth=torch.from_numpy(np.ascontiguousarray(v.depth)).to(device),
+            mask=torch.from_numpy(np.ascontiguousarray(v.mask)).to(device),
+            scale=torch.from_numpy(np.ascontiguousarray(v.scale)).to(device),
+            quat=torch.from_numpy(np.ascontiguousarray(v.quat)).to(device),
+            opacity=torch.from_numpy(np.ascontiguousarray(v.opacity)).to(device),
+            feat=torch.from_numpy(np.ascontiguousarray(v.feat)).to(device),
+            cam=v.cam))
+    return dict(views=views, C=scene.C, feat_dtype=scene.feat_dtype)
+
+
+class Gaussians:
+    """A library-owned, device-resident set of Gaussians (tsplat_gaussians)."""
+
+    def __init__(self, handle: ctypes.c_void_p, C: int, feat_dtype: int, capacity: int):
+        self.handle = handle
+        self.C = C
+        self.feat_dtype = feat_dtype
+        self.capacity = capacity
+
+    @classmethod
+    def create(cls, capacity: int, C: int, feat_dtype: int = F32) -> "Gaussians":
+        h = ctypes.c_void_p()
+        L.call("tsplat_gaussians_create", capacity, C, feat_dtype, ctypes.byref(h))
+        return cls(h, C, feat_dtype, capacity)
+
+    @classmethod
+    def from_arrays(cls, mean, cov, opac, feat, feat_dtype: int = F32, stream=None) -> "Gaussians":
+        n, C = feat.shape
+        g = cls.create(max(n, 1), C, feat_dtype)
+        g.set(mean, cov, opac, feat, stream)
+        return g
+
+    def set(self, mean, cov, opac, feat, stream=None):
+        n = mean.shape[0]
+        din = BF16 if feat.dtype == torch.bfloat16 else F32
+        if din == F32 and feat.dtype != torch.float32:
+            raise ValueError("features must be float32 or bfloat16")
+        L.call("tsplat_gaussians_set", self.handle, n, _ptr(mean), _ptr(cov), _ptr(opac), _ptr(feat), din, _stream(stream))
+
+    @classmethod
+    def build(cls, views: Sequence[L.CSrcView], C: int, feat_dtype: int = F32, stream=None) -> "Gaussians":
+        arr = (L.CSrcView * len(views))(*views)
+        h = ctypes.c_void_p()
+        L.call("tsplat_build", arr, len(views), C, feat_dtype, ctypes.byref(h), _stream(stream))
+        cap = sum(v.cam.width * v.cam.height for v in views)
+        return cls(h, C, feat_dtype, cap)
+
+    def build_into(self, views: Sequence[L.CSrcView], stream=None):
+        arr = (L.CSrcView * len(views))(*views)
+        L.call("tsplat_build_into", self.handle, arr, len(views), _stream(stream))
+
+    def count(self) -> int:
+        n = ctypes.c_int64()
+        L.call("tsplat_gaussians_count", self.handle, ctypes.byref(n))
+        return int(n.value)
+
+    def get(self, stream=None) -> Dict[str, torch.Tensor]:
+        n = self.count()
+        dev = torch.device("cuda")
+        fdt = torch.bfloat16 if self.feat_dtype == BF16 else torch.float32
+        out = dict(mean=torch.empty((n, 3), device=dev), cov=torch.empty((n, 6), device=dev),
+                   opac=torch.empty((n,), device=dev), feat=torch.empty((n, self.C), device=dev, dtype=fdt))
+        if n:
+            L.call("tsplat_gaussians_get", self.handle, _ptr(out["mean"]), _ptr(out["cov"]), _ptr(out["opac"]),
+                   _ptr(out["feat"]), _stream(stream))
+        return out
+
+    def close(self):
+        if self.handle:
+            L.lib().tsplat_gaussians_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Context:
+    """Render context (tsplat_ctx): scratch of one stream + saved state."""
+
+    def __init__(self):
+        h = ctypes.c_void_p()
+        L.call("tsplat_ctx_create", ctypes.byref(h))
+        self.handle = h
+        self.n = None
+
+    def reserve(self, max_gaussians: int, max_pairs: int, max_width: int, max_height: int, C: int = 32):
+        L.call("tsplat_ctx_reserve", self.handle, max_gaussians, max_pairs, max_width, max_height, C)
+
+    def render(self, g: Gaussians, cam, params: Optional[L.CParams] = None, save=False, async_=False,
+               out_feat=None, out_alpha=None, stream=None):
+        cc = ccamera(cam)
+        W, H = cc.width, cc.height
+        if out_feat is None:
+            out_feat = torch.empty((g.C, H, W), device="cuda")
+        if out_alpha is None:
+            out_alpha = torch.empty((H, W), device="cuda")
+        p = _with_flags(params, save, async_)
+        L.call("tsplat_render", g.handle, ctypes.byref(cc), ctypes.byref(p), _ptr(out_feat), _ptr(out_alpha),
+               self.handle, _stream(stream))
+        self.n = None
+        return out_feat, out_alpha
+
+    def rasterize(self, mean2d, conic, opac, depth, radius, feat, width: int, height: int,
+                  params: Optional[L.CParams] = None, save=False, async_=False, out_feat=None, out_alpha=None,
+                  stream=None):
+        n, C = feat.shape
+        dt = BF16 if feat.dtype == torch.bfloat16 else F32
+        if out_feat is None:
+            out_feat = torch.empty((C, height, width), device="cuda")
+        if out_alpha is None:
+            out_alpha = torch.empty((height, width), device="cuda")
+        p = _with_flags(params, save, async_)
+        L.call("tsplat_rasterize", n, _ptr(mean2d), _ptr(conic), _ptr(opac), _ptr(depth), _ptr(radius), _ptr(feat),
+               C, dt, width, height, ctypes.byref(p), _ptr(out_feat), _ptr(out_alpha), self.handle, _stream(stream))
+        self.n = n
+        return out_feat, out_alpha
+
+    def backward(self, dF, dA=None, n: Optional[int] = None, C: Optional[int] = None, stream=None):
+        """Gradients (d_mean2d (N,2), d_conic (N,3), d_opac (N,), d_feat (N,C))."""
+        st = self.stats()
+        n = n if n is not None else (self.n if self.n is not None else st["n_gaussians"])
+        C = C if C is not None else st["C"]
+        dev = torch.device("cuda")
+        outs = (torch.empty((n, 2), device=dev), torch.empty((n, 3), device=dev), torch.empty((n,), device=dev),
+                torch.empty((n, C), device=dev))
+        L.call("tsplat_backward", self.handle, _ptr(dF.contiguous()), _ptr(None if dA is None else dA.contiguous()),
+               *(_ptr(o) for o in outs), _stream(stream))
+        return outs
+
+    def stats(self) -> Dict[str, int]:
+        s = L.CStats()
+        L.call("tsplat_ctx_stats_get", self.handle, ctypes.byref(s))
+        return {k: getattr(s, k) for k, _ in L.CStats._fields_}
+
+    def status(self):
+        L.call("tsplat_ctx_status", self.handle)
+
+    def export(self, what: str) -> torch.Tensor:
+        st = self.stats()
+        n, P, T = st["n_gaussians"], st["n_pairs"], st["tiles_x"] * st["tiles_y"]
+        HW = st["width"] * st["height"]
+        shapes = {"rect": ((n, 4), torch.int32), "depthkey": ((n,), torch.int32), "mean2d": ((n, 2), torch.float32),
+                  "conic": ((n, 3), torch.float32), "radius": ((n,), torch.float32),
+                  "pairs": ((min(P, st["pair_capacity"]),), torch.int32), "ranges": ((T, 2), torch.int32),
+                  "tfinal": ((st["height"], st["width"]), torch.float32), "last": ((st["height"], st["width"]), torch.int32)}
+        shape, dt = shapes[what]
+        t = torch.empty(shape, device="cuda", dtype=dt)
+        nbytes = t.numel() * t.element_size()
+        if nbytes:
+            L.call("tsplat_ctx_export", self.handle, L.EXPORT[what], _ptr(t), nbytes, _stream())
+        torch.cuda.current_stream().synchronize()
+        del HW
+        return t
+
+    def close(self):
+        if self.handle:
+            L.lib().tsplat_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,659 @@
+// Host side of the C ABI declared in include/tsplat.h: handles, scratch
+// management and the ordering of the kernel launches.  No arithmetic of the
+// method happens here; every step runs in the kernels of k_*.cu.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+
+#include "common.cuh"
+#include "internal.h"
+
+using namespace tsp;
+
+namespace {
+
+thread_local std::string g_err;
+
+tsplat_status fail(tsplat_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define TRY_CUDA(expr)                                                                                \
+    do {                                                                                              \
+        cudaError_t e_ = (expr);                                                                      \
+        if (e_ != cudaSuccess)                                                                        \
+            return fail(e_ == cudaErrorMemoryAllocation ? TSPLAT_ERR_OOM : TSPLAT_ERR_CUDA, "%s: %s (%s:%d)", \
+                        #expr, cudaGetErrorString(e_), __FILE__, __LINE__);                          \
+    } while (0)
+
+#define TRY(expr)                                  \
+    do {                                           \
+        tsplat_status s_ = (expr);                 \
+        if (s_ != TSPLAT_OK) return s_;            \
+    } while (0)
+
+tsplat_status check_launch(const char *what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(TSPLAT_ERR_CUDA, "%s: kernel launch failed: %s", what, cudaGetErrorString(e));
+    return TSPLAT_OK;
+}
+
+inline cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// A device buffer that grows (stream-ordered) and never shrinks.
+struct DBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    template <typename T>
+    T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+tsplat_status grow(DBuf &b, size_t bytes, cudaStream_t s) {
+    if (bytes == 0) bytes = 16;
+    if (b.bytes >= bytes) return TSPLAT_OK;
+    if (b.p) TRY_CUDA(cudaFreeAsync(b.p, s));
+    b.p = nullptr;
+    b.bytes = 0;
+    const size_t nb = bytes + bytes / 8 + 256;
+    TRY_CUDA(cudaMallocAsync(&b.p, nb, s));
+    b.bytes = nb;
+    return TSPLAT_OK;
+}
+
+void release(DBuf &b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+size_t feat_size(int dtype) { return dtype == TSPLAT_BF16 ? 2 : 4; }
+
+int tile_digits(int n_tiles) {  // radix passes over tile ids 0..n_tiles-1
+    if (n_tiles <= 1) return 0;
+    int bits = 0;
+    while ((1u << bits) < (uint32_t)n_tiles) ++bits;
+    return (bits + 7) / 8;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ handles
+
+struct tsplat_gaussians {
+    int64_t cap = 0;
+    int C = 0;
+    int dtype = TSPLAT_F32;
+    DBuf xyzo, cova, covb, feat, n_dev, blk;
+    cudaStream_t last_stream = nullptr;
+};
+
+struct tsplat_ctx {
+    // N-sized
+    DBuf hdr, rect, ntiles, dkey, radius, skeys0, skeys1, svals0, svals1, hist_n, emit_blk;
+    // P-sized
+    DBuf pk0, pk1, pv0, pv1, hist_p;
+    // tiles / pixels
+    DBuf ranges, tfinal, last;
+    // small words: kminmax[2], n_vis, npass, p_dev, p_eff, status, n_dev, totals[4*256]
+    DBuf small;
+    uint32_t *host_small = nullptr;  // pinned mirror
+    int64_t p_cap = 0;
+
+    // last render
+    cudaStream_t stream = nullptr;
+    int64_t n_cap = 0;
+    const uint32_t *n_dev = nullptr;
+    int W = 0, H = 0, C = 0, dtype = TSPLAT_F32, tiles_x = 0, tiles_y = 0;
+    const void *feat = nullptr;
+    const uint32_t *pairs = nullptr;  // sorted Gaussian ids
+    bool saved = false;
+    float alpha_max = 0, alpha_min = 0;
+};
+
+namespace {
+enum { SM_KMIN = 0, SM_KMAX = 1, SM_NVIS = 2, SM_NPASS = 3, SM_P = 4, SM_PEFF = 5, SM_STATUS = 6, SM_N = 7,
+       SM_TOTALS = 16, SM_WORDS = 16 + 4 * 256 };
+uint32_t *small_ptr(tsplat_ctx *c, int w) { return c->small.as<uint32_t>() + w; }
+}  // namespace
+
+extern "C" {
+
+void tsplat_render_params_default(tsplat_render_params *p) {
+    if (!p) return;
+    p->lowpass = 0.3f;
+    p->alpha_max = 0.99f;
+    p->alpha_min = 1.0f / 255.0f;
+    p->t_min = 1e-4f;
+    p->frustum_clamp = 1.3f;
+    p->flags = 0;
+}
+
+const char *tsplat_last_error(void) { return g_err.c_str(); }
+
+const char *tsplat_version(void) { return "tsplat 0.1 (sm_103a)"; }
+
+tsplat_status tsplat_gaussians_create(int64_t capacity, int32_t C, int32_t feat_dtype, tsplat_gaussians **out) {
+    if (!out) return fail(TSPLAT_ERR_INVALID_ARG, "gaussians_create: out is NULL");
+    *out = nullptr;
+    if (capacity < 0 || capacity >= (int64_t)1 << 31) return fail(TSPLAT_ERR_INVALID_ARG, "capacity %lld out of range", (long long)capacity);
+    if (C < 1 || C > 64) return fail(TSPLAT_ERR_INVALID_ARG, "C = %d not in [1, 64]", C);
+    if (feat_dtype != TSPLAT_F32 && feat_dtype != TSPLAT_BF16) return fail(TSPLAT_ERR_INVALID_ARG, "feat_dtype %d", feat_dtype);
+    tsplat_gaussians *g = new (std::nothrow) tsplat_gaussians();
+    if (!g) return fail(TSPLAT_ERR_OOM, "host allocation failed");
+    g->cap = capacity;
+    g->C = C;
+    g->dtype = feat_dtype;
+    const size_t n = (size_t)std::max<int64_t>(capacity, 1);
+    cudaStream_t s = nullptr;
+    tsplat_status st = TSPLAT_OK;
+    if ((st = grow(g->xyzo, n * 16, s)) || (st = grow(g->cova, n * 16, s)) || (st = grow(g->covb, n * 8, s)) ||
+        (st = grow(g->feat, n * C * feat_size(feat_dtype), s)) || (st = grow(g->n_dev, 16, s))) {
+        tsplat_gaussians_destroy(g);
+        return st;
+    }
+    if (cudaMemsetAsync(g->n_dev.p, 0, 4, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+        tsplat_gaussians_destroy(g);
+        return fail(TSPLAT_ERR_CUDA, "gaussians_create: %s", cudaGetErrorString(cudaGetLastError()));
+    }
+    *out = g;
+    return TSPLAT_OK;
+}
+
+tsplat_status tsplat_gaussians_destroy(tsplat_gaussians *g) {
+    if (!g) return TSPLAT_OK;
+    cudaDeviceSynchronize();
+    release(g->xyzo); release(g->cova); release(g->covb); release(g->feat); release(g->n_dev); release(g->blk);
+    delete g;
+    return TSPLAT_OK;
+}
+
+tsplat_status tsplat_gaussians_set(tsplat_gaussians *g, int64_t n, const float *mean, const float *cov,
+                                   const float *opac, const void *feat, int32_t feat_dtype_in, void *stream) {
+    if (!g) return fail(TSPLAT_ERR_INVALID_ARG, "gaussians_set: g is NULL");
+    if (n < 0 || n > g->cap) return fail(TSPLAT_ERR_CAPACITY, "gaussians_set: n = %lld exceeds capacity %lld", (long long)n, (long long)g->cap);
+    if (n > 0 && (!mean || !cov || !opac || !feat)) return fail(TSPLAT_ERR_INVALID_ARG, "gaussians_set: NULL array");
+    if (feat_dtype_in != TSPLAT_F32 && feat_dtype_in != TSPLAT_BF16) return fail(TSPLAT_ERR_INVALID_ARG, "feat_dtype %d", feat_dtype_in);
+    launch_gaussians_set(n, mean, cov, opac, feat, feat_dtype_in, g->C, g->dtype, g->xyzo.as<float4>(),
+                         g->cova.as<float4>(), g->covb.as<float2>(), g->feat.p, g->n_dev.as<uint32_t>(), S(stream));
+    g->last_stream = S(stream);
+    return check_launch("gaussians_set");
+}
+
+tsplat_status tsplat_gaussians_count(const tsplat_gaussians *g, int64_t *n) {
+    if (!g || !n) return fail(TSPLAT_ERR_INVALID_ARG, "gaussians_count: NULL argument");
+    uint32_t v = 0;
+    TRY_CUDA(cudaStreamSynchronize(g->last_stream));
+    TRY_CUDA(cudaMemcpy(&v, g->n_dev.p, 4, cudaMemcpyDeviceToHost));
+    *n = v;
+    return TSPLAT_OK;
+}
+
+tsplat_status tsplat_gaussians_shape(const tsplat_gaussians *g, int64_t *capacity, int32_t *C, int32_t *feat_dtype) {
+    if (!g) return fail(TSPLAT_ERR_INVALID_ARG, "gaussians_shape: g is NULL");
+    if (capacity) *capacity = g->cap;
+    if (C) *C = g->C;
+    if (feat_dtype) *feat_dtype = g->dtype;
+    return TSPLAT_OK;
+}
+
+tsplat_status tsplat_gaussians_get(const tsplat_gaussians *g, float *mean, float *cov, float *opac, void *feat,
+                                   void *stream) {
+    if (!g) return fail(TSPLAT_ERR_INVALID_ARG, "gaussians_get: g is NULL");
+    TRY_CUDA(cudaStreamSynchronize(g->last_stream));
+    launch_gaussians_get(g->n_dev.as<uint32_t>(), g->cap, g->C, g->dtype, g->xyzo.as<float4>(), g->cova.as<float4>(),
+                         g->covb.as<float2>(), g->feat.p, mean, cov, opac, feat, S(stream));
+    return check_launch("gaussians_get");
+}
+
+static tsplat_status build_into(tsplat_gaussians *g, const tsplat_src_view *views, int32_t n_views, cudaStream_t s) {
+    if (n_views < 1 || n_views > MAX_VIEWS) return fail(TSPLAT_ERR_INVALID_ARG, "n_views = %d not in [1, %d]", n_views, MAX_VIEWS);
+    BuildArgs a;
+    memset(&a, 0, sizeof(a));
+    int64_t total = 0;
+    for (int v = 0; v < n_views; ++v) {
+        const tsplat_src_view &sv = views[v];
+        const int H = sv.cam.height, W = sv.cam.width;
+        if (H <= 0 || W <= 0 || H > 16383 || W > 16383) return fail(TSPLAT_ERR_INVALID_ARG, "view %d: size %dx%d", v, W, H);
+        if (!sv.depth || !sv.scale || !sv.opacity || !sv.feat) return fail(TSPLAT_ERR_INVALID_ARG, "view %d: NULL map", v);
+        if (sv.quat && ((uintptr_t)sv.quat & 15)) return fail(TSPLAT_ERR_INVALID_ARG, "view %d: quat not 16-byte aligned", v);
+        if (sv.feat_dtype != TSPLAT_F32 && sv.feat_dtype != TSPLAT_BF16) return fail(TSPLAT_ERR_INVALID_ARG, "view %d: feat_dtype", v);
+        ViewDesc &d = a.views[v];
+        d.depth = sv.depth; d.mask = sv.mask; d.scale = sv.scale; d.quat = sv.quat; d.opacity = sv.opacity;
+        d.feat = sv.feat; d.feat_dtype = sv.feat_dtype; d.H = H; d.W = W; d.pix_off = total; d.cam = sv.cam;
+        total += (int64_t)H * W;
+    }
+    if (total > g->cap) return fail(TSPLAT_ERR_CAPACITY, "build: %lld pixels exceed capacity %lld", (long long)total, (long long)g->cap);
+    a.n_views = n_views;
+    a.total_pix = total;
+    a.C = g->C;
+    a.out_dtype = g->dtype;
+    a.xyzo = g->xyzo.as<float4>();
+    a.cova = g->cova.as<float4>();
+    a.covb = g->covb.as<float2>();
+    a.feat = g->feat.p;
+    a.nblocks = (int)((total + BUILD_PIX_PER_BLOCK - 1) / BUILD_PIX_PER_BLOCK);
+    TRY(grow(g->blk, (size_t)a.nblocks * 8, s));
+    a.blk_cnt = g->blk.as<uint32_t>();
+    a.blk_off = a.blk_cnt + a.nblocks;
+    a.n_dev = g->n_dev.as<uint32_t>();
+    launch_build(a, s);
+    g->last_stream = s;
+    return check_launch("build");
+}
+
+tsplat_status tsplat_build(const tsplat_src_view *views, int32_t n_views, int32_t C, int32_t feat_dtype,
+                           tsplat_gaussians **out, void *stream) {
+    if (!views || !out) return fail(TSPLAT_ERR_INVALID_ARG, "build: NULL argument");
+    if (n_views < 1 || n_views > MAX_VIEWS) return fail(TSPLAT_ERR_INVALID_ARG, "n_views = %d not in [1, %d]", n_views, MAX_VIEWS);
+    int64_t total = 0;
+    for (int v = 0; v < n_views; ++v) total += (int64_t)std::max(views[v].cam.height, 0) * std::max(views[v].cam.width, 0);
+    TRY(tsplat_gaussians_create(total, C, feat_dtype, out));
+    tsplat_status st = build_into(*out, views, n_views, S(stream));
+    if (st != TSPLAT_OK) {
+        tsplat_gaussians_destroy(*out);
+        *out = nullptr;
+    }
+    return st;
+}
+
+tsplat_status tsplat_build_into(tsplat_gaussians *g, const tsplat_src_view *views, int32_t n_views, void *stream) {
+    if (!g || !views) return fail(TSPLAT_ERR_INVALID_ARG, "build_into: NULL argument");
+    return build_into(g, views, n_views, S(stream));
+}
+
+// ---------------------------------------------------------------- contexts
+
+tsplat_status tsplat_ctx_create(tsplat_ctx **out) {
+    if (!out) return fail(TSPLAT_ERR_INVALID_ARG, "ctx_create: out is NULL");
+    tsplat_ctx *c = new (std::nothrow) tsplat_ctx();
+    if (!c) return fail(TSPLAT_ERR_OOM, "host allocation failed");
+    tsplat_status st = grow(c->small, SM_WORDS * 4, nullptr);
+    if (st == TSPLAT_OK && cudaMallocHost(&c->host_small, SM_WORDS * 4) != cudaSuccess) st = fail(TSPLAT_ERR_OOM, "pinned allocation failed");
+    if (st == TSPLAT_OK && (cudaMemset(c->small.p, 0, SM_WORDS * 4) != cudaSuccess)) st = fail(TSPLAT_ERR_CUDA, "memset");
+    if (st == TSPLAT_OK && cudaStreamSynchronize(nullptr) != cudaSuccess) st = fail(TSPLAT_ERR_CUDA, "sync");
+    if (st != TSPLAT_OK) {
+        tsplat_ctx_destroy(c);
+        return st;
+    }
+    *out = c;
+    return TSPLAT_OK;
+}
+
+tsplat_status tsplat_ctx_destroy(tsplat_ctx *c) {
+    if (!c) return TSPLAT_OK;
+    cudaDeviceSynchronize();
+    DBuf *bufs[] = {&c->hdr, &c->rect, &c->ntiles, &c->dkey, &c->radius, &c->skeys0, &c->skeys1, &c->svals0,
+                    &c->svals1, &c->hist_n, &c->emit_blk, &c->pk0, &c->pk1, &c->pv0, &c->pv1, &c->hist_p,
+                    &c->ranges, &c->tfinal, &c->last, &c->small};
+    for (DBuf *b : bufs) release(*b);
+    if (c->host_small) cudaFreeHost(c->host_small);
+    delete c;
+    return TSPLAT_OK;
+}
+
+static tsplat_status ensure_n(tsplat_ctx *c, int64_t n, cudaStream_t s) {
+    const size_t N = (size_t)std::max<int64_t>(n, 1);
+    const size_t nb = (N + RS_TILE - 1) / RS_TILE;
+    TRY(grow(c->hdr, N * sizeof(Header), s));
+    TRY(grow(c->rect, N * 8, s));
+    TRY(grow(c->ntiles, N * 4, s));
+    TRY(grow(c->dkey, N * 4, s));
+    TRY(grow(c->radius, N * 4, s));
+    TRY(grow(c->skeys0, N * 4, s));
+    TRY(grow(c->skeys1, N * 4, s));
+    TRY(grow(c->svals0, N * 4, s));
+    TRY(grow(c->svals1, N * 4, s));
+    TRY(grow(c->hist_n, nb * 256 * 4, s));
+    TRY(grow(c->emit_blk, nb * 4, s));
+    return TSPLAT_OK;
+}
+
+static tsplat_status ensure_p(tsplat_ctx *c, int64_t p, cudaStream_t s) {
+    if (p <= c->p_cap && c->pk0.p) return TSPLAT_OK;
+    const int64_t cap = std::max<int64_t>(p + p / 8, 4096);
+    const size_t nb = (size_t)((cap + RS_TILE - 1) / RS_TILE);
+    TRY(grow(c->pk0, (size_t)cap * 4, s));
+    TRY(grow(c->pk1, (size_t)cap * 4, s));
+    TRY(grow(c->pv0, (size_t)cap * 4, s));
+    TRY(grow(c->pv1, (size_t)cap * 4, s));
+    TRY(grow(c->hist_p, nb * 256 * 4, s));
+    c->p_cap = cap;
+    return TSPLAT_OK;
+}
+
+static tsplat_status ensure_pix(tsplat_ctx *c, int W, int H, int n_tiles, bool save, cudaStream_t s) {
+    TRY(grow(c->ranges, (size_t)std::max(n_tiles, 1) * 8, s));
+    if (save) {
+        TRY(grow(c->tfinal, (size_t)W * H * 4, s));
+        TRY(grow(c->last, (size_t)W * H * 4, s));
+    }
+    return TSPLAT_OK;
+}
+
+tsplat_status tsplat_ctx_reserve(tsplat_ctx *c, int64_t max_gaussians, int64_t max_pairs, int32_t max_width,
+                                 int32_t max_height, int32_t C) {
+    (void)C;
+    if (!c) return fail(TSPLAT_ERR_INVALID_ARG, "ctx_reserve: ctx is NULL");
+    if (max_gaussians < 0 || max_pairs < 0 || max_width < 0 || max_height < 0) return fail(TSPLAT_ERR_INVALID_ARG, "ctx_reserve: negative size");
+    cudaStream_t s = nullptr;
+    TRY(ensure_n(c, max_gaussians, s));
+    TRY(ensure_p(c, max_pairs, s));
+    const int tx = (max_width + TILE - 1) / TILE, ty = (max_height + TILE - 1) / TILE;
+    TRY(ensure_pix(c, max_width, max_height, tx * ty, true, s));
+    TRY_CUDA(cudaStreamSynchronize(s));
+    return TSPLAT_OK;
+}
+
+// A2 (done by the caller of this function) .. A7
+static tsplat_status render_tail(tsplat_ctx *c, int64_t n_cap, const uint32_t *n_dev, const void *feat, int C,
+                                 int dtype, int W, int H, const tsplat_render_params &par, float *out_feat,
+                                 float *out_alpha, cudaStream_t s) {
+    const int tiles_x = (W + TILE - 1) / TILE, tiles_y = (H + TILE - 1) / TILE, n_tiles = tiles_x * tiles_y;
+    const bool async_mode = (par.flags & TSPLAT_RENDER_ASYNC) != 0;
+    const bool save = (par.flags & TSPLAT_RENDER_SAVE) != 0;
+    uint32_t *sm = c->small.as<uint32_t>();
+
+    // depth order of the Gaussians (radix passes only over the differing bytes)
+    launch_depth_npass(sm + SM_KMIN, sm + SM_NPASS, s);
+    RadixSort ds;
+    memset(&ds, 0, sizeof(ds));
+    ds.keys_in = c->dkey.as<uint32_t>();
+    ds.vals_in = nullptr;
+    ds.keys[0] = c->skeys0.as<uint32_t>();
+    ds.keys[1] = c->skeys1.as<uint32_t>();
+    ds.vals[0] = c->svals0.as<uint32_t>();
+    ds.vals[1] = c->svals1.as<uint32_t>();
+    ds.n_dev = n_dev;
+    ds.npass_dev = sm + SM_NPASS;
+    ds.kmin = sm + SM_KMIN;
+    ds.hist = c->hist_n.as<uint32_t>();
+    ds.totals = sm + SM_TOTALS;
+    ds.nblocks = (int)((std::max<int64_t>(n_cap, 1) + RS_TILE - 1) / RS_TILE);
+    launch_radix_sort(ds, 4, s);
+
+    // scan of tiles per Gaussian in depth order and pair emission
+    EmitArgs em;
+    memset(&em, 0, sizeof(em));
+    em.order.vals_in = nullptr;
+    em.order.vals[0] = ds.vals[0];
+    em.order.vals[1] = ds.vals[1];
+    em.order.npass_dev = sm + SM_NPASS;
+    em.n_dev = n_dev;
+    em.n_cap = n_cap;
+    em.ntiles = c->ntiles.as<uint32_t>();
+    em.rect = c->rect.as<uint2>();
+    em.tiles_x = tiles_x;
+    em.tile_base = 0;
+    em.blk_sum = c->emit_blk.as<uint32_t>();
+    em.p_dev = sm + SM_P;
+    em.status = sm + SM_STATUS;
+    launch_emit_count(em, s);
+    TRY(check_launch("render: sort/count"));
+
+    if (!async_mode) {
+        TRY_CUDA(cudaMemcpyAsync(c->host_small + SM_P, sm + SM_P, 4, cudaMemcpyDeviceToHost, s));
+        TRY_CUDA(cudaStreamSynchronize(s));
+        TRY(ensure_p(c, (int64_t)c->host_small[SM_P], s));
+    } else if (!c->pk0.p) {
+        return fail(TSPLAT_ERR_CAPACITY, "render: TSPLAT_RENDER_ASYNC needs tsplat_ctx_reserve first");
+    }
+    em.pair_tile = c->pk1.as<uint32_t>();
+    em.pair_id = c->pv1.as<uint32_t>();
+    em.p_cap = c->p_cap;
+    launch_emit_write(em, s);
+
+    // stable sort of the pairs on the tile digits; the emit buffer is the
+    // odd ping-pong buffer, so two passes end where they started
+    const int tpass = tile_digits(n_tiles);
+    RadixSort ts;
+    memset(&ts, 0, sizeof(ts));
+    ts.keys_in = c->pk1.as<uint32_t>();
+    ts.vals_in = c->pv1.as<uint32_t>();
+    ts.keys[0] = c->pk0.as<uint32_t>();
+    ts.keys[1] = c->pk1.as<uint32_t>();
+    ts.vals[0] = c->pv0.as<uint32_t>();
+    ts.vals[1] = c->pv1.as<uint32_t>();
+    ts.n_dev = sm + SM_PEFF;
+    ts.npass_dev = nullptr;
+    ts.npass_host = tpass;
+    ts.kmin = nullptr;
+    ts.hist = c->hist_p.as<uint32_t>();
+    ts.totals = sm + SM_TOTALS;
+    ts.nblocks = (int)((c->p_cap + RS_TILE - 1) / RS_TILE);
+    // effective pair count: P, or 0 when the pairs did not fit
+    launch_pairs_effective(sm + SM_P, (uint32_t)std::min<int64_t>(c->p_cap, 0xffffffffll), sm + SM_PEFF, s);
+    if (tpass > 0) launch_radix_sort(ts, tpass, s);
+    const uint32_t *tiles_sorted = tpass == 0 ? ts.keys_in : ts.keys[(tpass - 1) & 1];
+    const uint32_t *ids_sorted = tpass == 0 ? ts.vals_in : ts.vals[(tpass - 1) & 1];
+    launch_ranges(tiles_sorted, sm + SM_PEFF, c->p_cap, c->ranges.as<uint2>(), n_tiles, s);
+    TRY(check_launch("render: bins"));
+
+    CompositeArgs ca;
+    memset(&ca, 0, sizeof(ca));
+    ca.ranges = c->ranges.as<uint2>();
+    ca.ids = ids_sorted;
+    ca.hdr = c->hdr.as<Header>();
+    ca.feat = feat;
+    ca.C = C;
+    ca.feat_dtype = dtype;
+    ca.W = W;
+    ca.H = H;
+    ca.tiles_x = tiles_x;
+    ca.tiles_y = tiles_y;
+    ca.alpha_max = par.alpha_max;
+    ca.alpha_min = par.alpha_min;
+    ca.t_min = par.t_min;
+    ca.out_feat = out_feat;
+    ca.out_alpha = out_alpha;
+    ca.out_T = save ? c->tfinal.as<float>() : nullptr;
+    ca.out_last = save ? c->last.as<uint32_t>() : nullptr;
+    launch_composite(ca, s);
+    TRY(check_launch("render: composite"));
+
+    c->stream = s;
+    c->n_cap = n_cap;
+    c->n_dev = n_dev;
+    c->W = W; c->H = H; c->C = C; c->dtype = dtype;
+    c->tiles_x = tiles_x; c->tiles_y = tiles_y;
+    c->feat = feat;
+    c->pairs = ids_sorted;
+    c->saved = save;
+    c->alpha_max = par.alpha_max;
+    c->alpha_min = par.alpha_min;
+    return TSPLAT_OK;
+}
+
+static tsplat_status check_common(tsplat_ctx *c, int W, int H, int C, int dtype, const tsplat_render_params *p,
+                                  const float *out_feat) {
+    if (!c || !p || !out_feat) return fail(TSPLAT_ERR_INVALID_ARG, "render: NULL argument");
+    if (W <= 0 || H <= 0 || W > 16383 || H > 16383) return fail(TSPLAT_ERR_INVALID_ARG, "render: image %dx%d", W, H);
+    if (C < 1 || C > 64) return fail(TSPLAT_ERR_INVALID_ARG, "render: C = %d", C);
+    if (dtype != TSPLAT_F32 && dtype != TSPLAT_BF16) return fail(TSPLAT_ERR_INVALID_ARG, "render: feat_dtype %d", dtype);
+    return TSPLAT_OK;
+}
+
+static void init_small(tsplat_ctx *c, cudaStream_t s) {
+    uint32_t *sm = c->small.as<uint32_t>();
+    launch_fill_u32(sm + SM_KMIN, CULLED_KEY, 1, s);
+    cudaMemsetAsync(sm + SM_KMAX, 0, sizeof(uint32_t) * 6, s);  // kmax, n_vis, npass, P, P_eff, status
+}
+
+tsplat_status tsplat_render(const tsplat_gaussians *g, const tsplat_camera *cam, const tsplat_render_params *params,
+                            float *out_feat, float *out_alpha, tsplat_ctx *ctx, void *stream) {
+    if (!g || !cam) return fail(TSPLAT_ERR_INVALID_ARG, "render: NULL argument");
+    TRY(check_common(ctx, cam->width, cam->height, g->C, g->dtype, params, out_feat));
+    cudaStream_t s = S(stream);
+    const int W = cam->width, H = cam->height;
+    const int tiles_x = (W + TILE - 1) / TILE, tiles_y = (H + TILE - 1) / TILE;
+    const bool async_mode = (params->flags & TSPLAT_RENDER_ASYNC) != 0;
+    if (async_mode) {
+        if (ctx->hdr.bytes < (size_t)std::max<int64_t>(g->cap, 1) * sizeof(Header) ||
+            ctx->ranges.bytes < (size_t)tiles_x * tiles_y * 8 ||
+            ((params->flags & TSPLAT_RENDER_SAVE) && ctx->tfinal.bytes < (size_t)W * H * 4))
+            return fail(TSPLAT_ERR_CAPACITY, "render: TSPLAT_RENDER_ASYNC needs tsplat_ctx_reserve for these sizes");
+    } else {
+        TRY(ensure_n(ctx, g->cap, s));
+        TRY(ensure_pix(ctx, W, H, tiles_x * tiles_y, (params->flags & TSPLAT_RENDER_SAVE) != 0, s));
+    }
+    init_small(ctx, s);
+    ProjectOut o;
+    o.hdr = ctx->hdr.as<Header>();
+    o.rect = ctx->rect.as<uint2>();
+    o.ntiles = ctx->ntiles.as<uint32_t>();
+    o.dkey = ctx->dkey.as<uint32_t>();
+    o.radius = ctx->radius.as<float>();
+    o.kminmax = small_ptr(ctx, SM_KMIN);
+    o.n_vis = small_ptr(ctx, SM_NVIS);
+    launch_project(g->xyzo.as<float4>(), g->cova.as<float4>(), g->covb.as<float2>(), g->n_dev.as<uint32_t>(), g->cap,
+                   *cam, *params, tiles_x, tiles_y, o, s);
+    TRY(check_launch("render: project"));
+    return render_tail(ctx, g->cap, g->n_dev.as<uint32_t>(), g->feat.p, g->C, g->dtype, W, H, *params, out_feat,
+                       out_alpha, s);
+}
+
+tsplat_status tsplat_rasterize(int64_t n, const float *mean2d, const float *conic, const float *opac,
+                               const float *depth, const int32_t *radius, const void *feat, int32_t C,
+                               int32_t feat_dtype, int32_t width, int32_t height,
+                               const tsplat_render_params *params, float *out_feat, float *out_alpha,
+                               tsplat_ctx *ctx, void *stream) {
+    TRY(check_common(ctx, width, height, C, feat_dtype, params, out_feat));
+    if (n < 0 || n >= (int64_t)1 << 31) return fail(TSPLAT_ERR_INVALID_ARG, "rasterize: n = %lld", (long long)n);
+    if (n > 0 && (!mean2d || !conic || !opac || !depth || !radius || !feat)) return fail(TSPLAT_ERR_INVALID_ARG, "rasterize: NULL array");
+    if ((C * (int)feat_size(feat_dtype)) % 16 == 0 && ((uintptr_t)feat & 15))
+        return fail(TSPLAT_ERR_INVALID_ARG, "rasterize: feat not 16-byte aligned");
+    cudaStream_t s = S(stream);
+    const int tiles_x = (width + TILE - 1) / TILE, tiles_y = (height + TILE - 1) / TILE;
+    const bool async_mode = (params->flags & TSPLAT_RENDER_ASYNC) != 0;
+    if (async_mode) {
+        if (ctx->hdr.bytes < (size_t)std::max<int64_t>(n, 1) * sizeof(Header) || ctx->ranges.bytes < (size_t)tiles_x * tiles_y * 8)
+            return fail(TSPLAT_ERR_CAPACITY, "rasterize: TSPLAT_RENDER_ASYNC needs tsplat_ctx_reserve for these sizes");
+    } else {
+        TRY(ensure_n(ctx, n, s));
+        TRY(ensure_pix(ctx, width, height, tiles_x * tiles_y, (params->flags & TSPLAT_RENDER_SAVE) != 0, s));
+    }
+    init_small(ctx, s);
+    launch_fill_u32(small_ptr(ctx, SM_N), (uint32_t)n, 1, s);
+    ProjectOut o;
+    o.hdr = ctx->hdr.as<Header>();
+    o.rect = ctx->rect.as<uint2>();
+    o.ntiles = ctx->ntiles.as<uint32_t>();
+    o.dkey = ctx->dkey.as<uint32_t>();
+    o.radius = ctx->radius.as<float>();
+    o.kminmax = small_ptr(ctx, SM_KMIN);
+    o.n_vis = small_ptr(ctx, SM_NVIS);
+    launch_prepare_2d(n, mean2d, conic, opac, depth, radius, *params, tiles_x, tiles_y, o, s);
+    TRY(check_launch("rasterize: prepare"));
+    return render_tail(ctx, n, small_ptr(ctx, SM_N), feat, C, feat_dtype, width, height, *params, out_feat, out_alpha, s);
+}
+
+tsplat_status tsplat_backward(tsplat_ctx *c, const float *dL_dfeat, const float *dL_dalpha, float *d_mean2d,
+                              float *d_conic, float *d_opac, float *d_feat, void *stream) {
+    if (!c || !dL_dfeat) return fail(TSPLAT_ERR_INVALID_ARG, "backward: NULL argument");
+    if (!c->saved) return fail(TSPLAT_ERR_INVALID_ARG, "backward: the last render on this context did not use TSPLAT_RENDER_SAVE");
+    cudaStream_t s = S(stream);
+    launch_zero_f32_n(d_mean2d, c->n_dev, 2, c->n_cap, s);
+    launch_zero_f32_n(d_conic, c->n_dev, 3, c->n_cap, s);
+    launch_zero_f32_n(d_opac, c->n_dev, 1, c->n_cap, s);
+    launch_zero_f32_n(d_feat, c->n_dev, c->C, c->n_cap, s);
+    BackwardArgs b;
+    memset(&b, 0, sizeof(b));
+    b.ranges = c->ranges.as<uint2>();
+    b.ids = c->pairs;
+    b.hdr = c->hdr.as<Header>();
+    b.feat = c->feat;
+    b.C = c->C;
+    b.feat_dtype = c->dtype;
+    b.W = c->W; b.H = c->H; b.tiles_x = c->tiles_x; b.tiles_y = c->tiles_y;
+    b.alpha_max = c->alpha_max;
+    b.alpha_min = c->alpha_min;
+    b.T_final = c->tfinal.as<float>();
+    b.last = c->last.as<uint32_t>();
+    b.dF = dL_dfeat;
+    b.dA = dL_dalpha;
+    b.d_mean2d = d_mean2d;
+    b.d_conic = d_conic;
+    b.d_opac = d_opac;
+    b.d_feat = d_feat;
+    launch_backward(b, s);
+    return check_launch("backward");
+}
+
+tsplat_status tsplat_ctx_status(tsplat_ctx *c) {
+    if (!c) return fail(TSPLAT_ERR_INVALID_ARG, "ctx_status: ctx is NULL");
+    TRY_CUDA(cudaStreamSynchronize(c->stream));
+    uint32_t st = 0;
+    TRY_CUDA(cudaMemcpy(&st, small_ptr(c, SM_STATUS), 4, cudaMemcpyDeviceToHost));
+    if (st) return fail((tsplat_status)st, "device status %u (pair capacity %lld)", st, (long long)c->p_cap);
+    return TSPLAT_OK;
+}
+
+tsplat_status tsplat_ctx_stats_get(tsplat_ctx *c, tsplat_ctx_stats *out) {
+    if (!c || !out) return fail(TSPLAT_ERR_INVALID_ARG, "ctx_stats: NULL argument");
+    TRY_CUDA(cudaStreamSynchronize(c->stream));
+    uint32_t w[SM_TOTALS];
+    TRY_CUDA(cudaMemcpy(w, c->small.p, sizeof(w), cudaMemcpyDeviceToHost));
+    uint32_t n = 0;
+    if (c->n_dev) TRY_CUDA(cudaMemcpy(&n, c->n_dev, 4, cudaMemcpyDeviceToHost));
+    out->n_gaussians = n;
+    out->n_visible = w[SM_NVIS];
+    out->n_pairs = w[SM_P];
+    out->pair_capacity = c->p_cap;
+    out->tiles_x = c->tiles_x;
+    out->tiles_y = c->tiles_y;
+    out->width = c->W;
+    out->height = c->H;
+    out->C = c->C;
+    out->device_status = (int32_t)w[SM_STATUS];
+    return TSPLAT_OK;
+}
+
+tsplat_status tsplat_ctx_export(tsplat_ctx *c, int32_t what, void *dst, size_t bytes, void *stream) {
+    if (!c || !dst) return fail(TSPLAT_ERR_INVALID_ARG, "ctx_export: NULL argument");
+    cudaStream_t s = S(stream);
+    TRY_CUDA(cudaStreamSynchronize(c->stream));
+    uint32_t n = 0, P = 0;
+    if (c->n_dev) TRY_CUDA(cudaMemcpy(&n, c->n_dev, 4, cudaMemcpyDeviceToHost));
+    TRY_CUDA(cudaMemcpy(&P, small_ptr(c, SM_PEFF), 4, cudaMemcpyDeviceToHost));
+    const size_t HW = (size_t)c->W * c->H;
+    size_t need = 0;
+    switch (what) {
+        case TSPLAT_EXPORT_RECT: need = (size_t)n * 16; break;
+        case TSPLAT_EXPORT_DEPTHKEY: need = (size_t)n * 4; break;
+        case TSPLAT_EXPORT_MEAN2D: need = (size_t)n * 8; break;
+        case TSPLAT_EXPORT_CONIC: need = (size_t)n * 12; break;
+        case TSPLAT_EXPORT_RADIUS: need = (size_t)n * 4; break;
+        case TSPLAT_EXPORT_PAIRS: need = (size_t)P * 4; break;
+        case TSPLAT_EXPORT_RANGES: need = (size_t)c->tiles_x * c->tiles_y * 8; break;
+        case TSPLAT_EXPORT_TFINAL:
+        case TSPLAT_EXPORT_LAST:
+            if (!c->saved) return fail(TSPLAT_ERR_INVALID_ARG, "ctx_export: render without TSPLAT_RENDER_SAVE");
+            need = HW * 4;
+            break;
+        default: return fail(TSPLAT_ERR_INVALID_ARG, "ctx_export: unknown item %d", what);
+    }
+    if (bytes < need) return fail(TSPLAT_ERR_CAPACITY, "ctx_export: need %zu bytes, got %zu", need, bytes);
+    switch (what) {
+        case TSPLAT_EXPORT_RECT: launch_export_rect(c->rect.as<uint2>(), c->n_dev, c->n_cap, (int32_t *)dst, s); break;
+        case TSPLAT_EXPORT_DEPTHKEY: TRY_CUDA(cudaMemcpyAsync(dst, c->dkey.p, need, cudaMemcpyDeviceToDevice, s)); break;
+        case TSPLAT_EXPORT_MEAN2D:
+        case TSPLAT_EXPORT_CONIC: launch_export_header(c->hdr.as<Header>(), c->n_dev, c->n_cap, what, dst, s); break;
+        case TSPLAT_EXPORT_RADIUS: TRY_CUDA(cudaMemcpyAsync(dst, c->radius.p, need, cudaMemcpyDeviceToDevice, s)); break;
+        case TSPLAT_EXPORT_PAIRS: if (need) TRY_CUDA(cudaMemcpyAsync(dst, c->pairs, need, cudaMemcpyDeviceToDevice, s)); break;
+        case TSPLAT_EXPORT_RANGES: TRY_CUDA(cudaMemcpyAsync(dst, c->ranges.p, need, cudaMemcpyDeviceToDevice, s)); break;
+        case TSPLAT_EXPORT_TFINAL: TRY_CUDA(cudaMemcpyAsync(dst, c->tfinal.p, need, cudaMemcpyDeviceToDevice, s)); break;
+        case TSPLAT_EXPORT_LAST: TRY_CUDA(cudaMemcpyAsync(dst, c->last.p, need, cudaMemcpyDeviceToDevice, s)); break;
+    }
+    return check_launch("ctx_export");
+}
+
+}  // extern "C"

@@ -1,0 +1,59 @@
+// Internal definitions shared by the CUDA translation units of libtsplat.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/tsplat.h"
+
+namespace tsp {
+
+constexpr int TILE = 16;            // tile edge in pixels (the 3DGS rasterizer's)
+constexpr int TILE_PIX = TILE * TILE;
+constexpr uint32_t CULLED_KEY = 0xFFFFFFFFu;
+
+// Projected record of one Gaussian in the target view, 32 bytes (one DRAM
+// sector), read by the compositing once per (Gaussian, tile) pair:
+//   h0 = (mean2d.x, mean2d.y, conic a, conic b)
+//   h1 = (conic c, opacity, ex, ey) with (ex, ey) the half extents of the
+//        box that bounds every pixel where alpha can reach alpha_min.
+struct __align__(16) Header {
+    float4 h0;
+    float4 h1;
+};
+
+// Single-precision operations with one rounding each (no contraction), for
+// the quantities that decide integers (key mode).
+__device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float fsqrt(float a) { return __fsqrt_rn(a); }
+
+// Exponent q of the Gaussian at offset d = p - mean2d:
+//   q = -1/2 (a dx^2 + c dy^2) - b dx dy.
+// Forward and backward kernels both call this function, so both evaluate
+// the same instruction sequence and take identical skip decisions.
+__device__ __forceinline__ float gauss_q(float dx, float dy, float a, float b, float c) {
+    const float s = __fmaf_rn(a, __fmul_rn(dx, dx), __fmul_rn(c, __fmul_rn(dy, dy)));
+    return __fmaf_rn(-0.5f, s, -__fmul_rn(b, __fmul_rn(dx, dy)));
+}
+
+// alpha before the alpha_max clamp: o e^q
+__device__ __forceinline__ float gauss_alpha_raw(float q, float o) { return __fmul_rn(o, __expf(q)); }
+
+// Pack / unpack a tile rect [x0,x1) x [y0,y1) (each < 65536) into 64 bits.
+__device__ __forceinline__ uint2 pack_rect(int x0, int y0, int x1, int y1) {
+    return make_uint2((uint32_t)x0 | ((uint32_t)y0 << 16), (uint32_t)x1 | ((uint32_t)y1 << 16));
+}
+__device__ __forceinline__ void unpack_rect(uint2 r, int &x0, int &y0, int &x1, int &y1) {
+    x0 = r.x & 0xFFFF; y0 = r.x >> 16; x1 = r.y & 0xFFFF; y1 = r.y >> 16;
+}
+
+// Status word written by kernels (first error wins).
+__device__ __forceinline__ void set_status(uint32_t *st, uint32_t code) {
+    if (st) atomicCAS(st, 0u, code);
+}
+
+}  // namespace tsp

@@ -1,0 +1,235 @@
+// A1: lifting of foreground source pixels to 3D Gaussians (Tele-Aloha
+// Sec. 4.2: positions unprojected from the depth maps with the camera
+// parameters; scale, opacity and latent feature from the encoder maps).
+//
+// Three launches: per-block foreground counts, a scan of those counts, and
+// the lift itself, which numbers Gaussians in (view, row, column) order of
+// the foreground pixels.  Single precision, one rounding per operation in a
+// fixed order (the oracle's key mode follows the same order).
+#include "common.cuh"
+#include "internal.h"
+
+namespace tsp {
+
+namespace {
+
+constexpr int BT = 256;                             // threads per block
+constexpr int BI = BUILD_PIX_PER_BLOCK / BT;        // pixels per thread (16)
+constexpr uint32_t FULL = 0xffffffffu;
+
+__device__ __forceinline__ int view_of(const BuildArgs &a, int64_t g) {
+    int v = 0;
+    for (int k = 1; k < a.n_views; ++k)
+        if (g >= a.views[k].pix_off) v = k;
+    return v;
+}
+
+__device__ __forceinline__ bool is_fg(const BuildArgs &a, int64_t g) {
+    if (g >= a.total_pix) return false;
+    const ViewDesc &vd = a.views[view_of(a, g)];
+    return vd.mask == nullptr || vd.mask[g - vd.pix_off] != 0;
+}
+
+template <int NW>
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *sw, uint32_t &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sw[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < NW ? sw[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < NW; o <<= 1) {
+            uint32_t y = __shfl_up_sync(FULL, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < NW) sw[lane] = w;
+    }
+    __syncthreads();
+    total = sw[NW - 1];
+    const uint32_t pre = warp ? sw[warp - 1] : 0u;
+    __syncthreads();
+    return pre + x - v;
+}
+
+__global__ __launch_bounds__(BT) void k_build_count(BuildArgs a) {
+    __shared__ uint32_t sw[BT / 32];
+    const int64_t base = (int64_t)blockIdx.x * BUILD_PIX_PER_BLOCK + (int64_t)threadIdx.x * BI;
+    uint32_t c = 0;
+    for (int i = 0; i < BI; ++i) c += is_fg(a, base + i) ? 1u : 0u;
+    uint32_t tot;
+    block_excl_scan<BT / 32>(c, sw, tot);
+    if (threadIdx.x == 0) a.blk_cnt[blockIdx.x] = tot;
+}
+
+__global__ __launch_bounds__(1024) void k_build_scan(BuildArgs a) {
+    __shared__ uint32_t sw[32];
+    const int nb = a.nblocks;
+    const int per = (nb + 1023) / 1024;
+    const int b0 = min((int)threadIdx.x * per, nb), b1 = min(b0 + per, nb);
+    uint32_t local = 0;
+    for (int b = b0; b < b1; ++b) local += a.blk_cnt[b];
+    uint32_t tot;
+    uint32_t run = block_excl_scan<32>(local, sw, tot);
+    for (int b = b0; b < b1; ++b) {
+        a.blk_off[b] = run;
+        run += a.blk_cnt[b];
+    }
+    if (threadIdx.x == 0) *a.n_dev = tot;
+}
+
+__device__ __forceinline__ void copy_feat(const void *src, int src_dtype, int64_t src_row, void *dst,
+                                          int dst_dtype, int64_t dst_row, int C) {
+    if (src_dtype == TSPLAT_F32) {
+        const float *s = (const float *)src + src_row * C;
+        if (dst_dtype == TSPLAT_F32) {
+            float *d = (float *)dst + dst_row * C;
+            for (int c = 0; c < C; ++c) d[c] = s[c];
+        } else {
+            __nv_bfloat16 *d = (__nv_bfloat16 *)dst + dst_row * C;
+            for (int c = 0; c < C; ++c) d[c] = __float2bfloat16_rn(s[c]);
+        }
+    } else {
+        const __nv_bfloat16 *s = (const __nv_bfloat16 *)src + src_row * C;
+        if (dst_dtype == TSPLAT_F32) {
+            float *d = (float *)dst + dst_row * C;
+            for (int c = 0; c < C; ++c) d[c] = __bfloat162float(s[c]);
+        } else {
+            __nv_bfloat16 *d = (__nv_bfloat16 *)dst + dst_row * C;
+            for (int c = 0; c < C; ++c) d[c] = s[c];
+        }
+    }
+}
+
+// Lift pixel p (row v, column u) of view vd into Gaussian `id`.
+__device__ __forceinline__ void lift_one(const BuildArgs &a, const ViewDesc &vd, int64_t p, int64_t id) {
+    const int u = (int)(p % vd.W), v = (int)(p / vd.W);
+    const tsplat_camera &cam = vd.cam;
+    const float *R = cam.R;
+    const float z = vd.depth[p];
+    const float rx = fdiv(fsub((float)u, cam.cx), cam.fx);
+    const float ry = fdiv(fsub((float)v, cam.cy), cam.fy);
+    const float d0 = fsub(fmul(rx, z), cam.t[0]);
+    const float d1 = fsub(fmul(ry, z), cam.t[1]);
+    const float d2 = fsub(z, cam.t[2]);
+    float m[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) m[i] = fadd(fadd(fmul(R[0 * 3 + i], d0), fmul(R[1 * 3 + i], d1)), fmul(R[2 * 3 + i], d2));
+
+    float w = 1.0f, x = 0.0f, y = 0.0f, zq = 0.0f;
+    if (vd.quat) {
+        const float4 q = reinterpret_cast<const float4 *>(vd.quat)[p];
+        w = q.x; x = q.y; y = q.z; zq = q.w;
+    }
+    const float nn = fadd(fadd(fadd(fmul(w, w), fmul(x, x)), fmul(y, y)), fmul(zq, zq));
+    const float nq = fsqrt(nn);
+    w = fdiv(w, nq); x = fdiv(x, nq); y = fdiv(y, nq); zq = fdiv(zq, nq);
+    float Rq[3][3];
+    Rq[0][0] = fsub(1.0f, fmul(2.0f, fadd(fmul(y, y), fmul(zq, zq))));
+    Rq[0][1] = fmul(2.0f, fsub(fmul(x, y), fmul(w, zq)));
+    Rq[0][2] = fmul(2.0f, fadd(fmul(x, zq), fmul(w, y)));
+    Rq[1][0] = fmul(2.0f, fadd(fmul(x, y), fmul(w, zq)));
+    Rq[1][1] = fsub(1.0f, fmul(2.0f, fadd(fmul(x, x), fmul(zq, zq))));
+    Rq[1][2] = fmul(2.0f, fsub(fmul(y, zq), fmul(w, x)));
+    Rq[2][0] = fmul(2.0f, fsub(fmul(x, zq), fmul(w, y)));
+    Rq[2][1] = fmul(2.0f, fadd(fmul(y, zq), fmul(w, x)));
+    Rq[2][2] = fsub(1.0f, fmul(2.0f, fadd(fmul(x, x), fmul(y, y))));
+    const float s[3] = {vd.scale[3 * p], vd.scale[3 * p + 1], vd.scale[3 * p + 2]};
+    float M[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float rg = fadd(fadd(fmul(R[0 * 3 + i], Rq[0][j]), fmul(R[1 * 3 + i], Rq[1][j])), fmul(R[2 * 3 + i], Rq[2][j]));
+            M[i][j] = fmul(rg, s[j]);
+        }
+    auto cv = [&](int i, int j) {
+        return fadd(fadd(fmul(M[i][0], M[j][0]), fmul(M[i][1], M[j][1])), fmul(M[i][2], M[j][2]));
+    };
+    a.xyzo[id] = make_float4(m[0], m[1], m[2], vd.opacity[p]);
+    a.cova[id] = make_float4(cv(0, 0), cv(0, 1), cv(0, 2), cv(1, 1));
+    a.covb[id] = make_float2(cv(1, 2), cv(2, 2));
+    copy_feat(vd.feat, vd.feat_dtype, p, a.feat, a.out_dtype, id, a.C);
+}
+
+__global__ __launch_bounds__(BT) void k_build_lift(BuildArgs a) {
+    __shared__ uint32_t sw[BT / 32];
+    const int64_t base = (int64_t)blockIdx.x * BUILD_PIX_PER_BLOCK + (int64_t)threadIdx.x * BI;
+    uint32_t flags = 0, c = 0;
+#pragma unroll
+    for (int i = 0; i < BI; ++i)
+        if (is_fg(a, base + i)) { flags |= 1u << i; ++c; }
+    uint32_t tot;
+    int64_t id = (int64_t)a.blk_off[blockIdx.x] + block_excl_scan<BT / 32>(c, sw, tot);
+    for (int i = 0; i < BI; ++i) {
+        if (!(flags & (1u << i))) continue;
+        const int64_t g = base + i;
+        const ViewDesc &vd = a.views[view_of(a, g)];
+        lift_one(a, vd, g - vd.pix_off, id);
+        ++id;
+    }
+}
+
+__global__ void k_gaussians_set(uint64_t n, const float *mean, const float *cov, const float *opac,
+                                const void *feat, int dtype_in, int C, int dtype_out, float4 *xyzo,
+                                float4 *cova, float2 *covb, void *feat_out, uint32_t *n_dev) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) *n_dev = (uint32_t)n;
+    if (i >= n) return;
+    xyzo[i] = make_float4(mean[3 * i], mean[3 * i + 1], mean[3 * i + 2], opac[i]);
+    cova[i] = make_float4(cov[6 * i], cov[6 * i + 1], cov[6 * i + 2], cov[6 * i + 3]);
+    covb[i] = make_float2(cov[6 * i + 4], cov[6 * i + 5]);
+    copy_feat(feat, dtype_in, (int64_t)i, feat_out, dtype_out, (int64_t)i, C);
+}
+
+__global__ void k_gaussians_get(const uint32_t *n_dev, int C, int dtype, const float4 *xyzo,
+                                const float4 *cova, const float2 *covb, const void *feat_in, float *mean,
+                                float *cov, float *opac, void *feat_out) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= *n_dev) return;
+    const float4 g = xyzo[i];
+    const float4 ca = cova[i];
+    const float2 cb = covb[i];
+    if (mean) { mean[3 * i] = g.x; mean[3 * i + 1] = g.y; mean[3 * i + 2] = g.z; }
+    if (opac) opac[i] = g.w;
+    if (cov) {
+        cov[6 * i] = ca.x; cov[6 * i + 1] = ca.y; cov[6 * i + 2] = ca.z;
+        cov[6 * i + 3] = ca.w; cov[6 * i + 4] = cb.x; cov[6 * i + 5] = cb.y;
+    }
+    if (feat_out) copy_feat(feat_in, dtype, (int64_t)i, feat_out, dtype, (int64_t)i, C);
+}
+
+}  // namespace
+
+void launch_build(const BuildArgs &a, cudaStream_t s) {
+    if (a.nblocks <= 0) {
+        cudaMemsetAsync(a.n_dev, 0, sizeof(uint32_t), s);
+        return;
+    }
+    k_build_count<<<a.nblocks, BT, 0, s>>>(a);
+    k_build_scan<<<1, 1024, 0, s>>>(a);
+    k_build_lift<<<a.nblocks, BT, 0, s>>>(a);
+}
+
+void launch_gaussians_set(int64_t n, const float *mean, const float *cov, const float *opac, const void *feat,
+                          int feat_dtype_in, int C, int out_dtype, float4 *xyzo, float4 *cova, float2 *covb,
+                          void *feat_out, uint32_t *n_dev, cudaStream_t s) {
+    const int64_t blocks = n > 0 ? (n + 255) / 256 : 1;
+    k_gaussians_set<<<(unsigned)blocks, 256, 0, s>>>((uint64_t)n, mean, cov, opac, feat, feat_dtype_in, C,
+                                                     out_dtype, xyzo, cova, covb, feat_out, n_dev);
+}
+
+void launch_gaussians_get(const uint32_t *n_dev, int64_t cap, int C, int dtype, const float4 *xyzo,
+                          const float4 *cova, const float2 *covb, const void *feat_in, float *mean, float *cov,
+                          float *opac, void *feat_out, cudaStream_t s) {
+    if (cap <= 0) return;
+    k_gaussians_get<<<(unsigned)((cap + 255) / 256), 256, 0, s>>>(n_dev, C, dtype, xyzo, cova, covb, feat_in,
+                                                                  mean, cov, opac, feat_out);
+}
+
+}  // namespace tsp

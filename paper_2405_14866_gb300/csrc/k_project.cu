@@ -1,0 +1,251 @@
+// A2: EWA projection of 3D Gaussians into the target camera (the cited
+// 3DGS rasterizer's preprocessing, Tele-Aloha Sec. 4.2).
+//
+// Every quantity that decides an integer -- visibility, radius, tile rect,
+// depth key -- is evaluated in single precision one correctly rounded
+// operation at a time (__f*_rn), in a fixed order, so that an independent
+// implementation following the same order obtains the same bits.
+#include <math.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace tsp {
+
+namespace {
+
+// Half extents of the box around mean2d outside which alpha < alpha_min:
+// o e^q >= alpha_min  <=>  d^T Q d <= kappa = 2 ln(o / alpha_min), whose
+// bounding box has half widths sqrt(kappa Q^-1_00), sqrt(kappa Q^-1_11).
+// Padded by 1% + 0.01 px so that the kernel's own rounding never reaches
+// it; unbounded when Q is too ill-conditioned to evaluate safely.
+__device__ __forceinline__ void cull_extents(float a, float b, float c, float o, float alpha_min,
+                                             float &ex, float &ey) {
+    if (!(o >= alpha_min)) {  // alpha <= o < alpha_min everywhere (or NaN)
+        ex = ey = -INFINITY;
+        return;
+    }
+    const float kappa = 2.0f * logf(o / alpha_min);
+    const float detq = a * c - b * b;
+    if (!(detq > 1e-4f * a * c) || !isfinite(detq)) {
+        ex = ey = INFINITY;
+        return;
+    }
+    ex = sqrtf(kappa * c / detq) * 1.01f + 0.01f;
+    ey = sqrtf(kappa * a / detq) * 1.01f + 0.01f;
+    if (!isfinite(ex) || !isfinite(ey)) ex = ey = INFINITY;
+}
+
+// floor(v) clamped to [0, hi] and converted (v may be +-inf)
+__device__ __forceinline__ int clamp_floor(float v, int hi) {
+    return (int)fminf((float)hi, fmaxf(0.0f, floorf(v)));
+}
+
+__device__ __forceinline__ void write_culled(const ProjectOut &o, uint64_t i) {
+    o.hdr[i].h0 = make_float4(0.f, 0.f, 0.f, 0.f);
+    o.hdr[i].h1 = make_float4(0.f, 0.f, -INFINITY, -INFINITY);
+    o.rect[i] = make_uint2(0u, 0u);
+    o.ntiles[i] = 0u;
+    o.dkey[i] = CULLED_KEY;
+    o.radius[i] = 0.0f;
+}
+
+// Rendered-Gaussian bookkeeping: depth-key range (for the radix sort's pass
+// count) and the visible count, reduced per warp before the atomics.
+// Called by all 32 lanes of every warp.
+__device__ __forceinline__ void account(const ProjectOut &o, bool vis, uint32_t key) {
+    const uint32_t m = 0xffffffffu;
+    const uint32_t kmin = __reduce_min_sync(m, vis ? key : CULLED_KEY);
+    const uint32_t kmax = __reduce_max_sync(m, vis ? key : 0u);
+    const uint32_t nv = __popc(__ballot_sync(m, vis));
+    if ((threadIdx.x & 31) == 0 && nv) {
+        atomicMin(&o.kminmax[0], kmin);
+        atomicMax(&o.kminmax[1], kmax);
+        atomicAdd(o.n_vis, nv);
+    }
+}
+
+// Tile rect from mean2d and radius, as the cited rasterizer defines it.
+__device__ __forceinline__ int tile_rect(float mx, float my, float r, int tiles_x, int tiles_y, int &x0,
+                                         int &y0, int &x1, int &y1) {
+    x0 = clamp_floor(fdiv(fsub(mx, r), 16.0f), tiles_x);
+    x1 = clamp_floor(fdiv(fadd(fadd(mx, r), 15.0f), 16.0f), tiles_x);
+    y0 = clamp_floor(fdiv(fsub(my, r), 16.0f), tiles_y);
+    y1 = clamp_floor(fdiv(fadd(fadd(my, r), 15.0f), 16.0f), tiles_y);
+    return (x1 - x0) * (y1 - y0);
+}
+
+__global__ __launch_bounds__(256) void k_project(const float4 *__restrict__ xyzo,
+                                                 const float4 *__restrict__ cova,
+                                                 const float2 *__restrict__ covb,
+                                                 const uint32_t *n_dev, tsplat_camera cam,
+                                                 tsplat_render_params par, int tiles_x, int tiles_y,
+                                                 ProjectOut o) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = i < (uint64_t)*n_dev;
+    bool vis = false;
+    uint32_t key = CULLED_KEY;
+    if (active) {
+    const float4 g = xyzo[i];
+    const float *R = cam.R;
+    const float px = fadd(fadd(fadd(fmul(R[0], g.x), fmul(R[1], g.y)), fmul(R[2], g.z)), cam.t[0]);
+    const float py = fadd(fadd(fadd(fmul(R[3], g.x), fmul(R[4], g.y)), fmul(R[5], g.z)), cam.t[1]);
+    const float pz = fadd(fadd(fadd(fmul(R[6], g.x), fmul(R[7], g.y)), fmul(R[8], g.z)), cam.t[2]);
+    vis = pz > cam.z_near && pz < cam.z_far;
+    if (vis) {
+        const float limx = fmul(par.frustum_clamp, fdiv(fmul(0.5f, (float)cam.width), cam.fx));
+        const float limy = fmul(par.frustum_clamp, fdiv(fmul(0.5f, (float)cam.height), cam.fy));
+        const float txz = fminf(limx, fmaxf(-limx, fdiv(px, pz)));
+        const float tyz = fminf(limy, fmaxf(-limy, fdiv(py, pz)));
+        const float tx = fmul(txz, pz), ty = fmul(tyz, pz);
+        const float pz2 = fmul(pz, pz);
+        const float j00 = fdiv(cam.fx, pz), j02 = -fdiv(fmul(cam.fx, tx), pz2);
+        const float j11 = fdiv(cam.fy, pz), j12 = -fdiv(fmul(cam.fy, ty), pz2);
+        float T0[3], T1[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            T0[j] = fadd(fmul(j00, R[0 * 3 + j]), fmul(j02, R[2 * 3 + j]));
+            T1[j] = fadd(fmul(j11, R[1 * 3 + j]), fmul(j12, R[2 * 3 + j]));
+        }
+        const float4 ca = cova[i];
+        const float2 cb = covb[i];
+        const float V[3][3] = {{ca.x, ca.y, ca.z}, {ca.y, ca.w, cb.x}, {ca.z, cb.x, cb.y}};
+        float U0[3], U1[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            U0[k] = fadd(fadd(fmul(T0[0], V[0][k]), fmul(T0[1], V[1][k])), fmul(T0[2], V[2][k]));
+            U1[k] = fadd(fadd(fmul(T1[0], V[0][k]), fmul(T1[1], V[1][k])), fmul(T1[2], V[2][k]));
+        }
+        const float s00 = fadd(fadd(fmul(U0[0], T0[0]), fmul(U0[1], T0[1])), fmul(U0[2], T0[2]));
+        const float s01 = fadd(fadd(fmul(U0[0], T1[0]), fmul(U0[1], T1[1])), fmul(U0[2], T1[2]));
+        const float s11 = fadd(fadd(fmul(U1[0], T1[0]), fmul(U1[1], T1[1])), fmul(U1[2], T1[2]));
+        const float a = fadd(s00, par.lowpass), b = s01, c = fadd(s11, par.lowpass);
+        const float det = fsub(fmul(a, c), fmul(b, b));
+        if (!(det > 0.0f) || !isfinite(det)) {
+            vis = false;
+        } else {
+            const float mid = fmul(0.5f, fadd(a, c));
+            const float disc = fmaxf(0.1f, fsub(fmul(mid, mid), det));
+            const float lam = fadd(mid, fsqrt(disc));
+            const float r = ceilf(fmul(3.0f, fsqrt(lam)));
+            const float mx = fadd(fdiv(fmul(cam.fx, px), pz), cam.cx);
+            const float my = fadd(fdiv(fmul(cam.fy, py), pz), cam.cy);
+            int x0, y0, x1, y1;
+            const int nt = tile_rect(mx, my, r, tiles_x, tiles_y, x0, y0, x1, y1);
+            if (nt <= 0) {
+                vis = false;
+            } else {
+                const float ca_ = fdiv(c, det), cb_ = -fdiv(b, det), cc_ = fdiv(a, det);
+                float ex, ey;
+                cull_extents(ca_, cb_, cc_, g.w, par.alpha_min, ex, ey);
+                o.hdr[i].h0 = make_float4(mx, my, ca_, cb_);
+                o.hdr[i].h1 = make_float4(cc_, g.w, ex, ey);
+                o.rect[i] = pack_rect(x0, y0, x1, y1);
+                o.ntiles[i] = (uint32_t)nt;
+                key = __float_as_uint(pz);
+                o.dkey[i] = key;
+                o.radius[i] = r;
+            }
+        }
+    }
+    if (!vis) write_culled(o, i);
+    }
+    account(o, vis, key);
+}
+
+__global__ __launch_bounds__(256) void k_prepare_2d(uint64_t n, const float *__restrict__ mean2d,
+                                                    const float *__restrict__ conic,
+                                                    const float *__restrict__ opac,
+                                                    const float *__restrict__ depth,
+                                                    const int32_t *__restrict__ radius,
+                                                    tsplat_render_params par, int tiles_x,
+                                                    int tiles_y, ProjectOut o) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = i < n;
+    bool vis = false;
+    uint32_t key = CULLED_KEY;
+    if (active) {
+    const int32_t ri = radius[i];
+    const float z = depth[i];
+    vis = ri > 0 && z > 0.0f;
+    if (vis) {
+        const float mx = mean2d[2 * i], my = mean2d[2 * i + 1];
+        const float r = (float)ri;
+        int x0, y0, x1, y1;
+        const int nt = tile_rect(mx, my, r, tiles_x, tiles_y, x0, y0, x1, y1);
+        if (nt <= 0) {
+            vis = false;
+        } else {
+            const float a = conic[3 * i], b = conic[3 * i + 1], c = conic[3 * i + 2];
+            float ex, ey;
+            cull_extents(a, b, c, opac[i], par.alpha_min, ex, ey);
+            o.hdr[i].h0 = make_float4(mx, my, a, b);
+            o.hdr[i].h1 = make_float4(c, opac[i], ex, ey);
+            o.rect[i] = pack_rect(x0, y0, x1, y1);
+            o.ntiles[i] = (uint32_t)nt;
+            key = __float_as_uint(z);
+            o.dkey[i] = key;
+            o.radius[i] = r;
+        }
+    }
+    if (!vis) write_culled(o, i);
+    }
+    account(o, vis, key);
+}
+
+// export of header fields: 2 = mean2d, 3 = conic
+__global__ void k_export_header(const Header *hdr, const uint32_t *n_dev, int what, float *dst) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= *n_dev) return;
+    const Header h = hdr[i];
+    if (what == TSPLAT_EXPORT_MEAN2D) {
+        dst[2 * i] = h.h0.x;
+        dst[2 * i + 1] = h.h0.y;
+    } else {
+        dst[3 * i] = h.h0.z;
+        dst[3 * i + 1] = h.h0.w;
+        dst[3 * i + 2] = h.h1.x;
+    }
+}
+
+__global__ void k_export_rect(const uint2 *rect, const uint32_t *n_dev, int32_t *dst) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= *n_dev) return;
+    int x0, y0, x1, y1;
+    unpack_rect(rect[i], x0, y0, x1, y1);
+    dst[4 * i] = x0;
+    dst[4 * i + 1] = y0;
+    dst[4 * i + 2] = x1;
+    dst[4 * i + 3] = y1;
+}
+
+}  // namespace
+
+void launch_export_rect(const uint2 *rect, const uint32_t *n_dev, int64_t n_cap, int32_t *dst, cudaStream_t s) {
+    if (n_cap <= 0) return;
+    k_export_rect<<<(unsigned)((n_cap + 255) / 256), 256, 0, s>>>(rect, n_dev, dst);
+}
+
+void launch_project(const float4 *xyzo, const float4 *cova, const float2 *covb, const uint32_t *n_dev,
+                    int64_t n_cap, const tsplat_camera &cam, const tsplat_render_params &par,
+                    int tiles_x, int tiles_y, const ProjectOut &o, cudaStream_t s) {
+    if (n_cap <= 0) return;
+    k_project<<<(unsigned)((n_cap + 255) / 256), 256, 0, s>>>(xyzo, cova, covb, n_dev, cam, par, tiles_x,
+                                                              tiles_y, o);
+}
+
+void launch_prepare_2d(int64_t n, const float *mean2d, const float *conic, const float *opac,
+                       const float *depth, const int32_t *radius, const tsplat_render_params &par,
+                       int tiles_x, int tiles_y, const ProjectOut &o, cudaStream_t s) {
+    if (n <= 0) return;
+    k_prepare_2d<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((uint64_t)n, mean2d, conic, opac, depth, radius,
+                                                             par, tiles_x, tiles_y, o);
+}
+
+void launch_export_header(const Header *hdr, const uint32_t *n_dev, int64_t n_cap, int what, void *dst,
+                          cudaStream_t s) {
+    if (n_cap <= 0) return;
+    k_export_header<<<(unsigned)((n_cap + 255) / 256), 256, 0, s>>>(hdr, n_dev, what, (float *)dst);
+}
+
+}  // namespace tsp

@@ -1,0 +1,67 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry
+point that include/tsplat.h declares (no GPU work: host-only calls)."""
+import ctypes
+import os
+import re
+import subprocess
+
+from paper_2405_14866_gb300 import _lib as L
+from paper_2405_14866_gb300 import build as B
+
+HEADERS = [os.path.join(B.ROOT, "include", f) for f in sorted(os.listdir(os.path.join(B.ROOT, "include")))
+           if f.endswith(".h")]
+
+
+def declared():
+    names = set()
+    for h in HEADERS:
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"\b(tsplat_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol():
+    lib = L.lib()
+    names = declared()
+    assert len(names) >= 20
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    out = subprocess.run(["nm", "-D", "--defined-only", B.LIB], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (tsplat_\w+)", out))
+    assert set(names) <= exported
+
+
+def test_binding_signatures_cover_the_header():
+    assert set(declared()) == set(L.declared_symbols())
+
+
+def test_struct_layouts_match_header():
+    assert ctypes.sizeof(L.CCamera) == 4 * 4 + 2 * 4 + 9 * 4 + 3 * 4 + 2 * 4
+    assert ctypes.sizeof(L.CParams) == 6 * 4
+    assert ctypes.sizeof(L.CSrcView) == 6 * 8 + 2 * 4 + ctypes.sizeof(L.CCamera)
+
+
+def test_host_only_calls():
+    lib = L.lib()
+    p = L.CParams()
+    lib.tsplat_render_params_default(ctypes.byref(p))
+    assert abs(p.lowpass - 0.3) < 1e-7 and abs(p.alpha_max - 0.99) < 1e-7
+    assert abs(p.alpha_min - 1 / 255) < 1e-9 and abs(p.t_min - 1e-4) < 1e-10 and p.flags == 0
+    assert b"sm_103a" in lib.tsplat_version()
+
+
+def test_invalid_arguments_are_rejected_without_device_work():
+    lib = L.lib()
+    h = ctypes.c_void_p()
+    assert lib.tsplat_gaussians_create(10, 0, 0, ctypes.byref(h)) == 1      # C = 0
+    assert b"C = 0" in lib.tsplat_last_error()
+    assert lib.tsplat_gaussians_create(10, 8, 7, ctypes.byref(h)) == 1      # bad dtype
+    assert lib.tsplat_build(None, 1, 8, 0, ctypes.byref(h), None) == 1
+    assert lib.tsplat_backward(None, None, None, None, None, None, None, None) == 1
+
+
+def test_sources_use_no_multicast_and_no_trap():
+    bad = re.compile(r"multicast|__trap|asm\s*\(\s*\"trap")
+    for src in B.sources():
+        assert not bad.search(open(src).read()), src
