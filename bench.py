@@ -1,0 +1,411 @@
+#!/usr/bin/env python
+"""Benchmark of the latent-Gaussian splatting hot path on GB300.
+
+Workload (default): four 1024x1024 source views -> ~2.10M Gaussians with
+32-channel features stored as BF16, rendered into one 1024x1024 target view.
+One step = lifting (A1, tsplat_build) + rendering (A2..A7, tsplat_render) of
+one view, so `value` is views/s for the whole path.  Inputs (source maps,
+~660 MB) and the Gaussian store (~220 MB) exceed the 129 MB L2, so no flush
+is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (the only other implementation of this path), scaled to views/s.
+With N > 1 (torchrun) each rank renders its own replica (weak scaling);
+there is no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "views/s & p99 ms, 2M-Gaussian 1024² 32-ch feature splat; % of HBM roofline"
+STAGES = ("project", "depth_sort", "scan_emit", "tile_sort", "ranges", "composite")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["precision", "paper", "tiny"], default="precision")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def make_scene(workload, rank):
+    from paper_2405_14866_gb300 import gen
+    if workload == "precision":
+        return gen.scene_precision(seed=2 + 1000 * rank)
+    if workload == "paper":
+        return gen.scene_paper(seed=1 + 1000 * rank)
+    return gen.scene_tiny(seed=0 + 1000 * rank)
+
+
+def workload_desc(sc):
+    v = sc.views[0]
+    H, W = v.depth.shape
+    t = sc.targets[0]
+    return (f"{sc.name}: {len(sc.views)} x {W}x{H} source views -> {sc.n_foreground} Gaussians, "
+            f"{sc.C}-ch {'BF16' if sc.feat_dtype == 1 else 'FP32'} features, {t.width}x{t.height} target")
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.samples = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", gpu_id], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.time(), [x.strip() for x in line.split(",")]))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        inside = [s for (t, s) in self.samples if t0 - 0.1 <= t <= t1 + 0.1]
+        if not inside and self.samples:  # timed region shorter than the sampling period: nearest sample
+            inside = [min(self.samples, key=lambda ts: abs(ts[0] - (t0 + t1) / 2))[1]]
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "n_samples": 0}
+        sm = [float(s[0]) for s in inside if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in inside if s[1].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[k] for s in inside for k in range(4) if len(s) > 3 + k and s[3 + k] == "Active"})
+        pw = [float(s[2]) for s in inside if s[2].replace(".", "").isdigit()]
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "n_samples": len(inside), "power_w_max": max(pw) if pw else None}
+
+
+def gpu_id_for(dev):
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return str(dev)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    return 6800.0, "fallback (6.8 TB/s)"
+
+
+def kernel_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel's
+    source is unchanged since the capture (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p)).get(kernel)
+    if not d:
+        return None
+    src = os.path.join(ROOT, "paper_2405_14866_gb300", "csrc", d["source"])
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return d["bytes_per_launch"] if h == d["source_sha256_16"] else None
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded sample (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+class OracleSample:
+    """Times the FP64 oracle on a bounded sample of the workload and scales
+    it to one view: lifting + projection + binning on every 16th source row
+    (x16), compositing on a fixed set of tiles (x tiles/sample)."""
+
+    ROW_STRIDE = 16
+    N_TILES = 32
+
+    def __init__(self, sc):
+        from oracle import oracle as O
+        self.O = O
+        self.sc = sc
+        self.cam = sc.targets[0]
+        g32 = O.lift_scene(sc, "f32")
+        pr = O.project_f32(g32, self.cam)
+        self.bins = O.bin_gaussians(pr, self.cam.width, self.cam.height)
+        self.g32 = g32
+        self.mu = pr.mu.astype(np.float64)
+        self.conic = pr.conic.astype(np.float64)
+        self.opac = g32.opac.astype(np.float64)
+        self.feat = g32.feat.astype(np.float64)
+        T = self.bins.tiles_x * self.bins.tiles_y
+        nonempty = [t for t in range(T) if self.bins.ranges[t, 1] > self.bins.ranges[t, 0]]
+        # representative sample: evenly spaced over all tiles (empty ones included)
+        self.tiles = list(range(0, T, max(1, T // self.N_TILES)))[: self.N_TILES]
+        self.T = T
+        self.sub_views = []
+        from paper_2405_14866_gb300 import gen
+        for v in sc.views:
+            s = slice(None, None, self.ROW_STRIDE)
+            self.sub_views.append(gen.SourceView(v.depth[s], v.mask[s], v.scale[s], v.quat[s], v.opacity[s],
+                                                 v.feat[s], v.cam))
+        self.nonempty = len(nonempty)
+
+    def step(self):
+        O = self.O
+        t0 = time.perf_counter()
+        parts = [O.lift_view(v, "f32") for v in self.sub_views]
+        g = O.Gaussians(*(np.concatenate([getattr(p, k) for p in parts], 0) for k in ("mean", "cov", "opac", "feat")))
+        pr = O.project_f32(g, self.cam)
+        O.bin_gaussians(pr, self.cam.width, self.cam.height)
+        t1 = time.perf_counter()
+        O.composite(self.mu, self.conic, self.opac, self.feat, self.cam.width, self.cam.height, self.bins,
+                    tiles=self.tiles)
+        t2 = time.perf_counter()
+        view_s = (t1 - t0) * self.ROW_STRIDE + (t2 - t1) * self.T / len(self.tiles)
+        return view_s, t2 - t0
+
+    def describe(self):
+        return (f"FP64 oracle: lift+project+bin on every {self.ROW_STRIDE}th source row (x{self.ROW_STRIDE}), "
+                f"composite on {len(self.tiles)} of {self.T} tiles (x{self.T / len(self.tiles):.0f}); "
+                f"scaled to one view")
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    sc = make_scene(args.workload, 0)
+    samp = OracleSample(sc)
+    for _ in range(max(0, min(args.warmup, 1))):
+        samp.step()
+    tot_view, tot_wall = 0.0, 0.0
+    for _ in range(args.steps):
+        v, w = samp.step()
+        tot_view += v
+        tot_wall += w
+    value = args.steps / tot_view
+    line = {"metric": METRIC, "value": value, "unit": "views/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot_view / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": workload_desc(sc), "step": "one view, scaled from a bounded sample"},
+            "cpu_baseline": {"value": value, "unit": "views/s", "cores": O.num_threads(), "kind": "oracle",
+                             "sample": samp.describe()},
+            "e2e": {"value": value, "unit": "views/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+
+    from paper_2405_14866_gb300 import api
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    sc = make_scene(args.workload, rank)
+    cam = sc.targets[0]
+    up = api.upload_scene(sc)
+    views = [api.source_view(v["depth"], v["mask"], v["scale"], v["quat"], v["opacity"], v["feat"], v["cam"])
+             for v in up["views"]]
+    g = api.Gaussians.build(views, sc.C, sc.feat_dtype)
+    ctx = api.Context()
+    F, A = ctx.render(g, cam)                     # sizes the scratch (one synchronizing render)
+    st = ctx.stats()
+    N, P = st["n_gaussians"], st["n_pairs"]
+    ctx.reserve(g.capacity, int(P * 1.25) + 65536, cam.width, cam.height, sc.C)
+
+    def step(profile):
+        g.build_into(views)
+        ctx.render(g, cam, async_=True, out_feat=F, out_alpha=A, profile=profile)
+
+    for _ in range(args.warmup):
+        step(False)
+    ctx.status()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    sampler = ClockSampler(gpu_id_for(dev))
+    time.sleep(0.3)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    launches0 = api.launch_count()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.time()
+    ev[0].record()
+    for k in range(args.steps):
+        step(True)
+        ev[k + 1].record()
+    torch.cuda.synchronize()
+    t1 = time.time()
+    barrier()
+    launches = api.launch_count() - launches0
+    sampler.stop()
+    ctx.status()                                   # no capacity overflow inside the timed region
+    stages = ctx.timings()
+    step_ms = np.array([ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)])
+    total_ms = float(ev[0].elapsed_time(ev[-1]))
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    value = world * args.steps / (total_ms * 1e-3)
+    clocks = sampler.summary(t0, t1)
+
+    # render only (Gaussians resident), for context
+    for _ in range(3):
+        ctx.render(g, cam, async_=True, out_feat=F, out_alpha=A)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        ctx.render(g, cam, async_=True, out_feat=F, out_alpha=A)
+    e1.record()
+    torch.cuda.synchronize()
+    render_ms = e0.elapsed_time(e1) / args.steps
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b0.record()
+    for _ in range(args.steps):
+        g.build_into(views)
+    b1.record()
+    torch.cuda.synchronize()
+    build_ms = b0.elapsed_time(b1) / args.steps
+    ctx.status()
+
+    # roofline of the dominant kernel (compositing): algorithmic bytes per
+    # launch = P (4 B id + 24 B record + C*b_f features) + W*H*(4C + 4) outputs
+    bf = 2 if sc.feat_dtype == api.BF16 else 4
+    comp_bytes = P * (4 + 24 + sc.C * bf) + cam.width * cam.height * (4 * sc.C + 4)
+    comp_ms = stages["composite"]
+    peak, peak_src = measured_peaks()
+    achieved = comp_bytes / (comp_ms * 1e-3) / 1e9
+    roofline = {"kernel": "k_composite", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": kernel_traffic("k_composite"),
+                "algorithmic_bytes": comp_bytes, "peak_source": peak_src}
+    # whole path (A1..A7) against the same peak, per the algorithmic byte model
+    path_bytes = (N * (40 + 36) + N * 8 + N * 12 + P * 12 + P * 24 + P * 8 + st["tiles_x"] * st["tiles_y"] * 8
+                  + comp_bytes)
+    build_bytes = sum(v.depth.size * (4 + 1 + 12 + 16 + 4 + 4 * sc.C) for v in sc.views) + N * (40 + sc.C * bf)
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        pin = [{k: t.cpu().pin_memory() for k, t in v.items() if k != "cam"} for v in up["views"]]
+        Fh = torch.empty(F.shape, dtype=F.dtype, pin_memory=True)
+        Ah = torch.empty(A.shape, dtype=A.dtype, pin_memory=True)
+        h2d = sum(t.numel() * t.element_size() for v in pin for t in v.values())
+        d2h = F.numel() * 4 + A.numel() * 4
+
+        def e2e_step():
+            for v, p in zip(up["views"], pin):
+                for k, t in p.items():
+                    v[k].copy_(t, non_blocking=True)
+            g.build_into(views)
+            ctx.render(g, cam, async_=True, out_feat=F, out_alpha=A)
+            Fh.copy_(F, non_blocking=True)
+            Ah.copy_(A, non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        x0.record()
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        x1.record()
+        torch.cuda.synchronize()
+        ctx.status()
+        e2e_ms = x0.elapsed_time(x1) / args.e2e_steps
+        e2e = {"value": world * 1e3 / e2e_ms, "unit": "views/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import oracle as O
+        samp = OracleSample(sc)
+        vals = [samp.step()[0] for _ in range(2)]
+        cpu = {"value": 1.0 / float(np.mean(vals)), "unit": "views/s", "cores": O.num_threads(), "kind": "oracle",
+               "sample": samp.describe()}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "views/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": workload_desc(sc), "gaussians": N, "pairs": P, "feat_storage":
+                           "bf16" if sc.feat_dtype == api.BF16 else "f32",
+                           "step": "tsplat_build (A1) + tsplat_render (A2-A7) of one 1024^2 view",
+                           "l2": "inputs larger than L2 (source maps ~660 MB, Gaussians ~220 MB)",
+                           "parallelism": f"replicas x{world}"},
+                "step_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
+                "render_only": {"views_per_s": 1e3 / render_ms, "ms": render_ms,
+                                "frac_of_peak": path_bytes / (render_ms * 1e-3) / 1e9 / peak},
+                "build_ms": build_ms, "build_gbs": build_bytes / (build_ms * 1e-3) / 1e9,
+                "stages_ms": stages, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": int(launches)}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -78,7 +78,10 @@ enum {
     TSPLAT_RENDER_ASYNC = 1u << 0,
     /* Keep what tsplat_backward needs (final transmittance and last
      * blended index per pixel). */
-    TSPLAT_RENDER_SAVE = 1u << 1
+    TSPLAT_RENDER_SAVE = 1u << 1,
+    /* Record CUDA events between the stages of this render on its stream
+     * (read back with tsplat_ctx_timings). */
+    TSPLAT_RENDER_PROFILE = 1u << 2
 };
 
 /* Rasterizer constants (the 3DGS rasterizer's; all parameters). */
@@ -281,6 +284,16 @@ tsplat_status tsplat_rasterize(int64_t n, const float *mean2d, const float *coni
 tsplat_status tsplat_backward(tsplat_ctx *ctx, const float *dL_dfeat, const float *dL_dalpha,
                               float *d_mean2d, float *d_conic, float *d_opac, float *d_feat,
                               void *stream);
+
+/* Mean stage durations, in milliseconds, of the renders on `ctx` that used
+ * TSPLAT_RENDER_PROFILE since the previous call (at most the last 256),
+ * measured with CUDA events on the render's stream; synchronizes and
+ * resets.  ms[0..5] = project (A2), depth sort, scan + emission (A3/A4),
+ * tile sort (A5), ranges (A6), composite (A7); *n_out = 6. */
+tsplat_status tsplat_ctx_timings(tsplat_ctx *ctx, float *ms, int32_t capacity, int32_t *n_out);
+
+/* Number of kernel launches the library has issued in this process. */
+uint64_t tsplat_launch_count(void);
 
 /* Thread-local message of the last failed call on this thread. */
 const char *tsplat_last_error(void);

@@ -49,22 +49,29 @@ def ccamera(cam) -> L.CCamera:
 
 
 def cparams(lowpass=0.3, alpha_max=0.99, alpha_min=1.0 / 255.0, t_min=1e-4, frustum_clamp=1.3,
-            save=False, async_=False) -> L.CParams:
+            save=False, async_=False, profile=False) -> L.CParams:
     p = L.CParams()
     p.lowpass, p.alpha_max, p.alpha_min, p.t_min, p.frustum_clamp = lowpass, alpha_max, alpha_min, t_min, frustum_clamp
-    p.flags = (L.RENDER_SAVE if save else 0) | (L.RENDER_ASYNC if async_ else 0)
+    p.flags = (L.RENDER_SAVE if save else 0) | (L.RENDER_ASYNC if async_ else 0) | (L.RENDER_PROFILE if profile else 0)
     return p
 
 
-def _with_flags(params: Optional[L.CParams], save: bool, async_: bool) -> L.CParams:
+def _with_flags(params: Optional[L.CParams], save: bool, async_: bool, profile: bool = False) -> L.CParams:
     if params is None:
-        return cparams(save=save, async_=async_)
+        return cparams(save=save, async_=async_, profile=profile)
     p = L.CParams.from_buffer_copy(params)
     if save:
         p.flags |= L.RENDER_SAVE
     if async_:
         p.flags |= L.RENDER_ASYNC
+    if profile:
+        p.flags |= L.RENDER_PROFILE
     return p
+
+
+def launch_count() -> int:
+    """Kernel launches issued by libtsplat in this process."""
+    return int(L.lib().tsplat_launch_count())
 
 
 def source_view(depth, mask, scale, quat, opacity, feat, cam, feat_dtype=F32) -> L.CSrcView:
@@ -176,14 +183,14 @@ class Context:
         L.call("tsplat_ctx_reserve", self.handle, max_gaussians, max_pairs, max_width, max_height, C)
 
     def render(self, g: Gaussians, cam, params: Optional[L.CParams] = None, save=False, async_=False,
-               out_feat=None, out_alpha=None, stream=None):
+               out_feat=None, out_alpha=None, stream=None, profile=False):
         cc = ccamera(cam)
         W, H = cc.width, cc.height
         if out_feat is None:
             out_feat = torch.empty((g.C, H, W), device="cuda")
         if out_alpha is None:
             out_alpha = torch.empty((H, W), device="cuda")
-        p = _with_flags(params, save, async_)
+        p = _with_flags(params, save, async_, profile)
         L.call("tsplat_render", g.handle, ctypes.byref(cc), ctypes.byref(p), _ptr(out_feat), _ptr(out_alpha),
                self.handle, _stream(stream))
         self.n = None
@@ -215,6 +222,13 @@ class Context:
         L.call("tsplat_backward", self.handle, _ptr(dF.contiguous()), _ptr(None if dA is None else dA.contiguous()),
                *(_ptr(o) for o in outs), _stream(stream))
         return outs
+
+    def timings(self) -> Dict[str, float]:
+        """Stage durations (ms) of the last profiled render (synchronizes)."""
+        ms = (ctypes.c_float * len(L.STAGES))()
+        n = ctypes.c_int32()
+        L.call("tsplat_ctx_timings", self.handle, ms, len(L.STAGES), ctypes.byref(n))
+        return {L.STAGES[i]: float(ms[i]) for i in range(n.value)}
 
     def stats(self) -> Dict[str, int]:
         s = L.CStats()

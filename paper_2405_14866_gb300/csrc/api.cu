@@ -1,11 +1,13 @@
 // Host side of the C ABI declared in include/tsplat.h: handles, scratch
 // management and the ordering of the kernel launches.  No arithmetic of the
 // method happens here; every step runs in the kernels of k_*.cu.
+#include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <new>
 #include <string>
 
@@ -17,6 +19,7 @@ using namespace tsp;
 namespace {
 
 thread_local std::string g_err;
+std::atomic<uint64_t> g_launches{0};
 
 tsplat_status fail(tsplat_status st, const char *fmt, ...) {
     char buf[512];
@@ -87,6 +90,10 @@ int tile_digits(int n_tiles) {  // radix passes over tile ids 0..n_tiles-1
 
 }  // namespace
 
+namespace tsp {
+void note_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+}  // namespace tsp
+
 // ------------------------------------------------------------------ handles
 
 struct tsplat_gaussians {
@@ -118,6 +125,11 @@ struct tsplat_ctx {
     const uint32_t *pairs = nullptr;  // sorted Gaussian ids
     bool saved = false;
     float alpha_max = 0, alpha_min = 0;
+    // stage events of profiled renders (TSPLAT_RENDER_PROFILE): a ring of
+    // the last RING renders, averaged and reset by tsplat_ctx_timings
+    static constexpr int N_EV = 7, RING = 256;
+    cudaEvent_t ev[RING][N_EV] = {};
+    int64_t n_prof = 0;
 };
 
 namespace {
@@ -226,6 +238,7 @@ static tsplat_status build_into(tsplat_gaussians *g, const tsplat_src_view *view
         if (H <= 0 || W <= 0 || H > 16383 || W > 16383) return fail(TSPLAT_ERR_INVALID_ARG, "view %d: size %dx%d", v, W, H);
         if (!sv.depth || !sv.scale || !sv.opacity || !sv.feat) return fail(TSPLAT_ERR_INVALID_ARG, "view %d: NULL map", v);
         if (sv.quat && ((uintptr_t)sv.quat & 15)) return fail(TSPLAT_ERR_INVALID_ARG, "view %d: quat not 16-byte aligned", v);
+        if ((g->C % 4) == 0 && ((uintptr_t)sv.feat & 15)) return fail(TSPLAT_ERR_INVALID_ARG, "view %d: feat not 16-byte aligned", v);
         if (sv.feat_dtype != TSPLAT_F32 && sv.feat_dtype != TSPLAT_BF16) return fail(TSPLAT_ERR_INVALID_ARG, "view %d: feat_dtype", v);
         ViewDesc &d = a.views[v];
         d.depth = sv.depth; d.mask = sv.mask; d.scale = sv.scale; d.quat = sv.quat; d.opacity = sv.opacity;
@@ -296,6 +309,9 @@ tsplat_status tsplat_ctx_destroy(tsplat_ctx *c) {
                     &c->svals1, &c->hist_n, &c->emit_blk, &c->pk0, &c->pk1, &c->pv0, &c->pv1, &c->hist_p,
                     &c->ranges, &c->tfinal, &c->last, &c->small};
     for (DBuf *b : bufs) release(*b);
+    for (auto &row : c->ev)
+        for (cudaEvent_t e : row)
+            if (e) cudaEventDestroy(e);
     if (c->host_small) cudaFreeHost(c->host_small);
     delete c;
     return TSPLAT_OK;
@@ -354,6 +370,15 @@ tsplat_status tsplat_ctx_reserve(tsplat_ctx *c, int64_t max_gaussians, int64_t m
     return TSPLAT_OK;
 }
 
+static tsplat_status mark(tsplat_ctx *c, bool prof, int i, cudaStream_t s) {
+    if (!prof) return TSPLAT_OK;
+    cudaEvent_t &e = c->ev[c->n_prof % tsplat_ctx::RING][i];
+    if (!e) TRY_CUDA(cudaEventCreate(&e));
+    TRY_CUDA(cudaEventRecord(e, s));
+    if (i == tsplat_ctx::N_EV - 1) ++c->n_prof;
+    return TSPLAT_OK;
+}
+
 // A2 (done by the caller of this function) .. A7
 static tsplat_status render_tail(tsplat_ctx *c, int64_t n_cap, const uint32_t *n_dev, const void *feat, int C,
                                  int dtype, int W, int H, const tsplat_render_params &par, float *out_feat,
@@ -361,7 +386,9 @@ static tsplat_status render_tail(tsplat_ctx *c, int64_t n_cap, const uint32_t *n
     const int tiles_x = (W + TILE - 1) / TILE, tiles_y = (H + TILE - 1) / TILE, n_tiles = tiles_x * tiles_y;
     const bool async_mode = (par.flags & TSPLAT_RENDER_ASYNC) != 0;
     const bool save = (par.flags & TSPLAT_RENDER_SAVE) != 0;
+    const bool prof = (par.flags & TSPLAT_RENDER_PROFILE) != 0;
     uint32_t *sm = c->small.as<uint32_t>();
+    TRY(mark(c, prof, 1, s));
 
     // depth order of the Gaussians (radix passes only over the differing bytes)
     launch_depth_npass(sm + SM_KMIN, sm + SM_NPASS, s);
@@ -380,6 +407,7 @@ static tsplat_status render_tail(tsplat_ctx *c, int64_t n_cap, const uint32_t *n
     ds.totals = sm + SM_TOTALS;
     ds.nblocks = (int)((std::max<int64_t>(n_cap, 1) + RS_TILE - 1) / RS_TILE);
     launch_radix_sort(ds, 4, s);
+    TRY(mark(c, prof, 2, s));
 
     // scan of tiles per Gaussian in depth order and pair emission
     EmitArgs em;
@@ -411,6 +439,7 @@ static tsplat_status render_tail(tsplat_ctx *c, int64_t n_cap, const uint32_t *n
     em.pair_id = c->pv1.as<uint32_t>();
     em.p_cap = c->p_cap;
     launch_emit_write(em, s);
+    TRY(mark(c, prof, 3, s));
 
     // stable sort of the pairs on the tile digits; the emit buffer is the
     // odd ping-pong buffer, so two passes end where they started
@@ -433,10 +462,12 @@ static tsplat_status render_tail(tsplat_ctx *c, int64_t n_cap, const uint32_t *n
     // effective pair count: P, or 0 when the pairs did not fit
     launch_pairs_effective(sm + SM_P, (uint32_t)std::min<int64_t>(c->p_cap, 0xffffffffll), sm + SM_PEFF, s);
     if (tpass > 0) launch_radix_sort(ts, tpass, s);
+    TRY(mark(c, prof, 4, s));
     const uint32_t *tiles_sorted = tpass == 0 ? ts.keys_in : ts.keys[(tpass - 1) & 1];
     const uint32_t *ids_sorted = tpass == 0 ? ts.vals_in : ts.vals[(tpass - 1) & 1];
     launch_ranges(tiles_sorted, sm + SM_PEFF, c->p_cap, c->ranges.as<uint2>(), n_tiles, s);
     TRY(check_launch("render: bins"));
+    TRY(mark(c, prof, 5, s));
 
     CompositeArgs ca;
     memset(&ca, 0, sizeof(ca));
@@ -453,12 +484,15 @@ static tsplat_status render_tail(tsplat_ctx *c, int64_t n_cap, const uint32_t *n
     ca.alpha_max = par.alpha_max;
     ca.alpha_min = par.alpha_min;
     ca.t_min = par.t_min;
+    ca.log2_alpha_min = (float)log2((double)par.alpha_min);
+    ca.status = sm + SM_STATUS;
     ca.out_feat = out_feat;
     ca.out_alpha = out_alpha;
     ca.out_T = save ? c->tfinal.as<float>() : nullptr;
     ca.out_last = save ? c->last.as<uint32_t>() : nullptr;
     launch_composite(ca, s);
     TRY(check_launch("render: composite"));
+    TRY(mark(c, prof, 6, s));
 
     c->stream = s;
     c->n_cap = n_cap;
@@ -506,6 +540,7 @@ tsplat_status tsplat_render(const tsplat_gaussians *g, const tsplat_camera *cam,
         TRY(ensure_pix(ctx, W, H, tiles_x * tiles_y, (params->flags & TSPLAT_RENDER_SAVE) != 0, s));
     }
     init_small(ctx, s);
+    TRY(mark(ctx, (params->flags & TSPLAT_RENDER_PROFILE) != 0, 0, s));
     ProjectOut o;
     o.hdr = ctx->hdr.as<Header>();
     o.rect = ctx->rect.as<uint2>();
@@ -543,6 +578,7 @@ tsplat_status tsplat_rasterize(int64_t n, const float *mean2d, const float *coni
     }
     init_small(ctx, s);
     launch_fill_u32(small_ptr(ctx, SM_N), (uint32_t)n, 1, s);
+    TRY(mark(ctx, (params->flags & TSPLAT_RENDER_PROFILE) != 0, 0, s));
     ProjectOut o;
     o.hdr = ctx->hdr.as<Header>();
     o.rect = ctx->rect.as<uint2>();
@@ -576,6 +612,7 @@ tsplat_status tsplat_backward(tsplat_ctx *c, const float *dL_dfeat, const float 
     b.W = c->W; b.H = c->H; b.tiles_x = c->tiles_x; b.tiles_y = c->tiles_y;
     b.alpha_max = c->alpha_max;
     b.alpha_min = c->alpha_min;
+    b.log2_alpha_min = (float)log2((double)c->alpha_min);
     b.T_final = c->tfinal.as<float>();
     b.last = c->last.as<uint32_t>();
     b.dF = dL_dfeat;
@@ -587,6 +624,29 @@ tsplat_status tsplat_backward(tsplat_ctx *c, const float *dL_dfeat, const float 
     launch_backward(b, s);
     return check_launch("backward");
 }
+
+tsplat_status tsplat_ctx_timings(tsplat_ctx *c, float *ms, int32_t capacity, int32_t *n_out) {
+    if (!c || !ms) return fail(TSPLAT_ERR_INVALID_ARG, "ctx_timings: NULL argument");
+    if (c->n_prof == 0) return fail(TSPLAT_ERR_INVALID_ARG, "ctx_timings: no render with TSPLAT_RENDER_PROFILE since the last call");
+    const int n = std::min<int>(capacity, tsplat_ctx::N_EV - 1);
+    const int64_t k0 = std::max<int64_t>(0, c->n_prof - tsplat_ctx::RING);
+    TRY_CUDA(cudaEventSynchronize(c->ev[(c->n_prof - 1) % tsplat_ctx::RING][tsplat_ctx::N_EV - 1]));
+    for (int i = 0; i < n; ++i) ms[i] = 0.0f;
+    for (int64_t k = k0; k < c->n_prof; ++k) {
+        cudaEvent_t *row = c->ev[k % tsplat_ctx::RING];
+        for (int i = 0; i < n; ++i) {
+            float t = 0.0f;
+            TRY_CUDA(cudaEventElapsedTime(&t, row[i], row[i + 1]));
+            ms[i] += t;
+        }
+    }
+    for (int i = 0; i < n; ++i) ms[i] /= (float)(c->n_prof - k0);
+    c->n_prof = 0;
+    if (n_out) *n_out = n;
+    return TSPLAT_OK;
+}
+
+uint64_t tsplat_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 tsplat_status tsplat_ctx_status(tsplat_ctx *c) {
     if (!c) return fail(TSPLAT_ERR_INVALID_ARG, "ctx_status: ctx is NULL");

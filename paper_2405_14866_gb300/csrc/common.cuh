@@ -16,8 +16,9 @@ constexpr uint32_t CULLED_KEY = 0xFFFFFFFFu;
 // Projected record of one Gaussian in the target view, 32 bytes (one DRAM
 // sector), read by the compositing once per (Gaussian, tile) pair:
 //   h0 = (mean2d.x, mean2d.y, conic a, conic b)
-//   h1 = (conic c, opacity, ex, ey) with (ex, ey) the half extents of the
-//        box that bounds every pixel where alpha can reach alpha_min.
+//   h1 = (conic c, log2(opacity), ex, ey) with (ex, ey) the half extents of
+//        the box that bounds every pixel where alpha can reach alpha_min.
+// The compositing evaluates alpha = min(alpha_max, 2^(q log2(e) + log2(o))).
 struct __align__(16) Header {
     float4 h0;
     float4 h1;

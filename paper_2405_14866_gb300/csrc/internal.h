@@ -142,6 +142,8 @@ struct CompositeArgs {
     int feat_dtype;
     int W, H, tiles_x, tiles_y;
     float alpha_max, alpha_min, t_min;
+    float log2_alpha_min;  // blend test: log2(o) + q log2(e) >= log2(alpha_min)
+    uint32_t *status;      // TSPLAT_ERR_TIMEOUT if a bounded wait expired
     float *out_feat;
     float *out_alpha;
     float *out_T;        // may be NULL
@@ -159,6 +161,7 @@ struct BackwardArgs {
     int feat_dtype;
     int W, H, tiles_x, tiles_y;
     float alpha_max, alpha_min;
+    float log2_alpha_min;
     const float *T_final;
     const uint32_t *last;
     const float *dF;
@@ -169,6 +172,9 @@ struct BackwardArgs {
     float *d_feat;
 };
 void launch_backward(const BackwardArgs &a, cudaStream_t s);
+
+// every launcher reports its launches here (tsplat_launch_count)
+void note_launches(int n);
 
 // small utilities
 void launch_fill_u32(uint32_t *p, uint32_t v, int64_t n, cudaStream_t s);

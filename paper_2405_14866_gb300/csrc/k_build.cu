@@ -57,11 +57,19 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *sw, ui
     return pre + x - v;
 }
 
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Pixels of block b: [b * 4096, (b + 1) * 4096), visited in 16 rounds of 256
+// consecutive pixels (thread t takes pixel round * 256 + t).
 __global__ __launch_bounds__(BT) void k_build_count(BuildArgs a) {
     __shared__ uint32_t sw[BT / 32];
-    const int64_t base = (int64_t)blockIdx.x * BUILD_PIX_PER_BLOCK + (int64_t)threadIdx.x * BI;
+    const int64_t base = (int64_t)blockIdx.x * BUILD_PIX_PER_BLOCK + threadIdx.x;
     uint32_t c = 0;
-    for (int i = 0; i < BI; ++i) c += is_fg(a, base + i) ? 1u : 0u;
+    for (int r = 0; r < BI; ++r) c += is_fg(a, base + (int64_t)r * BT) ? 1u : 0u;
     uint32_t tot;
     block_excl_scan<BT / 32>(c, sw, tot);
     if (threadIdx.x == 0) a.blk_cnt[blockIdx.x] = tot;
@@ -154,24 +162,78 @@ __device__ __forceinline__ void lift_one(const BuildArgs &a, const ViewDesc &vd,
     a.xyzo[id] = make_float4(m[0], m[1], m[2], vd.opacity[p]);
     a.cova[id] = make_float4(cv(0, 0), cv(0, 1), cv(0, 2), cv(1, 1));
     a.covb[id] = make_float2(cv(1, 2), cv(2, 2));
-    copy_feat(vd.feat, vd.feat_dtype, p, a.feat, a.out_dtype, id, a.C);
+}
+
+// Copy `rows` feature rows (Gaussian ids first .. first + rows - 1, source
+// pixels s_src[]) cooperatively: consecutive threads take consecutive 4-wide
+// chunks, so both the reads and the writes are coalesced.
+__device__ __forceinline__ void copy_rows(const BuildArgs &a, const int64_t *s_src, int rows, int64_t first) {
+    const int C = a.C;
+    const bool vec = (C & 3) == 0;
+    const int cpr = vec ? C / 4 : C;  // chunks per row
+    for (int ch = threadIdx.x; ch < rows * cpr; ch += BT) {
+        const int row = ch / cpr, part = ch - row * cpr;
+        const int64_t g = s_src[row];
+        const ViewDesc &vd = a.views[view_of(a, g)];
+        const int64_t p = g - vd.pix_off, id = first + row;
+        if (vec) {
+            const int c0 = part * 4;
+            float v[4];
+            if (vd.feat_dtype == TSPLAT_F32) {
+                const float4 x = *reinterpret_cast<const float4 *>((const float *)vd.feat + p * C + c0);
+                v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+            } else {
+                const uint2 x = *reinterpret_cast<const uint2 *>((const __nv_bfloat16 *)vd.feat + p * C + c0);
+                v[0] = __uint_as_float(x.x << 16); v[1] = __uint_as_float(x.x & 0xffff0000u);
+                v[2] = __uint_as_float(x.y << 16); v[3] = __uint_as_float(x.y & 0xffff0000u);
+            }
+            if (a.out_dtype == TSPLAT_F32) {
+                *reinterpret_cast<float4 *>((float *)a.feat + id * C + c0) = make_float4(v[0], v[1], v[2], v[3]);
+            } else {
+                __nv_bfloat162 lo = __floats2bfloat162_rn(v[0], v[1]), hi = __floats2bfloat162_rn(v[2], v[3]);
+                uint2 o;
+                o.x = *reinterpret_cast<uint32_t *>(&lo);
+                o.y = *reinterpret_cast<uint32_t *>(&hi);
+                *reinterpret_cast<uint2 *>((__nv_bfloat16 *)a.feat + id * C + c0) = o;
+            }
+        } else {
+            float v = vd.feat_dtype == TSPLAT_F32 ? ((const float *)vd.feat)[p * C + part]
+                                                  : __bfloat162float(((const __nv_bfloat16 *)vd.feat)[p * C + part]);
+            if (a.out_dtype == TSPLAT_F32) ((float *)a.feat)[id * C + part] = v;
+            else ((__nv_bfloat16 *)a.feat)[id * C + part] = __float2bfloat16_rn(v);
+        }
+    }
 }
 
 __global__ __launch_bounds__(BT) void k_build_lift(BuildArgs a) {
-    __shared__ uint32_t sw[BT / 32];
-    const int64_t base = (int64_t)blockIdx.x * BUILD_PIX_PER_BLOCK + (int64_t)threadIdx.x * BI;
-    uint32_t flags = 0, c = 0;
+    __shared__ uint32_t s_wn[BT / 32];
+    __shared__ int64_t s_src[BT];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t base = (int64_t)blockIdx.x * BUILD_PIX_PER_BLOCK;
+    int64_t running = a.blk_off[blockIdx.x];
+    for (int r = 0; r < BI; ++r) {
+        const int64_t g = base + (int64_t)r * BT + threadIdx.x;
+        const bool fg = is_fg(a, g);
+        const uint32_t bal = __ballot_sync(FULL, fg);
+        if (lane == 0) s_wn[warp] = __popc(bal);
+        __syncthreads();
+        uint32_t woff = 0, tot = 0;
 #pragma unroll
-    for (int i = 0; i < BI; ++i)
-        if (is_fg(a, base + i)) { flags |= 1u << i; ++c; }
-    uint32_t tot;
-    int64_t id = (int64_t)a.blk_off[blockIdx.x] + block_excl_scan<BT / 32>(c, sw, tot);
-    for (int i = 0; i < BI; ++i) {
-        if (!(flags & (1u << i))) continue;
-        const int64_t g = base + i;
-        const ViewDesc &vd = a.views[view_of(a, g)];
-        lift_one(a, vd, g - vd.pix_off, id);
-        ++id;
+        for (int w = 0; w < BT / 32; ++w) {
+            const uint32_t c = s_wn[w];
+            woff += w < warp ? c : 0u;
+            tot += c;
+        }
+        const uint32_t local = woff + __popc(bal & lanemask_lt());
+        if (fg) {
+            const ViewDesc &vd = a.views[view_of(a, g)];
+            lift_one(a, vd, g - vd.pix_off, running + local);
+            s_src[local] = g;
+        }
+        __syncthreads();
+        copy_rows(a, s_src, (int)tot, running);
+        running += tot;
+        __syncthreads();
     }
 }
 
@@ -212,8 +274,11 @@ void launch_build(const BuildArgs &a, cudaStream_t s) {
         return;
     }
     k_build_count<<<a.nblocks, BT, 0, s>>>(a);
+    note_launches(1);
     k_build_scan<<<1, 1024, 0, s>>>(a);
+    note_launches(1);
     k_build_lift<<<a.nblocks, BT, 0, s>>>(a);
+    note_launches(1);
 }
 
 void launch_gaussians_set(int64_t n, const float *mean, const float *cov, const float *opac, const void *feat,
@@ -222,6 +287,7 @@ void launch_gaussians_set(int64_t n, const float *mean, const float *cov, const 
     const int64_t blocks = n > 0 ? (n + 255) / 256 : 1;
     k_gaussians_set<<<(unsigned)blocks, 256, 0, s>>>((uint64_t)n, mean, cov, opac, feat, feat_dtype_in, C,
                                                      out_dtype, xyzo, cova, covb, feat_out, n_dev);
+    note_launches(1);
 }
 
 void launch_gaussians_get(const uint32_t *n_dev, int64_t cap, int C, int dtype, const float4 *xyzo,
@@ -230,6 +296,7 @@ void launch_gaussians_get(const uint32_t *n_dev, int64_t cap, int C, int dtype, 
     if (cap <= 0) return;
     k_gaussians_get<<<(unsigned)((cap + 255) / 256), 256, 0, s>>>(n_dev, C, dtype, xyzo, cova, covb, feat_in,
                                                                   mean, cov, opac, feat_out);
+    note_launches(1);
 }
 
 }  // namespace tsp

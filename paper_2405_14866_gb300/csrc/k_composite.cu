@@ -3,46 +3,335 @@
 // splats latent features instead of colours and is differentiated end to
 // end).
 //
-// One CTA of 256 threads per tile; warp w owns an 8x4 pixel block.  The
-// tile's depth-ordered Gaussians are staged 256 at a time into shared
-// memory (32-byte projected record + feature row).  Each warp first tests
-// the 32-wide chunks of the batch against its block with the Gaussians'
-// alpha_min boxes (exact: outside its box a Gaussian's alpha is provably
-// below alpha_min, so skipping it is what the per-pixel test would do) and
-// iterates only over the survivors, in order.  A warp stops computing when
-// all its pixels are saturated; the CTA stops staging when all warps have.
-// No tensor cores: blending is a per-pixel sequential recurrence, not a
-// dense contraction.
+// Forward, one CTA per tile: 8 consumer warps, each owning an 8x4 pixel
+// block, and 1 producer warp.  The producer streams the tile's depth-ordered
+// Gaussians through a ring of shared-memory slots (64 Gaussians each),
+// gathering each Gaussian's 32-byte projected record and feature row with
+// 16-byte asynchronous copies (cp.async) whose completion arrives on the
+// slot's mbarrier; consumer warps advance at their own pace and release
+// slots, so no CTA-wide barrier couples them.  (One-bulk-copy-per-record
+// staging through the TMA engine measured slower for this gather.)
+//
+// Per slot a warp tests the 64 records against its block with each
+// Gaussian's alpha_min box (exact: outside it alpha < alpha_min, so skipping
+// is what the per-pixel test would do) and walks the survivors in order.
+// Each lane runs the per-pixel recurrence (alpha, T, stop) and produces the
+// blending weight w = alpha T; groups of 16 weights are applied to the
+// features as a warp-level bf16 tensor-core product
+//     F(32 px x C) += W(32 px x 16) * Feat(16 x C),
+// with W split into bf16 hi + lo parts (and FP32 features likewise), so the
+// product keeps ~2^-16 relative precision with FP32 accumulation.  A warp
+// stops when all its pixels are saturated; the producer stops when all
+// warps have.
 #include <algorithm>
 
 #include "common.cuh"
 #include "internal.h"
+#include "ptx.cuh"
 
 namespace tsp {
 
 namespace {
 
-constexpr int CT = 256;  // threads per CTA = pixels per tile
 constexpr uint32_t FULL = 0xffffffffu;
+constexpr float LOG2E = 1.4426950408889634f;
+
+// ------------------------------------------------------------------ forward
+constexpr int NCW = 8;               // consumer warps
+constexpr int NTHR = (NCW + 1) * 32; // + 1 producer warp
+constexpr int SB = 64;               // Gaussians per ring slot
+constexpr int WROW = 24;             // bf16 per W row (16 used; 48-byte stride avoids bank conflicts)
+
+template <int CP>
+struct Ring {
+    static constexpr int N = CP <= 32 ? 8 : 4;  // ring slots (deeper where shared memory allows)
+};
+
+template <int CP, bool F32F>
+struct CompSmem {
+    static constexpr int RING = Ring<CP>::N;
+    Header hdr[RING][SB];
+    __nv_bfloat16 fhi[RING][SB][CP];
+    __nv_bfloat16 flo[F32F ? RING : 1][F32F ? SB : 1][CP];
+    __nv_bfloat16 whi[NCW][32][WROW];
+    __nv_bfloat16 wlo[NCW][32][WROW];
+    __nv_bfloat16 zero[CP];
+    uint64_t full[RING];
+    uint64_t empty[RING];
+    uint32_t cnt[RING];
+    uint32_t done_mask;
+};
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+// Producer side of one Gaussian of a slot: its record (2 x 16 B) and, for
+// BF16 rows of exactly CP channels, its feature row by 16-byte asynchronous
+// copies; other feature layouts are loaded, split (FP32 -> bf16 hi + lo)
+// and zero-padded by the producer lane itself.
+template <int CP, bool F32F>
+__device__ __forceinline__ void produce_one(CompSmem<CP, F32F> &S, const CompositeArgs &a, int slot, int k,
+                                            uint32_t id) {
+    const uint4 *hs = reinterpret_cast<const uint4 *>(a.hdr + id);
+    cp_async16(&S.hdr[slot][k], hs);
+    cp_async16(reinterpret_cast<char *>(&S.hdr[slot][k]) + 16, hs + 1);
+    if (!F32F && a.C == CP) {
+        const uint4 *fs = reinterpret_cast<const uint4 *>(reinterpret_cast<const __nv_bfloat16 *>(a.feat) + (size_t)id * CP);
+#pragma unroll
+        for (int c = 0; c < CP / 8; ++c) cp_async16(&S.fhi[slot][k][8 * c], fs + c);
+    } else if (F32F) {
+        const float *src = reinterpret_cast<const float *>(a.feat) + (size_t)id * a.C;
+#pragma unroll 4
+        for (int c = 0; c < CP; c += 2) {
+            const float v0 = c < a.C ? __ldg(src + c) : 0.0f;
+            const float v1 = c + 1 < a.C ? __ldg(src + c + 1) : 0.0f;
+            const uint32_t hi = pack_bf16x2(v0, v1);
+            const uint32_t lo = pack_bf16x2(v0 - bf16_lo_f(hi), v1 - bf16_hi_f(hi));
+            *reinterpret_cast<uint32_t *>(&S.fhi[slot][k][c]) = hi;
+            *reinterpret_cast<uint32_t *>(&S.flo[F32F ? slot : 0][F32F ? k : 0][c]) = lo;
+        }
+    } else {
+        const __nv_bfloat16 *src = reinterpret_cast<const __nv_bfloat16 *>(a.feat) + (size_t)id * a.C;
+        for (int c = 0; c < CP; ++c) S.fhi[slot][k][c] = c < a.C ? src[c] : __float2bfloat16_rn(0.0f);
+    }
+}
+
+// The full barrier of a slot expects one regular arrival (lane 0, after the
+// slot's count is written) plus, per producer lane, the asynchronous arrival
+// that fires once that lane's copies have landed.  The ids of the next slot
+// are loaded before the current slot's copies are issued.
+template <int CP, bool F32F>
+__device__ void producer(CompSmem<CP, F32F> &S, const CompositeArgs &a, uint32_t first, int n, int lane) {
+    constexpr int RING = CompSmem<CP, F32F>::RING;
+    const int nbatch = (n + SB - 1) / SB;
+    bool timed_out = false;
+    uint32_t nid0 = lane < n ? a.ids[first + lane] : 0u;
+    uint32_t nid1 = lane + 32 < n ? a.ids[first + lane + 32] : 0u;
+    for (int i = 0; i <= nbatch; ++i) {
+        const int slot = i % RING;
+        if (!mbar_wait(&S.empty[slot], ((i / RING) & 1) ^ 1, a.status)) {
+            timed_out = true;
+            break;
+        }
+        const bool all_done = *reinterpret_cast<volatile uint32_t *>(&S.done_mask) == (1u << NCW) - 1;
+        const bool end = i == nbatch || all_done;  // the end marker is a slot with count 0
+        const int base = i * SB, cnt = end ? 0 : min(SB, n - base);
+        if (!end) {
+            const uint32_t id0 = nid0, id1 = nid1;
+            const int nbase = base + SB;
+            nid0 = nbase + lane < n ? a.ids[first + nbase + lane] : 0u;
+            nid1 = nbase + lane + 32 < n ? a.ids[first + nbase + lane + 32] : 0u;
+            if (lane < cnt) produce_one<CP, F32F>(S, a, slot, lane, id0);
+            if (lane + 32 < cnt) produce_one<CP, F32F>(S, a, slot, lane + 32, id1);
+        }
+        // every lane, every slot (the end marker too): counts against the
+        // barrier's expected arrivals (.noinc) and fires once this lane's
+        // copies have landed (immediately when it issued none)
+        asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&S.full[slot])) : "memory");
+        __syncwarp();
+        if (lane == 0) {
+            S.cnt[slot] = cnt;
+            mbar_arrive(&S.full[slot]);
+        }
+        if (end) break;
+    }
+    if (timed_out) {
+        set_status(a.status, TSPLAT_ERR_TIMEOUT);
+        // let the copies already issued land before the CTA can exit
+        asm volatile("cp.async.wait_all;" ::: "memory");
+    }
+}
+
+__device__ __forceinline__ bool box_hit(const Header &h, float bx0, float bx1, float by0, float by1) {
+    return (h.h0.x + h.h1.z >= bx0) && (h.h0.x - h.h1.z <= bx1) && (h.h0.y + h.h1.w >= by0) &&
+           (h.h0.y - h.h1.w <= by1);
+}
+
+template <int CP, bool F32F>
+__global__ __launch_bounds__(NTHR, 2) void k_composite(CompositeArgs a) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    CompSmem<CP, F32F> &S = *reinterpret_cast<CompSmem<CP, F32F> *>(smem_raw);
+    constexpr int NT8 = CP / 8;  // n8 tiles of the MMA
+    constexpr int RING = CompSmem<CP, F32F>::RING;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tile = blockIdx.x;
+    const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+    const uint2 rg = a.ranges[tile];
+    const int n = (int)(rg.y - rg.x);
+
+    if (tid == 0) {
+        for (int r = 0; r < RING; ++r) {
+            mbar_init(&S.full[r], 1 + 32);  // lane 0's arrival + one asynchronous arrival per producer lane
+            mbar_init(&S.empty[r], NCW);
+        }
+        S.done_mask = 0;
+        mbar_init_fence();
+    }
+    for (int c = tid; c < CP; c += NTHR) S.zero[c] = __float2bfloat16_rn(0.0f);
+    __syncthreads();
+
+    if (warp == NCW) {
+        producer<CP, F32F>(S, a, rg.x, n, lane);
+        return;
+    }
+
+    // ---------------------------------------------------------- consumers
+    const int bx0 = tx * TILE + (warp & 1) * 8, by0 = ty * TILE + (warp >> 1) * 4;
+    const int px = bx0 + (lane & 7), py = by0 + (lane >> 3);
+    const bool inside = px < a.W && py < a.H;
+    const float fpx = (float)px, fpy = (float)py;
+    const float fbx0 = (float)bx0, fbx1 = (float)(bx0 + 7), fby0 = (float)by0, fby1 = (float)(by0 + 3);
+    const float amax = a.alpha_max, l2min = a.log2_alpha_min, tmin = a.t_min;
+
+    float acc[2][NT8][4];
+#pragma unroll
+    for (int m = 0; m < 2; ++m)
+#pragma unroll
+        for (int t = 0; t < NT8; ++t)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[m][t][e] = 0.0f;
+    float T = 1.0f;
+    uint32_t last = 0;
+    bool done = !inside;
+    bool wdone = __all_sync(FULL, done);
+    if (wdone && lane == 0) atomicOr(&S.done_mask, 1u << warp);
+
+    // ldmatrix address pattern: lane supplies row (lane & 7) of matrix lane / 8
+    const int kl = ((lane >> 3) & 1) * 8 + (lane & 7);  // group entry whose B row this lane addresses
+    const int arow = kl, acol = (lane >> 4) * 8, bcol = (lane >> 4) * 8;
+
+    for (int i = 0;; ++i) {
+        const int slot = i % RING;
+        if (!mbar_wait(&S.full[slot], (i / RING) & 1, a.status)) {
+            set_status(a.status, TSPLAT_ERR_TIMEOUT);
+            break;
+        }
+        const int cnt = (int)S.cnt[slot];
+        if (cnt == 0) break;
+        if (!wdone) {
+            const int base = i * SB;
+            const bool r0 = lane < cnt && box_hit(S.hdr[slot][lane], fbx0, fbx1, fby0, fby1);
+            const bool r1 = lane + 32 < cnt && box_hit(S.hdr[slot][lane + 32], fbx0, fbx1, fby0, fby1);
+            uint32_t m0 = __ballot_sync(FULL, r0);
+            uint32_t m1 = __ballot_sync(FULL, r1);
+            while ((m0 | m1) && !wdone) {
+                uint32_t wh[8], wl[8];
+                int my_j = -1;  // slot index of group entry kl (B-operand row address)
+#pragma unroll
+                for (int g = 0; g < 16; g += 2) {
+                    float w2[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        // next survivor in order (warp-uniform), -1 when the group runs out
+                        const int j = m0 ? __ffs(m0) - 1 : (m1 ? 31 + __ffs(m1) : -1);
+                        if (m0) m0 &= m0 - 1;
+                        else m1 &= m1 - 1;
+                        if (kl == g + h) my_j = j;
+                        // straight-line recurrence: only T / done / last carry a dependency
+                        const int jj = j < 0 ? 0 : j;
+                        const float4 h0 = S.hdr[slot][jj].h0;
+                        const float4 h1 = S.hdr[slot][jj].h1;
+                        const float q = gauss_q(fpx - h0.x, fpy - h0.y, h0.z, h0.w, h1.x);
+                        const float e2 = fmaf(q, LOG2E, h1.y);
+                        const float al = fminf(amax, ex2(e2));
+                        const bool ok = (j >= 0) & !done & (q <= 0.0f) & (e2 >= l2min);
+                        const float Tn = T * (1.0f - al);
+                        const bool stop = ok & (Tn < tmin);
+                        const bool blend = ok & !stop;
+                        w2[h] = blend ? al * T : 0.0f;
+                        T = blend ? Tn : T;
+                        last = blend ? (uint32_t)(base + j + 1) : last;
+                        done = done | stop;
+                    }
+                    wh[g / 2] = pack_bf16x2(w2[0], w2[1]);
+                    wl[g / 2] = pack_bf16x2(w2[0] - bf16_lo_f(wh[g / 2]), w2[1] - bf16_hi_f(wh[g / 2]));
+                }
+                // this lane's row of W (pixel = lane), hi and lo parts
+                uint4 *rh = reinterpret_cast<uint4 *>(&S.whi[warp][lane][0]);
+                uint4 *rl = reinterpret_cast<uint4 *>(&S.wlo[warp][lane][0]);
+                rh[0] = make_uint4(wh[0], wh[1], wh[2], wh[3]);
+                rh[1] = make_uint4(wh[4], wh[5], wh[6], wh[7]);
+                rl[0] = make_uint4(wl[0], wl[1], wl[2], wl[3]);
+                rl[1] = make_uint4(wl[4], wl[5], wl[6], wl[7]);
+                __syncwarp();
+                uint32_t ah[2][4], aw[2][4];
+#pragma unroll
+                for (int m = 0; m < 2; ++m) {
+                    ldsm_x4(ah[m][0], ah[m][1], ah[m][2], ah[m][3], &S.whi[warp][m * 16 + arow][acol]);
+                    ldsm_x4(aw[m][0], aw[m][1], aw[m][2], aw[m][3], &S.wlo[warp][m * 16 + arow][acol]);
+                }
+                const __nv_bfloat16 *browh = my_j >= 0 ? &S.fhi[slot][my_j][0] : &S.zero[0];
+#pragma unroll
+                for (int p = 0; p < NT8 / 2; ++p) {
+                    uint32_t b[4];
+                    ldsm_x4_t(b[0], b[1], b[2], b[3], browh + p * 16 + bcol);
+#pragma unroll
+                    for (int m = 0; m < 2; ++m) {
+                        mma_bf16(acc[m][2 * p], ah[m][0], ah[m][1], ah[m][2], ah[m][3], b[0], b[1]);
+                        mma_bf16(acc[m][2 * p], aw[m][0], aw[m][1], aw[m][2], aw[m][3], b[0], b[1]);
+                        mma_bf16(acc[m][2 * p + 1], ah[m][0], ah[m][1], ah[m][2], ah[m][3], b[2], b[3]);
+                        mma_bf16(acc[m][2 * p + 1], aw[m][0], aw[m][1], aw[m][2], aw[m][3], b[2], b[3]);
+                    }
+                    if (F32F) {
+                        const __nv_bfloat16 *browl =
+                            my_j >= 0 ? &S.flo[F32F ? slot : 0][F32F ? my_j : 0][0] : &S.zero[0];
+                        ldsm_x4_t(b[0], b[1], b[2], b[3], browl + p * 16 + bcol);
+#pragma unroll
+                        for (int m = 0; m < 2; ++m) {
+                            mma_bf16(acc[m][2 * p], ah[m][0], ah[m][1], ah[m][2], ah[m][3], b[0], b[1]);
+                            mma_bf16(acc[m][2 * p], aw[m][0], aw[m][1], aw[m][2], aw[m][3], b[0], b[1]);
+                            mma_bf16(acc[m][2 * p + 1], ah[m][0], ah[m][1], ah[m][2], ah[m][3], b[2], b[3]);
+                            mma_bf16(acc[m][2 * p + 1], aw[m][0], aw[m][1], aw[m][2], aw[m][3], b[2], b[3]);
+                        }
+                    }
+                }
+                __syncwarp();
+                wdone = __all_sync(FULL, done);
+            }
+            if (wdone && lane == 0) atomicOr(&S.done_mask, 1u << warp);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&S.empty[slot]);
+    }
+
+    // outputs: the accumulator of lane l holds pixels l/4 (+8, +16, +24) and
+    // channels 8t + 2(l%4) (+1)
+    const size_t HW = (size_t)a.W * a.H;
+#pragma unroll
+    for (int m = 0; m < 2; ++m)
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+            const int p = m * 16 + hh * 8 + (lane >> 2);
+            const int x = bx0 + (p & 7), y = by0 + (p >> 3);
+            if (x < a.W && y < a.H) {
+                float *dst = a.out_feat + (size_t)y * a.W + x;
+#pragma unroll
+                for (int t = 0; t < NT8; ++t) {
+                    const int c = t * 8 + 2 * (lane & 3);
+                    if (c < a.C) dst[c * HW] = acc[m][t][2 * hh];
+                    if (c + 1 < a.C) dst[(c + 1) * HW] = acc[m][t][2 * hh + 1];
+                }
+            }
+        }
+    if (inside) {
+        const size_t pix = (size_t)py * a.W + px;
+        if (a.out_alpha) a.out_alpha[pix] = 1.0f - T;
+        if (a.out_T) a.out_T[pix] = T;
+        if (a.out_last) a.out_last[pix] = last;
+    }
+}
+
+// ----------------------------------------------------------------- backward
+constexpr int CT = 256;
 
 template <typename FT>
 struct FeatIO;
 
 template <>
 struct FeatIO<float> {
-    static constexpr int VEC = 4;  // elements per 16-byte vector
-    template <int CP>
-    __device__ static __forceinline__ void axpy(float (&F)[CP], const float *row, float w) {
-        const float4 *r4 = reinterpret_cast<const float4 *>(row);
-#pragma unroll
-        for (int i = 0; i < CP / 4; ++i) {
-            const float4 v = r4[i];
-            F[4 * i] = fmaf(v.x, w, F[4 * i]);
-            F[4 * i + 1] = fmaf(v.y, w, F[4 * i + 1]);
-            F[4 * i + 2] = fmaf(v.z, w, F[4 * i + 2]);
-            F[4 * i + 3] = fmaf(v.w, w, F[4 * i + 3]);
-        }
-    }
+    static constexpr int VEC = 4;
     template <int CP>
     __device__ static __forceinline__ void load(float (&f)[CP], const float *row) {
         const float4 *r4 = reinterpret_cast<const float4 *>(row);
@@ -54,44 +343,23 @@ struct FeatIO<float> {
     }
 };
 
-__device__ __forceinline__ float bf_lo(uint32_t u) { return __uint_as_float(u << 16); }
-__device__ __forceinline__ float bf_hi(uint32_t u) { return __uint_as_float(u & 0xffff0000u); }
-
 template <>
 struct FeatIO<__nv_bfloat16> {
     static constexpr int VEC = 8;
-    template <int CP>
-    __device__ static __forceinline__ void axpy(float (&F)[CP], const __nv_bfloat16 *row, float w) {
-        const uint4 *r4 = reinterpret_cast<const uint4 *>(row);
-#pragma unroll
-        for (int i = 0; i < CP / 8; ++i) {
-            const uint4 v = r4[i];
-            F[8 * i + 0] = fmaf(bf_lo(v.x), w, F[8 * i + 0]);
-            F[8 * i + 1] = fmaf(bf_hi(v.x), w, F[8 * i + 1]);
-            F[8 * i + 2] = fmaf(bf_lo(v.y), w, F[8 * i + 2]);
-            F[8 * i + 3] = fmaf(bf_hi(v.y), w, F[8 * i + 3]);
-            F[8 * i + 4] = fmaf(bf_lo(v.z), w, F[8 * i + 4]);
-            F[8 * i + 5] = fmaf(bf_hi(v.z), w, F[8 * i + 5]);
-            F[8 * i + 6] = fmaf(bf_lo(v.w), w, F[8 * i + 6]);
-            F[8 * i + 7] = fmaf(bf_hi(v.w), w, F[8 * i + 7]);
-        }
-    }
     template <int CP>
     __device__ static __forceinline__ void load(float (&f)[CP], const __nv_bfloat16 *row) {
         const uint4 *r4 = reinterpret_cast<const uint4 *>(row);
 #pragma unroll
         for (int i = 0; i < CP / 8; ++i) {
             const uint4 v = r4[i];
-            f[8 * i + 0] = bf_lo(v.x); f[8 * i + 1] = bf_hi(v.x);
-            f[8 * i + 2] = bf_lo(v.y); f[8 * i + 3] = bf_hi(v.y);
-            f[8 * i + 4] = bf_lo(v.z); f[8 * i + 5] = bf_hi(v.z);
-            f[8 * i + 6] = bf_lo(v.w); f[8 * i + 7] = bf_hi(v.w);
+            f[8 * i + 0] = bf16_lo_f(v.x); f[8 * i + 1] = bf16_hi_f(v.x);
+            f[8 * i + 2] = bf16_lo_f(v.y); f[8 * i + 3] = bf16_hi_f(v.y);
+            f[8 * i + 4] = bf16_lo_f(v.z); f[8 * i + 5] = bf16_hi_f(v.z);
+            f[8 * i + 6] = bf16_lo_f(v.w); f[8 * i + 7] = bf16_hi_f(v.w);
         }
     }
 };
 
-// Stage record + feature row of Gaussian `id` into slot `slot` (C real
-// channels; the padding channels of the shared rows stay zero).
 template <int CP, typename FT>
 __device__ __forceinline__ void stage(const Header *__restrict__ hdr, const FT *__restrict__ feat, int C,
                                       bool vec_ok, uint32_t id, Header *s_hdr, FT *s_feat, int slot) {
@@ -108,87 +376,6 @@ __device__ __forceinline__ void stage(const Header *__restrict__ hdr, const FT *
     }
 }
 
-template <int CP, typename FT>
-__global__ __launch_bounds__(CT, 2) void k_composite(CompositeArgs a) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    Header *s_hdr = reinterpret_cast<Header *>(smem);
-    FT *s_feat = reinterpret_cast<FT *>(smem + CT * sizeof(Header));
-    const FT *feat = reinterpret_cast<const FT *>(a.feat);
-
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int tile = blockIdx.x;
-    const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
-    const int bx0 = tx * TILE + (warp & 1) * 8, by0 = ty * TILE + (warp >> 1) * 4;
-    const int px = bx0 + (lane & 7), py = by0 + (lane >> 3);
-    const bool inside = px < a.W && py < a.H;
-    const float fpx = (float)px, fpy = (float)py;
-    const float fbx0 = (float)bx0, fbx1 = (float)(bx0 + 7), fby0 = (float)by0, fby1 = (float)(by0 + 3);
-
-    if (a.C < CP) {
-        // zero the padding channels once; staging writes only the first C
-        for (int i = tid; i < CT * CP; i += CT) s_feat[i] = FT(0.0f);
-    }
-    const uint2 rg = a.ranges[tile];
-    const int n = (int)(rg.y - rg.x);
-    const bool vec_ok = (a.C % FeatIO<FT>::VEC) == 0;
-
-    float F[CP];
-#pragma unroll
-    for (int c = 0; c < CP; ++c) F[c] = 0.0f;
-    float T = 1.0f;
-    uint32_t last = 0;
-    bool done = !inside;
-
-    for (int b0 = 0; b0 < n; b0 += CT) {
-        if (__syncthreads_and(done)) break;  // also guards the staging buffers
-        if (b0 + tid < n) stage<CP, FT>(a.hdr, feat, a.C, vec_ok, a.ids[rg.x + b0 + tid], s_hdr, s_feat, tid);
-        __syncthreads();
-        const int cnt = min(CT, n - b0);
-        if (__all_sync(FULL, done)) continue;
-        for (int c0 = 0; c0 < cnt; c0 += 32) {
-            bool rel = false;
-            if (c0 + lane < cnt) {
-                const Header h = s_hdr[c0 + lane];
-                rel = (h.h0.x + h.h1.z >= fbx0) && (h.h0.x - h.h1.z <= fbx1) && (h.h0.y + h.h1.w >= fby0) &&
-                      (h.h0.y - h.h1.w <= fby1);
-            }
-            uint32_t m = __ballot_sync(FULL, rel);
-            while (m) {
-                const int j = c0 + __ffs(m) - 1;
-                m &= m - 1;
-                const float4 h0 = s_hdr[j].h0;
-                const float4 h1 = s_hdr[j].h1;
-                const float q = gauss_q(fpx - h0.x, fpy - h0.y, h0.z, h0.w, h1.x);
-                float w = 0.0f;
-                if (!done && q <= 0.0f) {
-                    const float al = fminf(a.alpha_max, gauss_alpha_raw(q, h1.y));
-                    if (al >= a.alpha_min) {
-                        const float Tn = T * (1.0f - al);
-                        if (Tn < a.t_min) {
-                            done = true;
-                        } else {
-                            w = al * T;
-                            T = Tn;
-                            last = (uint32_t)(b0 + j + 1);
-                        }
-                    }
-                }
-                if (__any_sync(FULL, w != 0.0f)) FeatIO<FT>::template axpy<CP>(F, s_feat + (size_t)j * CP, w);
-            }
-            if (__all_sync(FULL, done)) break;
-        }
-    }
-    if (inside) {
-        const size_t HW = (size_t)a.W * a.H, pix = (size_t)py * a.W + px;
-#pragma unroll
-        for (int c = 0; c < CP; ++c)
-            if (c < a.C) a.out_feat[c * HW + pix] = F[c];
-        if (a.out_alpha) a.out_alpha[pix] = 1.0f - T;
-        if (a.out_T) a.out_T[pix] = T;
-        if (a.out_last) a.out_last[pix] = last;
-    }
-}
-
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
@@ -197,7 +384,9 @@ __device__ __forceinline__ float warp_sum(float v) {
 
 // A8: reverse traversal from each pixel's last blended Gaussian, with the
 // transmittance in front of each Gaussian recomputed by division from the
-// saved final transmittance.
+// saved final transmittance.  The blend decisions repeat the forward's
+// arithmetic exactly (same instructions), so the contributor set is the
+// forward's.
 template <int CP, typename FT>
 __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -236,8 +425,7 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
         for (int c = 0; c < CP; ++c)
             if (c < a.C) g[c] = a.dF[c * HW + pix];
     }
-    // the tile's deepest blended position
-    uint32_t wmax = __reduce_max_sync(FULL, lastk);
+    const uint32_t wmax = __reduce_max_sync(FULL, lastk);
     if (lane == 0) s_max[warp] = wmax;
     __syncthreads();
     uint32_t nmax = 0;
@@ -255,8 +443,7 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
         }
         __syncthreads();
         const int cnt = hi - lo;
-        const uint32_t wl = __reduce_max_sync(FULL, lastk);
-        if (wl <= (uint32_t)lo) continue;  // nothing of this batch blended in this warp
+        if (wmax <= (uint32_t)lo) continue;  // nothing of this batch blended in this warp
         for (int c1 = cnt; c1 > 0; c1 -= 32) {
             const int c0 = max(0, c1 - 32);
             bool rel = false;
@@ -276,12 +463,14 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
                 const float dx = fpx - h0.x, dy = fpy - h0.y;
                 const float q = gauss_q(dx, dy, h0.z, h0.w, h1.x);
                 bool contrib = false;
-                float al = 0.0f, eq = 0.0f, raw = 0.0f;
+                float al = 0.0f, raw = 0.0f;
                 if (k < lastk && q <= 0.0f) {
-                    eq = __expf(q);
-                    raw = __fmul_rn(h1.y, eq);
-                    al = fminf(a.alpha_max, raw);
-                    contrib = al >= a.alpha_min;
+                    const float e2 = fmaf(q, LOG2E, h1.y);
+                    if (e2 >= a.log2_alpha_min) {
+                        raw = ex2(e2);
+                        al = fminf(a.alpha_max, raw);
+                        contrib = true;
+                    }
                 }
                 if (!__any_sync(FULL, contrib)) continue;
                 float f[CP];
@@ -298,11 +487,10 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
                     sg = fmaf(wgt, fg, sg);
                     T = Tj;
                     if (raw < a.alpha_max) {
-                        d_o = eq * dal;
+                        d_o = (raw / ex2(h1.y)) * dal;  // d alpha / d o = e^q
                         dq = al * dal;
                     }
                 }
-                // per-Gaussian sums over the warp's pixels
                 if (a.d_feat) {
 #pragma unroll
                     for (int c = 0; c < CP; ++c) {
@@ -335,15 +523,16 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
     }
 }
 
-template <int CP, typename FT>
+template <int CP, bool F32F>
 void run_composite(const CompositeArgs &a, cudaStream_t s) {
-    const size_t smem = CT * sizeof(Header) + (size_t)CT * CP * sizeof(FT);
+    const size_t smem = sizeof(CompSmem<CP, F32F>);
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_composite<CP, FT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_composite<CP, F32F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
     }
-    k_composite<CP, FT><<<a.tiles_x * a.tiles_y, CT, smem, s>>>(a);
+    k_composite<CP, F32F><<<a.tiles_x * a.tiles_y, NTHR, smem, s>>>(a);
+    note_launches(1);
 }
 
 template <int CP, typename FT>
@@ -355,17 +544,17 @@ void run_backward(const BackwardArgs &a, cudaStream_t s) {
         attr = true;
     }
     k_backward<CP, FT><<<a.tiles_x * a.tiles_y, CT, smem, s>>>(a);
+    note_launches(1);
 }
 
 }  // namespace
 
 void launch_composite(const CompositeArgs &a, cudaStream_t s) {
     if (a.tiles_x * a.tiles_y == 0) return;
-    const bool bf = a.feat_dtype == TSPLAT_BF16;
-    if (a.C <= 8) { if (bf) run_composite<8, __nv_bfloat16>(a, s); else run_composite<8, float>(a, s); }
-    else if (a.C <= 16) { if (bf) run_composite<16, __nv_bfloat16>(a, s); else run_composite<16, float>(a, s); }
-    else if (a.C <= 32) { if (bf) run_composite<32, __nv_bfloat16>(a, s); else run_composite<32, float>(a, s); }
-    else { if (bf) run_composite<64, __nv_bfloat16>(a, s); else run_composite<64, float>(a, s); }
+    const bool f32 = a.feat_dtype == TSPLAT_F32;
+    if (a.C <= 16) { if (f32) run_composite<16, true>(a, s); else run_composite<16, false>(a, s); }
+    else if (a.C <= 32) { if (f32) run_composite<32, true>(a, s); else run_composite<32, false>(a, s); }
+    else { if (f32) run_composite<64, true>(a, s); else run_composite<64, false>(a, s); }
 }
 
 void launch_backward(const BackwardArgs &a, cudaStream_t s) {

@@ -51,27 +51,44 @@ __device__ __forceinline__ void write_culled(const ProjectOut &o, uint64_t i) {
 }
 
 // Rendered-Gaussian bookkeeping: depth-key range (for the radix sort's pass
-// count) and the visible count, reduced per warp before the atomics.
-// Called by all 32 lanes of every warp.
+// count) and the visible count, reduced per block before one set of
+// atomics.  Called by every thread of a 256-thread block.
 __device__ __forceinline__ void account(const ProjectOut &o, bool vis, uint32_t key) {
+    __shared__ uint32_t s_min[8], s_max[8], s_n[8];
     const uint32_t m = 0xffffffffu;
     const uint32_t kmin = __reduce_min_sync(m, vis ? key : CULLED_KEY);
     const uint32_t kmax = __reduce_max_sync(m, vis ? key : 0u);
     const uint32_t nv = __popc(__ballot_sync(m, vis));
-    if ((threadIdx.x & 31) == 0 && nv) {
-        atomicMin(&o.kminmax[0], kmin);
-        atomicMax(&o.kminmax[1], kmax);
-        atomicAdd(o.n_vis, nv);
+    const int warp = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        s_min[warp] = kmin;
+        s_max[warp] = kmax;
+        s_n[warp] = nv;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t bmin = CULLED_KEY, bmax = 0, bn = 0;
+        for (int w = 0; w < 8; ++w) {
+            bmin = min(bmin, s_min[w]);
+            bmax = max(bmax, s_max[w]);
+            bn += s_n[w];
+        }
+        if (bn) {
+            atomicMin(&o.kminmax[0], bmin);
+            atomicMax(&o.kminmax[1], bmax);
+            atomicAdd(o.n_vis, bn);
+        }
     }
 }
 
 // Tile rect from mean2d and radius, as the cited rasterizer defines it.
 __device__ __forceinline__ int tile_rect(float mx, float my, float r, int tiles_x, int tiles_y, int &x0,
                                          int &y0, int &x1, int &y1) {
-    x0 = clamp_floor(fdiv(fsub(mx, r), 16.0f), tiles_x);
-    x1 = clamp_floor(fdiv(fadd(fadd(mx, r), 15.0f), 16.0f), tiles_x);
-    y0 = clamp_floor(fdiv(fsub(my, r), 16.0f), tiles_y);
-    y1 = clamp_floor(fdiv(fadd(fadd(my, r), 15.0f), 16.0f), tiles_y);
+    // v / 16 == v * 0.0625 exactly (power-of-two scaling)
+    x0 = clamp_floor(fmul(fsub(mx, r), 0.0625f), tiles_x);
+    x1 = clamp_floor(fmul(fadd(fadd(mx, r), 15.0f), 0.0625f), tiles_x);
+    y0 = clamp_floor(fmul(fsub(my, r), 0.0625f), tiles_y);
+    y1 = clamp_floor(fmul(fadd(fadd(my, r), 15.0f), 0.0625f), tiles_y);
     return (x1 - x0) * (y1 - y0);
 }
 
@@ -139,7 +156,7 @@ __global__ __launch_bounds__(256) void k_project(const float4 *__restrict__ xyzo
                 float ex, ey;
                 cull_extents(ca_, cb_, cc_, g.w, par.alpha_min, ex, ey);
                 o.hdr[i].h0 = make_float4(mx, my, ca_, cb_);
-                o.hdr[i].h1 = make_float4(cc_, g.w, ex, ey);
+                o.hdr[i].h1 = make_float4(cc_, log2f(g.w), ex, ey);
                 o.rect[i] = pack_rect(x0, y0, x1, y1);
                 o.ntiles[i] = (uint32_t)nt;
                 key = __float_as_uint(pz);
@@ -180,7 +197,7 @@ __global__ __launch_bounds__(256) void k_prepare_2d(uint64_t n, const float *__r
             float ex, ey;
             cull_extents(a, b, c, opac[i], par.alpha_min, ex, ey);
             o.hdr[i].h0 = make_float4(mx, my, a, b);
-            o.hdr[i].h1 = make_float4(c, opac[i], ex, ey);
+            o.hdr[i].h1 = make_float4(c, log2f(opac[i]), ex, ey);
             o.rect[i] = pack_rect(x0, y0, x1, y1);
             o.ntiles[i] = (uint32_t)nt;
             key = __float_as_uint(z);
@@ -224,6 +241,7 @@ __global__ void k_export_rect(const uint2 *rect, const uint32_t *n_dev, int32_t 
 void launch_export_rect(const uint2 *rect, const uint32_t *n_dev, int64_t n_cap, int32_t *dst, cudaStream_t s) {
     if (n_cap <= 0) return;
     k_export_rect<<<(unsigned)((n_cap + 255) / 256), 256, 0, s>>>(rect, n_dev, dst);
+    note_launches(1);
 }
 
 void launch_project(const float4 *xyzo, const float4 *cova, const float2 *covb, const uint32_t *n_dev,
@@ -232,6 +250,7 @@ void launch_project(const float4 *xyzo, const float4 *cova, const float2 *covb, 
     if (n_cap <= 0) return;
     k_project<<<(unsigned)((n_cap + 255) / 256), 256, 0, s>>>(xyzo, cova, covb, n_dev, cam, par, tiles_x,
                                                               tiles_y, o);
+    note_launches(1);
 }
 
 void launch_prepare_2d(int64_t n, const float *mean2d, const float *conic, const float *opac,
@@ -240,12 +259,14 @@ void launch_prepare_2d(int64_t n, const float *mean2d, const float *conic, const
     if (n <= 0) return;
     k_prepare_2d<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((uint64_t)n, mean2d, conic, opac, depth, radius,
                                                              par, tiles_x, tiles_y, o);
+    note_launches(1);
 }
 
 void launch_export_header(const Header *hdr, const uint32_t *n_dev, int64_t n_cap, int what, void *dst,
                           cudaStream_t s) {
     if (n_cap <= 0) return;
     k_export_header<<<(unsigned)((n_cap + 255) / 256), 256, 0, s>>>(hdr, n_dev, what, (float *)dst);
+    note_launches(1);
 }
 
 }  // namespace tsp

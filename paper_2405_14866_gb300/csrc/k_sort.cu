@@ -210,10 +210,10 @@ __global__ __launch_bounds__(EM_THREADS) void k_emit_count(EmitArgs a) {
     __shared__ uint32_t sw[EM_THREADS / 32];
     const uint64_t n = *a.n_dev;
     const int np = sv_passes(a.order);
-    const uint64_t base = (uint64_t)blockIdx.x * EM_TILE + (uint64_t)threadIdx.x * EM_ITEMS;
+    const uint64_t base = (uint64_t)blockIdx.x * EM_TILE + threadIdx.x;
     uint32_t s = 0;
     for (int i = 0; i < EM_ITEMS; ++i) {
-        const uint64_t k = base + i;
+        const uint64_t k = base + (uint64_t)i * EM_THREADS;
         if (k < n) s += a.ntiles[sorted_val(a.order, np, k)];
     }
     uint32_t tot;
@@ -238,6 +238,11 @@ __global__ __launch_bounds__(1024) void k_emit_scan_blocks(EmitArgs a, int nbloc
     if (threadIdx.x == 0) *a.p_dev = tot;
 }
 
+// Items (depth-ordered Gaussians) of block b: [b * 4096, (b + 1) * 4096) in
+// 16 rounds of 256.  Per round a block scan gives each item its pair offset;
+// the 32 items of a warp own one contiguous run of pairs, which the warp
+// writes cooperatively (lane e of the run finds its Gaussian by binary
+// search over the lanes' offsets), so the stores are coalesced.
 __global__ __launch_bounds__(EM_THREADS) void k_emit_write(EmitArgs a) {
     __shared__ uint32_t sw[EM_THREADS / 32];
     if ((uint64_t)*a.p_dev > (uint64_t)a.p_cap) {  // nothing is emitted when the pairs do not fit
@@ -246,35 +251,45 @@ __global__ __launch_bounds__(EM_THREADS) void k_emit_write(EmitArgs a) {
     }
     const uint64_t n = *a.n_dev;
     const int np = sv_passes(a.order);
-    const uint64_t base = (uint64_t)blockIdx.x * EM_TILE + (uint64_t)threadIdx.x * EM_ITEMS;
-    uint32_t ids[EM_ITEMS], cnt[EM_ITEMS];
-    uint32_t s = 0;
-#pragma unroll
-    for (int i = 0; i < EM_ITEMS; ++i) {
-        const uint64_t k = base + i;
-        ids[i] = 0;
-        cnt[i] = 0;
+    const int lane = threadIdx.x & 31;
+    uint64_t running = a.blk_sum[blockIdx.x];
+    const uint64_t base = (uint64_t)blockIdx.x * EM_TILE;
+    for (int r = 0; r < EM_ITEMS; ++r) {
+        const uint64_t k = base + (uint64_t)r * EM_THREADS + threadIdx.x;
+        uint32_t id = 0, cnt = 0;
+        int x0 = 0, y0 = 0, x1 = 0, y1 = 0;
         if (k < n) {
-            ids[i] = sorted_val(a.order, np, k);
-            cnt[i] = a.ntiles[ids[i]];
+            id = sorted_val(a.order, np, k);
+            cnt = a.ntiles[id];
+            if (cnt) unpack_rect(a.rect[id], x0, y0, x1, y1);
         }
-        s += cnt[i];
-    }
-    uint32_t tot;
-    uint64_t off = (uint64_t)a.blk_sum[blockIdx.x] + block_excl_scan<EM_THREADS / 32>(s, sw, tot);
+        uint32_t tot;
+        const uint32_t excl = block_excl_scan<EM_THREADS / 32>(cnt, sw, tot);
+        const uint64_t my_off = running + excl;
+        const uint64_t wfirst = __shfl_sync(FULL, my_off, 0);
+        const uint32_t start = (uint32_t)(my_off - wfirst);           // run-relative start of this lane
+        const uint32_t wtot = __shfl_sync(FULL, start + cnt, 31);     // the warp's run length
+        const int w = x1 - x0;
+        for (uint32_t e0 = 0; e0 < wtot; e0 += 32) {  // warp-uniform trip count
+            const uint32_t e = e0 + lane;
+            int o = 0;  // owner: the last lane whose start <= e
 #pragma unroll
-    for (int i = 0; i < EM_ITEMS; ++i) {
-        if (cnt[i] == 0) continue;
-        int x0, y0, x1, y1;
-        unpack_rect(a.rect[ids[i]], x0, y0, x1, y1);
-        uint64_t o = off;
-        for (int ty = y0; ty < y1; ++ty)
-            for (int tx = x0; tx < x1; ++tx) {
-                a.pair_tile[o] = a.tile_base + (uint32_t)(ty * a.tiles_x + tx);
-                a.pair_id[o] = ids[i];
-                ++o;
+            for (int step = 16; step > 0; step >>= 1) {
+                const int cand = o + step;
+                const uint32_t sc = __shfl_sync(FULL, start, cand & 31);
+                if (cand < 32 && sc <= e) o = cand;
             }
-        off += cnt[i];
+            const uint32_t so = __shfl_sync(FULL, start, o);
+            const int ox0 = __shfl_sync(FULL, x0, o), oy0 = __shfl_sync(FULL, y0, o), ow = __shfl_sync(FULL, w, o);
+            const uint32_t oid = __shfl_sync(FULL, id, o);
+            if (e < wtot) {
+                const int loc = (int)(e - so);
+                const int ty = oy0 + loc / ow, tx = ox0 + loc % ow;
+                a.pair_tile[wfirst + e] = a.tile_base + (uint32_t)(ty * a.tiles_x + tx);
+                a.pair_id[wfirst + e] = oid;
+            }
+        }
+        running += tot;
     }
 }
 
@@ -307,13 +322,17 @@ void launch_radix_sort(const RadixSort &rs, int max_passes, cudaStream_t s) {
     cudaMemsetAsync(rs.totals, 0, sizeof(uint32_t) * 256 * max_passes, s);
     for (int p = 0; p < max_passes; ++p) {
         k_radix_upsweep<<<rs.nblocks, RS_THREADS, 0, s>>>(rs, p);
+    note_launches(1);
         k_radix_scan<<<256, 256, 0, s>>>(rs, p);
+    note_launches(1);
         k_radix_downsweep<<<rs.nblocks, RS_THREADS, 0, s>>>(rs, p);
+    note_launches(1);
     }
 }
 
 void launch_depth_npass(const uint32_t *kminmax, uint32_t *npass, cudaStream_t s) {
     k_depth_npass<<<1, 1, 0, s>>>(kminmax, npass);
+    note_launches(1);
 }
 
 static int emit_blocks(int64_t n_cap) { return (int)((n_cap + EM_TILE - 1) / EM_TILE); }
@@ -325,13 +344,16 @@ void launch_emit_count(const EmitArgs &a, cudaStream_t s) {
         return;
     }
     k_emit_count<<<nb, EM_THREADS, 0, s>>>(a);
+    note_launches(1);
     k_emit_scan_blocks<<<1, 1024, 0, s>>>(a, nb);
+    note_launches(1);
 }
 
 void launch_emit_write(const EmitArgs &a, cudaStream_t s) {
     const int nb = emit_blocks(a.n_cap);
     if (nb == 0) return;
     k_emit_write<<<nb, EM_THREADS, 0, s>>>(a);
+    note_launches(1);
 }
 
 void launch_ranges(const uint32_t *tiles_sorted, const uint32_t *p_dev, int64_t p_cap, uint2 *ranges,
@@ -341,21 +363,25 @@ void launch_ranges(const uint32_t *tiles_sorted, const uint32_t *p_dev, int64_t 
     const int threads = 256;
     const int64_t blocks = (p_cap + threads - 1) / threads;
     k_ranges<<<(unsigned)blocks, threads, 0, s>>>(tiles_sorted, p_dev, (uint64_t)p_cap, ranges, (uint32_t)n_tiles);
+    note_launches(1);
 }
 
 void launch_pairs_effective(const uint32_t *src, uint32_t cap, uint32_t *dst, cudaStream_t s) {
     k_pairs_effective<<<1, 1, 0, s>>>(src, cap, dst);
+    note_launches(1);
 }
 
 void launch_zero_f32_n(float *p, const uint32_t *n_dev, int mult, int64_t n_cap, cudaStream_t s) {
     if (!p || n_cap <= 0) return;
     const int64_t tot = n_cap * mult;
     k_zero_f32_n<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(p, n_dev, mult);
+    note_launches(1);
 }
 
 void launch_fill_u32(uint32_t *p, uint32_t v, int64_t n, cudaStream_t s) {
     if (n <= 0) return;
     k_fill_u32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, v, (uint64_t)n);
+    note_launches(1);
 }
 
 }  // namespace tsp
