@@ -133,8 +133,8 @@ struct tsplat_ctx {
 };
 
 namespace {
-enum { SM_KMIN = 0, SM_KMAX = 1, SM_NVIS = 2, SM_NPASS = 3, SM_P = 4, SM_PEFF = 5, SM_STATUS = 6, SM_N = 7,
-       SM_TOTALS = 16, SM_WORDS = 16 + 4 * 256 };
+enum { SM_KMIN = 0, SM_KMAX = 1, SM_NVIS = 2, SM_NPASS = 3, SM_P = 4, SM_PEFF = 5, SM_STATUS = 6, SM_TILECTR = 7,
+       SM_N = 8, SM_TOTALS = 16, SM_WORDS = 16 + 4 * 256 };
 uint32_t *small_ptr(tsplat_ctx *c, int w) { return c->small.as<uint32_t>() + w; }
 }  // namespace
 
@@ -486,6 +486,7 @@ static tsplat_status render_tail(tsplat_ctx *c, int64_t n_cap, const uint32_t *n
     ca.t_min = par.t_min;
     ca.log2_alpha_min = (float)log2((double)par.alpha_min);
     ca.status = sm + SM_STATUS;
+    ca.tile_counter = sm + SM_TILECTR;
     ca.out_feat = out_feat;
     ca.out_alpha = out_alpha;
     ca.out_T = save ? c->tfinal.as<float>() : nullptr;
@@ -519,7 +520,7 @@ static tsplat_status check_common(tsplat_ctx *c, int W, int H, int C, int dtype,
 static void init_small(tsplat_ctx *c, cudaStream_t s) {
     uint32_t *sm = c->small.as<uint32_t>();
     launch_fill_u32(sm + SM_KMIN, CULLED_KEY, 1, s);
-    cudaMemsetAsync(sm + SM_KMAX, 0, sizeof(uint32_t) * 6, s);  // kmax, n_vis, npass, P, P_eff, status
+    cudaMemsetAsync(sm + SM_KMAX, 0, sizeof(uint32_t) * 7, s);  // kmax, n_vis, npass, P, P_eff, status, tile counter
 }
 
 tsplat_status tsplat_render(const tsplat_gaussians *g, const tsplat_camera *cam, const tsplat_render_params *params,

@@ -144,6 +144,7 @@ struct CompositeArgs {
     float alpha_max, alpha_min, t_min;
     float log2_alpha_min;  // blend test: log2(o) + q log2(e) >= log2(alpha_min)
     uint32_t *status;      // TSPLAT_ERR_TIMEOUT if a bounded wait expired
+    uint32_t *tile_counter;  // next tile to hand out (0 at launch)
     float *out_feat;
     float *out_alpha;
     float *out_T;        // may be NULL

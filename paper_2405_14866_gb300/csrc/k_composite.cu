@@ -47,6 +47,8 @@ struct Ring {
     static constexpr int N = CP <= 32 ? 8 : 4;  // ring slots (deeper where shared memory allows)
 };
 
+constexpr uint32_t FINAL_TILE = 0xffffffffu;  // slot tile id of the last slot a CTA produces
+
 template <int CP, bool F32F>
 struct CompSmem {
     static constexpr int RING = Ring<CP>::N;
@@ -58,8 +60,11 @@ struct CompSmem {
     __nv_bfloat16 zero[CP];
     uint64_t full[RING];
     uint64_t empty[RING];
-    uint32_t cnt[RING];
-    uint32_t done_mask;
+    uint32_t cnt[RING];        // Gaussians in the slot; 0 marks the end of a tile (or of the CTA's work)
+    uint32_t tile[RING];       // tile the slot belongs to, FINAL_TILE after the last tile
+    uint32_t base[RING];       // list position of the slot's first Gaussian
+    int32_t done_seq[NCW];     // per consumer warp: sequence number of the last tile it is done with
+    uint8_t list[NCW][SB];     // per consumer warp: slot indices of its surviving Gaussians, in order
 };
 
 __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
@@ -97,49 +102,72 @@ __device__ __forceinline__ void produce_one(CompSmem<CP, F32F> &S, const Composi
     }
 }
 
-// The full barrier of a slot expects one regular arrival (lane 0, after the
-// slot's count is written) plus, per producer lane, the asynchronous arrival
-// that fires once that lane's copies have landed.  The ids of the next slot
-// are loaded before the current slot's copies are issued.
+// The producer warp takes tiles from the grid-wide counter until none are
+// left and streams each tile's list through the ring, followed by an
+// end-of-tile slot; a final slot tells the consumers to leave.  The full
+// barrier of a slot expects one regular arrival (lane 0, after the slot's
+// metadata is written) plus, per producer lane, the asynchronous arrival that
+// fires once that lane's copies have landed.  A tile whose consumer warps
+// are all saturated is cut short.
 template <int CP, bool F32F>
-__device__ void producer(CompSmem<CP, F32F> &S, const CompositeArgs &a, uint32_t first, int n, int lane) {
+__device__ void producer(CompSmem<CP, F32F> &S, const CompositeArgs &a, int lane) {
     constexpr int RING = CompSmem<CP, F32F>::RING;
-    const int nbatch = (n + SB - 1) / SB;
+    const uint32_t n_tiles = (uint32_t)(a.tiles_x * a.tiles_y);
+    uint32_t i = 0;  // slots produced so far (ring position and phase)
     bool timed_out = false;
-    uint32_t nid0 = lane < n ? a.ids[first + lane] : 0u;
-    uint32_t nid1 = lane + 32 < n ? a.ids[first + lane + 32] : 0u;
-    for (int i = 0; i <= nbatch; ++i) {
-        const int slot = i % RING;
-        if (!mbar_wait(&S.empty[slot], ((i / RING) & 1) ^ 1, a.status)) {
-            timed_out = true;
-            break;
+    for (int32_t seq = 0;; ++seq) {
+        uint32_t t = 0;
+        if (lane == 0) t = atomicAdd(a.tile_counter, 1u);
+        t = __shfl_sync(FULL, t, 0);
+        const bool last_tile = t >= n_tiles;
+        uint32_t first = 0;
+        int n = 0;
+        if (!last_tile) {
+            const uint2 rg = a.ranges[t];
+            first = rg.x;
+            n = (int)(rg.y - rg.x);
         }
-        const bool all_done = *reinterpret_cast<volatile uint32_t *>(&S.done_mask) == (1u << NCW) - 1;
-        const bool end = i == nbatch || all_done;  // the end marker is a slot with count 0
-        const int base = i * SB, cnt = end ? 0 : min(SB, n - base);
-        if (!end) {
-            const uint32_t id0 = nid0, id1 = nid1;
-            const int nbase = base + SB;
-            nid0 = nbase + lane < n ? a.ids[first + nbase + lane] : 0u;
-            nid1 = nbase + lane + 32 < n ? a.ids[first + nbase + lane + 32] : 0u;
-            if (lane < cnt) produce_one<CP, F32F>(S, a, slot, lane, id0);
-            if (lane + 32 < cnt) produce_one<CP, F32F>(S, a, slot, lane + 32, id1);
+        uint32_t nid0 = lane < n ? a.ids[first + lane] : 0u;
+        uint32_t nid1 = lane + 32 < n ? a.ids[first + lane + 32] : 0u;
+        for (int b = 0;; b += SB, ++i) {
+            const int slot = (int)(i % RING);
+            if (!mbar_wait(&S.empty[slot], ((i / RING) & 1) ^ 1, a.status)) {
+                timed_out = true;
+                break;
+            }
+            bool all_done = true;
+#pragma unroll
+            for (int w = 0; w < NCW; ++w) all_done &= *reinterpret_cast<volatile int32_t *>(&S.done_seq[w]) >= seq;
+            const bool end = last_tile || b >= n || all_done;
+            const int cnt = end ? 0 : min(SB, n - b);
+            if (!end) {
+                const uint32_t id0 = nid0, id1 = nid1;
+                const int nb = b + SB;
+                nid0 = nb + lane < n ? a.ids[first + nb + lane] : 0u;
+                nid1 = nb + lane + 32 < n ? a.ids[first + nb + lane + 32] : 0u;
+                if (lane < cnt) produce_one<CP, F32F>(S, a, slot, lane, id0);
+                if (lane + 32 < cnt) produce_one<CP, F32F>(S, a, slot, lane + 32, id1);
+            }
+            // every lane, every slot: counts against the barrier's expected
+            // arrivals (.noinc) and fires once this lane's copies have landed
+            asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&S.full[slot])) : "memory");
+            __syncwarp();
+            if (lane == 0) {
+                S.cnt[slot] = cnt;
+                S.tile[slot] = last_tile ? FINAL_TILE : t;
+                S.base[slot] = b;
+                mbar_arrive(&S.full[slot]);
+            }
+            if (end) {
+                ++i;
+                break;
+            }
         }
-        // every lane, every slot (the end marker too): counts against the
-        // barrier's expected arrivals (.noinc) and fires once this lane's
-        // copies have landed (immediately when it issued none)
-        asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&S.full[slot])) : "memory");
-        __syncwarp();
-        if (lane == 0) {
-            S.cnt[slot] = cnt;
-            mbar_arrive(&S.full[slot]);
-        }
-        if (end) break;
+        if (timed_out || last_tile) break;
     }
     if (timed_out) {
         set_status(a.status, TSPLAT_ERR_TIMEOUT);
-        // let the copies already issued land before the CTA can exit
-        asm volatile("cp.async.wait_all;" ::: "memory");
+        asm volatile("cp.async.wait_all;" ::: "memory");  // copies already issued land before the CTA exits
     }
 }
 
@@ -148,6 +176,8 @@ __device__ __forceinline__ bool box_hit(const Header &h, float bx0, float bx1, f
            (h.h0.y - h.h1.w <= by1);
 }
 
+// Persistent: gridDim.x CTAs (a few per SM) share the tiles through
+// a.tile_counter, which must be 0 at launch.
 template <int CP, bool F32F>
 __global__ __launch_bounds__(NTHR, 2) void k_composite(CompositeArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -156,87 +186,123 @@ __global__ __launch_bounds__(NTHR, 2) void k_composite(CompositeArgs a) {
     constexpr int RING = CompSmem<CP, F32F>::RING;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int tile = blockIdx.x;
-    const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
-    const uint2 rg = a.ranges[tile];
-    const int n = (int)(rg.y - rg.x);
-
     if (tid == 0) {
         for (int r = 0; r < RING; ++r) {
             mbar_init(&S.full[r], 1 + 32);  // lane 0's arrival + one asynchronous arrival per producer lane
             mbar_init(&S.empty[r], NCW);
         }
-        S.done_mask = 0;
         mbar_init_fence();
     }
+    if (tid < NCW) S.done_seq[tid] = -1;
     for (int c = tid; c < CP; c += NTHR) S.zero[c] = __float2bfloat16_rn(0.0f);
     __syncthreads();
 
     if (warp == NCW) {
-        producer<CP, F32F>(S, a, rg.x, n, lane);
+        producer<CP, F32F>(S, a, lane);
         return;
     }
 
     // ---------------------------------------------------------- consumers
-    const int bx0 = tx * TILE + (warp & 1) * 8, by0 = ty * TILE + (warp >> 1) * 4;
-    const int px = bx0 + (lane & 7), py = by0 + (lane >> 3);
-    const bool inside = px < a.W && py < a.H;
-    const float fpx = (float)px, fpy = (float)py;
-    const float fbx0 = (float)bx0, fbx1 = (float)(bx0 + 7), fby0 = (float)by0, fby1 = (float)(by0 + 3);
     const float amax = a.alpha_max, l2min = a.log2_alpha_min, tmin = a.t_min;
-
-    float acc[2][NT8][4];
-#pragma unroll
-    for (int m = 0; m < 2; ++m)
-#pragma unroll
-        for (int t = 0; t < NT8; ++t)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) acc[m][t][e] = 0.0f;
-    float T = 1.0f;
-    uint32_t last = 0;
-    bool done = !inside;
-    bool wdone = __all_sync(FULL, done);
-    if (wdone && lane == 0) atomicOr(&S.done_mask, 1u << warp);
-
+    const size_t HW = (size_t)a.W * a.H;
     // ldmatrix address pattern: lane supplies row (lane & 7) of matrix lane / 8
     const int kl = ((lane >> 3) & 1) * 8 + (lane & 7);  // group entry whose B row this lane addresses
     const int arow = kl, acol = (lane >> 4) * 8, bcol = (lane >> 4) * 8;
+    const uint32_t lt = (1u << lane) - 1u;
 
-    for (int i = 0;; ++i) {
-        const int slot = i % RING;
+    float acc[2][NT8][4];
+    float T = 1.0f;
+    uint32_t last = 0;
+    bool done = true, wdone = true;
+    int bx0 = 0, by0 = 0;          // this warp's 8x4 block in the current tile
+    float fpx = 0.f, fpy = 0.f;    // this lane's pixel centre
+    uint32_t cur = FINAL_TILE;     // tile in progress
+    int32_t seq = -1;
+
+    for (uint32_t i = 0;; ++i) {
+        const int slot = (int)(i % RING);
         if (!mbar_wait(&S.full[slot], (i / RING) & 1, a.status)) {
             set_status(a.status, TSPLAT_ERR_TIMEOUT);
             break;
         }
+        const uint32_t t = S.tile[slot];
         const int cnt = (int)S.cnt[slot];
-        if (cnt == 0) break;
-        if (!wdone) {
-            const int base = i * SB;
+        if (t == FINAL_TILE) break;
+        if (t != cur) {  // first slot of a new tile: reset the per-pixel state
+            cur = t;
+            ++seq;
+            const int tx = (int)(t % (uint32_t)a.tiles_x), ty = (int)(t / (uint32_t)a.tiles_x);
+            bx0 = tx * TILE + (warp & 1) * 8;
+            by0 = ty * TILE + (warp >> 1) * 4;
+            fpx = (float)(bx0 + (lane & 7));
+            fpy = (float)(by0 + (lane >> 3));
+#pragma unroll
+            for (int m = 0; m < 2; ++m)
+#pragma unroll
+                for (int u = 0; u < NT8; ++u)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) acc[m][u][e] = 0.0f;
+            T = 1.0f;
+            last = 0;
+            done = !(bx0 + (lane & 7) < a.W && by0 + (lane >> 3) < a.H);
+            wdone = __all_sync(FULL, done);
+            if (wdone && lane == 0) *reinterpret_cast<volatile int32_t *>(&S.done_seq[warp]) = seq;
+        }
+        if (cnt == 0) {
+            // end of the tile: write this warp's block (the accumulator of lane l
+            // holds pixels l/4 (+8, +16, +24) and channels 8u + 2(l%4) (+1))
+#pragma unroll
+            for (int m = 0; m < 2; ++m)
+#pragma unroll
+                for (int hh = 0; hh < 2; ++hh) {
+                    const int p = m * 16 + hh * 8 + (lane >> 2);
+                    const int x = bx0 + (p & 7), y = by0 + (p >> 3);
+                    if (x < a.W && y < a.H) {
+                        float *dst = a.out_feat + (size_t)y * a.W + x;
+#pragma unroll
+                        for (int u = 0; u < NT8; ++u) {
+                            const int c = u * 8 + 2 * (lane & 3);
+                            if (c < a.C) dst[c * HW] = acc[m][u][2 * hh];
+                            if (c + 1 < a.C) dst[(c + 1) * HW] = acc[m][u][2 * hh + 1];
+                        }
+                    }
+                }
+            const int px = bx0 + (lane & 7), py = by0 + (lane >> 3);
+            if (px < a.W && py < a.H) {
+                const size_t pix = (size_t)py * a.W + px;
+                if (a.out_alpha) a.out_alpha[pix] = 1.0f - T;
+                if (a.out_T) a.out_T[pix] = T;
+                if (a.out_last) a.out_last[pix] = last;
+            }
+            if (lane == 0) *reinterpret_cast<volatile int32_t *>(&S.done_seq[warp]) = seq;
+            cur = FINAL_TILE;
+        } else if (!wdone) {
+            const int base = (int)S.base[slot];
+            // survivors of the alpha_min box test, in list order
+            const float fbx0 = (float)bx0, fbx1 = (float)(bx0 + 7), fby0 = (float)by0, fby1 = (float)(by0 + 3);
             const bool r0 = lane < cnt && box_hit(S.hdr[slot][lane], fbx0, fbx1, fby0, fby1);
             const bool r1 = lane + 32 < cnt && box_hit(S.hdr[slot][lane + 32], fbx0, fbx1, fby0, fby1);
-            uint32_t m0 = __ballot_sync(FULL, r0);
-            uint32_t m1 = __ballot_sync(FULL, r1);
-            while ((m0 | m1) && !wdone) {
+            const uint32_t m0 = __ballot_sync(FULL, r0), m1 = __ballot_sync(FULL, r1);
+            const int c0 = __popc(m0), nrel = c0 + __popc(m1);
+            if (r0) S.list[warp][__popc(m0 & lt)] = (uint8_t)lane;
+            if (r1) S.list[warp][c0 + __popc(m1 & lt)] = (uint8_t)(lane + 32);
+            __syncwarp();
+            for (int g0 = 0; g0 < nrel && !wdone; g0 += 16) {
                 uint32_t wh[8], wl[8];
-                int my_j = -1;  // slot index of group entry kl (B-operand row address)
 #pragma unroll
                 for (int g = 0; g < 16; g += 2) {
                     float w2[2];
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
-                        // next survivor in order (warp-uniform), -1 when the group runs out
-                        const int j = m0 ? __ffs(m0) - 1 : (m1 ? 31 + __ffs(m1) : -1);
-                        if (m0) m0 &= m0 - 1;
-                        else m1 &= m1 - 1;
-                        if (kl == g + h) my_j = j;
                         // straight-line recurrence: only T / done / last carry a dependency
-                        const int jj = j < 0 ? 0 : j;
-                        const float4 h0 = S.hdr[slot][jj].h0;
-                        const float4 h1 = S.hdr[slot][jj].h1;
+                        const bool have = g0 + g + h < nrel;
+                        const int j = have ? S.list[warp][g0 + g + h] : 0;
+                        const float4 h0 = S.hdr[slot][j].h0;
+                        const float4 h1 = S.hdr[slot][j].h1;
                         const float q = gauss_q(fpx - h0.x, fpy - h0.y, h0.z, h0.w, h1.x);
                         const float e2 = fmaf(q, LOG2E, h1.y);
                         const float al = fminf(amax, ex2(e2));
-                        const bool ok = (j >= 0) & !done & (q <= 0.0f) & (e2 >= l2min);
+                        const bool ok = have & !done & (q <= 0.0f) & (e2 >= l2min);
                         const float Tn = T * (1.0f - al);
                         const bool stop = ok & (Tn < tmin);
                         const bool blend = ok & !stop;
@@ -262,64 +328,39 @@ __global__ __launch_bounds__(NTHR, 2) void k_composite(CompositeArgs a) {
                     ldsm_x4(ah[m][0], ah[m][1], ah[m][2], ah[m][3], &S.whi[warp][m * 16 + arow][acol]);
                     ldsm_x4(aw[m][0], aw[m][1], aw[m][2], aw[m][3], &S.wlo[warp][m * 16 + arow][acol]);
                 }
+                const int my_j = g0 + kl < nrel ? (int)S.list[warp][g0 + kl] : -1;
                 const __nv_bfloat16 *browh = my_j >= 0 ? &S.fhi[slot][my_j][0] : &S.zero[0];
 #pragma unroll
                 for (int p = 0; p < NT8 / 2; ++p) {
-                    uint32_t b[4];
-                    ldsm_x4_t(b[0], b[1], b[2], b[3], browh + p * 16 + bcol);
+                    uint32_t bb[4];
+                    ldsm_x4_t(bb[0], bb[1], bb[2], bb[3], browh + p * 16 + bcol);
 #pragma unroll
                     for (int m = 0; m < 2; ++m) {
-                        mma_bf16(acc[m][2 * p], ah[m][0], ah[m][1], ah[m][2], ah[m][3], b[0], b[1]);
-                        mma_bf16(acc[m][2 * p], aw[m][0], aw[m][1], aw[m][2], aw[m][3], b[0], b[1]);
-                        mma_bf16(acc[m][2 * p + 1], ah[m][0], ah[m][1], ah[m][2], ah[m][3], b[2], b[3]);
-                        mma_bf16(acc[m][2 * p + 1], aw[m][0], aw[m][1], aw[m][2], aw[m][3], b[2], b[3]);
+                        mma_bf16(acc[m][2 * p], ah[m][0], ah[m][1], ah[m][2], ah[m][3], bb[0], bb[1]);
+                        mma_bf16(acc[m][2 * p], aw[m][0], aw[m][1], aw[m][2], aw[m][3], bb[0], bb[1]);
+                        mma_bf16(acc[m][2 * p + 1], ah[m][0], ah[m][1], ah[m][2], ah[m][3], bb[2], bb[3]);
+                        mma_bf16(acc[m][2 * p + 1], aw[m][0], aw[m][1], aw[m][2], aw[m][3], bb[2], bb[3]);
                     }
                     if (F32F) {
                         const __nv_bfloat16 *browl =
                             my_j >= 0 ? &S.flo[F32F ? slot : 0][F32F ? my_j : 0][0] : &S.zero[0];
-                        ldsm_x4_t(b[0], b[1], b[2], b[3], browl + p * 16 + bcol);
+                        ldsm_x4_t(bb[0], bb[1], bb[2], bb[3], browl + p * 16 + bcol);
 #pragma unroll
                         for (int m = 0; m < 2; ++m) {
-                            mma_bf16(acc[m][2 * p], ah[m][0], ah[m][1], ah[m][2], ah[m][3], b[0], b[1]);
-                            mma_bf16(acc[m][2 * p], aw[m][0], aw[m][1], aw[m][2], aw[m][3], b[0], b[1]);
-                            mma_bf16(acc[m][2 * p + 1], ah[m][0], ah[m][1], ah[m][2], ah[m][3], b[2], b[3]);
-                            mma_bf16(acc[m][2 * p + 1], aw[m][0], aw[m][1], aw[m][2], aw[m][3], b[2], b[3]);
+                            mma_bf16(acc[m][2 * p], ah[m][0], ah[m][1], ah[m][2], ah[m][3], bb[0], bb[1]);
+                            mma_bf16(acc[m][2 * p], aw[m][0], aw[m][1], aw[m][2], aw[m][3], bb[0], bb[1]);
+                            mma_bf16(acc[m][2 * p + 1], ah[m][0], ah[m][1], ah[m][2], ah[m][3], bb[2], bb[3]);
+                            mma_bf16(acc[m][2 * p + 1], aw[m][0], aw[m][1], aw[m][2], aw[m][3], bb[2], bb[3]);
                         }
                     }
                 }
                 __syncwarp();
                 wdone = __all_sync(FULL, done);
             }
-            if (wdone && lane == 0) atomicOr(&S.done_mask, 1u << warp);
+            if (wdone && lane == 0) *reinterpret_cast<volatile int32_t *>(&S.done_seq[warp]) = seq;
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&S.empty[slot]);
-    }
-
-    // outputs: the accumulator of lane l holds pixels l/4 (+8, +16, +24) and
-    // channels 8t + 2(l%4) (+1)
-    const size_t HW = (size_t)a.W * a.H;
-#pragma unroll
-    for (int m = 0; m < 2; ++m)
-#pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-            const int p = m * 16 + hh * 8 + (lane >> 2);
-            const int x = bx0 + (p & 7), y = by0 + (p >> 3);
-            if (x < a.W && y < a.H) {
-                float *dst = a.out_feat + (size_t)y * a.W + x;
-#pragma unroll
-                for (int t = 0; t < NT8; ++t) {
-                    const int c = t * 8 + 2 * (lane & 3);
-                    if (c < a.C) dst[c * HW] = acc[m][t][2 * hh];
-                    if (c + 1 < a.C) dst[(c + 1) * HW] = acc[m][t][2 * hh + 1];
-                }
-            }
-        }
-    if (inside) {
-        const size_t pix = (size_t)py * a.W + px;
-        if (a.out_alpha) a.out_alpha[pix] = 1.0f - T;
-        if (a.out_T) a.out_T[pix] = T;
-        if (a.out_last) a.out_last[pix] = last;
     }
 }
 
@@ -526,12 +567,16 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
 template <int CP, bool F32F>
 void run_composite(const CompositeArgs &a, cudaStream_t s) {
     const size_t smem = sizeof(CompSmem<CP, F32F>);
-    static bool attr = false;
-    if (!attr) {
+    static int grid = 0;
+    if (!grid) {
         cudaFuncSetAttribute(k_composite<CP, F32F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_composite<CP, F32F>, NTHR, smem);
+        grid = std::max(1, sms) * std::max(1, per_sm);
     }
-    k_composite<CP, F32F><<<a.tiles_x * a.tiles_y, NTHR, smem, s>>>(a);
+    k_composite<CP, F32F><<<std::min(grid, std::max(1, a.tiles_x * a.tiles_y)), NTHR, smem, s>>>(a);
     note_launches(1);
 }
 

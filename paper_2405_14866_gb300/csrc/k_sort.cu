@@ -76,7 +76,7 @@ __global__ __launch_bounds__(RS_THREADS) void k_radix_upsweep(RadixSort rs, int 
     const bool remap = pass == 0 && rs.kmin;
     const uint32_t kmin = remap ? *rs.kmin : 0u;
     const int shift = 8 * pass;
-    const uint32_t *src = pass == 0 ? rs.keys_in : rs.keys[(pass - 1) & 1];
+    const uint32_t *src = pass == 0 ? rs.keys_in : (((pass - 1) & 1) ? rs.keys[1] : rs.keys[0]);
     const uint64_t base = (uint64_t)blockIdx.x * RS_TILE;
 #pragma unroll 4
     for (int i = 0; i < RS_ITEMS; ++i) {
@@ -119,28 +119,43 @@ __global__ __launch_bounds__(256) void k_radix_scan(RadixSort rs, int pass) {
     }
 }
 
-__global__ __launch_bounds__(RS_THREADS) void k_radix_downsweep(RadixSort rs, int pass) {
+// Stable scatter of one block's 4096 keys: (1) each warp ranks its 512 keys
+// (16 rounds of 32) among equal digits with a ballot per digit bit;
+// (2) digit offsets inside the block follow from the per-warp counts;
+// (3) keys and values are placed in shared memory in digit order;
+// (4) consecutive threads write consecutive entries, so each digit's run is
+// stored contiguously (coalesced) at its global offset.
+constexpr int DS_THREADS = 512;
+
+__global__ __launch_bounds__(DS_THREADS, 2) void k_radix_downsweep(RadixSort rs, int pass) {
     if (pass >= rs_passes(rs)) return;
-    constexpr int NW = RS_THREADS / 32;
-    constexpr int PER_WARP = RS_TILE / NW;  // 512 keys, 16 rounds of 32
-    __shared__ uint32_t wcnt[NW][256];
-    __shared__ uint32_t dbase[NW][256];
+    constexpr int NW = DS_THREADS / 32;
+    constexpr int PER_WARP = RS_TILE / NW;  // 256 keys, 8 rounds of 32
+    constexpr int ROUNDS = PER_WARP / 32;
+    __shared__ uint32_t wcnt[NW][256];      // per-warp digit counts, then per-warp digit offsets
+    __shared__ uint32_t lbase[256];         // first local position of each digit
+    __shared__ uint32_t gbase[256];         // global offset of each digit for this block
+    __shared__ uint32_t sw[NW];
+    __shared__ uint32_t skey[RS_TILE];
+    __shared__ uint32_t sval[RS_TILE];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    for (int i = tid; i < NW * 256; i += RS_THREADS) (&wcnt[0][0])[i] = 0;
+    for (int i = tid; i < NW * 256; i += DS_THREADS) (&wcnt[0][0])[i] = 0;
     __syncthreads();
     const uint64_t n = *rs.n_dev;
     const bool remap = pass == 0 && rs.kmin;
     const uint32_t kmin = remap ? *rs.kmin : 0u;
     const int shift = 8 * pass;
-    const uint32_t *ksrc = pass == 0 ? rs.keys_in : rs.keys[(pass - 1) & 1];
-    const uint32_t *vsrc = pass == 0 ? rs.vals_in : rs.vals[(pass - 1) & 1];
-    uint32_t *kdst = rs.keys[pass & 1];
-    uint32_t *vdst = rs.vals[pass & 1];
-    const uint64_t wbase = (uint64_t)blockIdx.x * RS_TILE + (uint64_t)warp * PER_WARP;
+    const bool odd = (pass & 1) != 0;
+    const uint32_t *ksrc = pass == 0 ? rs.keys_in : (odd ? rs.keys[0] : rs.keys[1]);
+    const uint32_t *vsrc = pass == 0 ? rs.vals_in : (odd ? rs.vals[0] : rs.vals[1]);
+    uint32_t *kdst = odd ? rs.keys[1] : rs.keys[0];
+    uint32_t *vdst = odd ? rs.vals[1] : rs.vals[0];
+    const uint64_t bbase = (uint64_t)blockIdx.x * RS_TILE;
+    const uint64_t wbase = bbase + (uint64_t)warp * PER_WARP;
     const uint32_t lt = lanemask_lt();
-    uint32_t key[PER_WARP / 32], val[PER_WARP / 32], rank[PER_WARP / 32];
+    uint32_t key[ROUNDS], val[ROUNDS], rank[ROUNDS];
 #pragma unroll
-    for (int r = 0; r < PER_WARP / 32; ++r) {
+    for (int r = 0; r < ROUNDS; ++r) {
         const uint64_t idx = wbase + (uint64_t)r * 32 + lane;
         const bool valid = idx < n;
         uint32_t k = 0, v = 0;
@@ -150,8 +165,13 @@ __global__ __launch_bounds__(RS_THREADS) void k_radix_downsweep(RadixSort rs, in
         }
         key[r] = k;
         val[r] = v;
-        const uint32_t d = valid ? ((k >> shift) & 255u) : 256u;
-        const uint32_t peers = __match_any_sync(FULL, d);
+        const uint32_t d = (k >> shift) & 255u;
+        uint32_t peers = __ballot_sync(FULL, valid);
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const uint32_t bal = __ballot_sync(FULL, (d >> b) & 1u);
+            peers &= ((d >> b) & 1u) ? bal : ~bal;
+        }
         uint32_t before = 0;
         if (valid) before = wcnt[warp][d];
         __syncwarp();
@@ -160,24 +180,42 @@ __global__ __launch_bounds__(RS_THREADS) void k_radix_downsweep(RadixSort rs, in
         rank[r] = before + __popc(peers & lt);
     }
     __syncthreads();
-    {
-        uint32_t run = rs.hist[(size_t)tid * rs.nblocks + blockIdx.x];
+    {   // thread d < 256 owns digit d: offsets of each warp inside the digit, digit base inside the block
+        uint32_t run = 0;
+        if (tid < 256) {
 #pragma unroll
-        for (int w = 0; w < NW; ++w) {
-            dbase[w][tid] = run;
-            run += wcnt[w][tid];
+            for (int w = 0; w < NW; ++w) {
+                const uint32_t c = wcnt[w][tid];
+                wcnt[w][tid] = run;
+                run += c;
+            }
+        }
+        uint32_t tot;
+        const uint32_t lb = block_excl_scan<NW>(run, sw, tot);
+        if (tid < 256) {
+            lbase[tid] = lb;
+            gbase[tid] = rs.hist[(size_t)tid * rs.nblocks + blockIdx.x];
         }
     }
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < PER_WARP / 32; ++r) {
+    for (int r = 0; r < ROUNDS; ++r) {
         const uint64_t idx = wbase + (uint64_t)r * 32 + lane;
         if (idx < n) {
             const uint32_t d = (key[r] >> shift) & 255u;
-            const uint32_t pos = dbase[warp][d] + rank[r];
-            kdst[pos] = key[r];
-            vdst[pos] = val[r];
+            const uint32_t pos = lbase[d] + wcnt[warp][d] + rank[r];
+            skey[pos] = key[r];
+            sval[pos] = val[r];
         }
+    }
+    __syncthreads();
+    const uint32_t cnt = (uint32_t)min((uint64_t)RS_TILE, n > bbase ? n - bbase : 0);
+    for (uint32_t p = tid; p < cnt; p += DS_THREADS) {
+        const uint32_t k = skey[p];
+        const uint32_t d = (k >> shift) & 255u;
+        const uint32_t pos = gbase[d] + (p - lbase[d]);
+        kdst[pos] = k;
+        vdst[pos] = sval[p];
     }
 }
 
@@ -199,7 +237,7 @@ constexpr int EM_TILE = EM_THREADS * EM_ITEMS;
 
 __device__ __forceinline__ uint32_t sorted_val(const SortedVals &s, int np, uint64_t k) {
     if (np == 0) return s.vals_in ? s.vals_in[k] : (uint32_t)k;
-    return s.vals[(np - 1) & 1][k];
+    return (((np - 1) & 1) ? s.vals[1] : s.vals[0])[k];
 }
 
 __device__ __forceinline__ int sv_passes(const SortedVals &s) {
@@ -325,7 +363,7 @@ void launch_radix_sort(const RadixSort &rs, int max_passes, cudaStream_t s) {
     note_launches(1);
         k_radix_scan<<<256, 256, 0, s>>>(rs, p);
     note_launches(1);
-        k_radix_downsweep<<<rs.nblocks, RS_THREADS, 0, s>>>(rs, p);
+        k_radix_downsweep<<<rs.nblocks, DS_THREADS, 0, s>>>(rs, p);
     note_launches(1);
     }
 }
