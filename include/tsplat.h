@@ -173,6 +173,24 @@ tsplat_status tsplat_build(const tsplat_src_view *views, int32_t n_views, int32_
 tsplat_status tsplat_build_into(tsplat_gaussians *g, const tsplat_src_view *views,
                                 int32_t n_views, void *stream);
 
+/* tsplat_build_into without any device allocation (the paper has no
+ * counterpart).  For callers that cannot call cudaMalloc at this point: a
+ * frame loop with a fixed latency budget (device allocation and release
+ * synchronize the device), work being recorded into a CUDA graph, or a
+ * process whose device memory is fully owned by another allocator.  Same
+ * inputs, outputs and results as tsplat_build_into; `g` is allocated by the
+ * caller beforehand (tsplat_gaussians_create).
+ * Limit: at most 64 Mi source pixels in total per call (e.g. 16 views of
+ * 2048 x 2048); larger inputs return TSPLAT_ERR_CAPACITY before any work.
+ * The per-block scratch of the compaction is one fixed 128 KiB device array
+ * that every GPU loading the library keeps until the process exits.  The
+ * first call on a device resolves that array's device address (with that
+ * device current); make that first call before any stream capture.  All
+ * calls share the array: calls that overlap on the GPU (other streams,
+ * other threads) race and must be serialized by the caller. */
+tsplat_status tsplat_build_into_noalloc(tsplat_gaussians *g, const tsplat_src_view *views,
+                                        int32_t n_views, void *stream);
+
 /* ------------------------------------------------------------------------
  * Render context: scratch memory of one render stream plus the state saved
  * for the backward pass.  One context must not be used by two streams at

@@ -58,6 +58,7 @@ _SIGS = {
     "tsplat_gaussians_shape": (c_int32, [c_void_p, POINTER(c_int64), POINTER(c_int32), POINTER(c_int32)]),
     "tsplat_build": (c_int32, [POINTER(CSrcView), c_int32, c_int32, c_int32, POINTER(c_void_p), c_void_p]),
     "tsplat_build_into": (c_int32, [c_void_p, POINTER(CSrcView), c_int32, c_void_p]),
+    "tsplat_build_into_noalloc": (c_int32, [c_void_p, POINTER(CSrcView), c_int32, c_void_p]),
     "tsplat_ctx_create": (c_int32, [POINTER(c_void_p)]),
     "tsplat_ctx_destroy": (c_int32, [c_void_p]),
     "tsplat_ctx_reserve": (c_int32, [c_void_p, c_int64, c_int64, c_int32, c_int32, c_int32]),

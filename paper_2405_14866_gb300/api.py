@@ -142,6 +142,11 @@ class Gaussians:
         arr = (L.CSrcView * len(views))(*views)
         L.call("tsplat_build_into", self.handle, arr, len(views), _stream(stream))
 
+    def build_into_noalloc(self, views: Sequence[L.CSrcView], stream=None):
+        """build_into without device allocation (fixed library scratch; see tsplat.h)."""
+        arr = (L.CSrcView * len(views))(*views)
+        L.call("tsplat_build_into_noalloc", self.handle, arr, len(views), _stream(stream))
+
     def count(self) -> int:
         n = ctypes.c_int64()
         L.call("tsplat_gaussians_count", self.handle, ctypes.byref(n))

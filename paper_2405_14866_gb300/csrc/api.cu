@@ -138,6 +138,21 @@ enum { SM_KMIN = 0, SM_KMAX = 1, SM_NVIS = 2, SM_NPASS = 3, SM_P = 4, SM_PEFF = 
 uint32_t *small_ptr(tsplat_ctx *c, int w) { return c->small.as<uint32_t>() + w; }
 }  // namespace
 
+namespace tsp {
+void gaussians_store(tsplat_gaussians *g, GaussianStore &out, cudaStream_t writer) {
+    out.cap = g->cap;
+    out.C = g->C;
+    out.dtype = g->dtype;
+    out.xyzo = g->xyzo.as<float4>();
+    out.cova = g->cova.as<float4>();
+    out.covb = g->covb.as<float2>();
+    out.feat = g->feat.p;
+    out.n_dev = g->n_dev.as<uint32_t>();
+    g->last_stream = writer;
+}
+tsplat_status record_error(tsplat_status st, const char *msg) { return fail(st, "%s", msg); }
+}  // namespace tsp
+
 extern "C" {
 
 void tsplat_render_params_default(tsplat_render_params *p) {

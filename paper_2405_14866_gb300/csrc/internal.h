@@ -177,6 +177,20 @@ void launch_backward(const BackwardArgs &a, cudaStream_t s);
 // every launcher reports its launches here (tsplat_launch_count)
 void note_launches(int n);
 
+// Device arrays of a Gaussian store (for entry points outside api.cu).
+struct GaussianStore {
+    int64_t cap;
+    int C, dtype;
+    float4 *xyzo;
+    float4 *cova;
+    float2 *covb;
+    void *feat;
+    uint32_t *n_dev;
+};
+void gaussians_store(tsplat_gaussians *g, GaussianStore &out, cudaStream_t writer);
+// Record the thread-local message returned by tsplat_last_error; returns st.
+tsplat_status record_error(tsplat_status st, const char *msg);
+
 // small utilities
 void launch_fill_u32(uint32_t *p, uint32_t v, int64_t n, cudaStream_t s);
 // *dst = *src if it fits in cap, else 0 (an overflowing render emits no pairs)
