@@ -271,6 +271,21 @@ tsplat_status tsplat_render(const tsplat_gaussians *g, const tsplat_camera *cam,
                             const tsplat_render_params *params, float *out_feat,
                             float *out_alpha, tsplat_ctx *ctx, void *stream);
 
+/* Several target views of the same Gaussians in one pass (the viewer's left
+ * and right eye views, Sec. 4.2; several viewers in serving): 1 <= n_views
+ * <= 8 cameras of any sizes.  Every view's Gaussians are projected in one
+ * launch (each Gaussian read once), one depth sort covers all
+ * (view, Gaussian) instances, the tile ids of all views form one space, and
+ * one compositing launch covers every tile.  out_feat[v] (C x H_v x W_v) and
+ * out_alpha[v] (H_v x W_v, or out_alpha == NULL) are device buffers.  Each
+ * view's result is bit-identical to tsplat_render of that view alone.
+ * TSPLAT_RENDER_SAVE is not supported here (TSPLAT_ERR_UNSUPPORTED).  In
+ * TSPLAT_RENDER_ASYNC mode, reserve the context for n_views * N Gaussians,
+ * the pairs of all views and the sum of their tiles. */
+tsplat_status tsplat_render_batch(const tsplat_gaussians *g, const tsplat_camera *cams, int32_t n_views,
+                                  const tsplat_render_params *params, float *const *out_feat,
+                                  float *const *out_alpha, tsplat_ctx *ctx, void *stream);
+
 /* A3..A7 from already projected 2D Gaussians (device arrays):
  *   mean2d N*2 f32, conic N*3 f32 (a, b, c), opac N f32,
  *   depth N f32 (sort key; must be > 0 for rendered Gaussians),
@@ -302,6 +317,82 @@ tsplat_status tsplat_rasterize(int64_t n, const float *mean2d, const float *coni
 tsplat_status tsplat_backward(tsplat_ctx *ctx, const float *dL_dfeat, const float *dL_dalpha,
                               float *d_mean2d, float *d_conic, float *d_opac, float *d_feat,
                               void *stream);
+
+/* ------------------------------------------------------------------------
+ * A9 -- serving: continuous batching of target views (the viewer's left and
+ * right eye views, Sec. 4.2; CUDA Graphs, Sec. 5.3).
+ *
+ * A worker thread admits submitted requests, in arrival order, into batches
+ * of up to max_views_per_batch views of any sizes (up to max_width x
+ * max_height) while the batch's estimated pairs fit one lane's pair
+ * buffer.  Each lane renders one batch at a time as one
+ * CUDA-graph replay of tsplat_render_batch; up to max_lanes batches overlap
+ * on the device, as many as budget_bytes of scratch allow.  A batch that
+ * overflows is re-run one view at a time.  Each result is bit-identical to
+ * rendering that view alone.  Outputs are caller device buffers as in
+ * tsplat_render; they must stay valid until the request completes, and no
+ * work on them may be pending at submission (the server's streams do not
+ * wait on the caller's).  Once tsplat_server_wait/poll reports completion
+ * the outputs may be read on any stream.
+ * ---------------------------------------------------------------------- */
+typedef struct tsplat_server tsplat_server;
+/* Issue each batch as plain launches instead of a CUDA-graph replay.  With
+ * max_views_per_batch = 1 and max_lanes = 1 the server renders one view per
+ * launch sequence, one at a time: the unbatched baseline behind the same
+ * queue. */
+#define TSPLAT_SERVER_NO_GRAPH 1
+typedef struct {
+    int32_t max_views_per_batch;  /* 1..8 (8) */
+    int32_t max_lanes;            /* batches in flight at once (3) */
+    int32_t max_width, max_height;/* largest view (1024 x 1024) */
+    int64_t max_gaussians;        /* capacity of the frames' Gaussian stores (2^22) */
+    int32_t C, feat_dtype;        /* of the frames (32, TSPLAT_BF16) */
+    /* admission estimate of a view's (Gaussian, tile) pairs:
+     * pairs_per_gaussian x frame capacity + pairs_per_pixel x width x height;
+     * a lane holds max_views_per_batch maximal views' worth */
+    float pairs_per_gaussian;     /* (2.5) */
+    float pairs_per_pixel;        /* (1.0) */
+    int32_t flags;                /* TSPLAT_SERVER_* (0) */
+    int32_t reserved;
+    int64_t budget_bytes;         /* device memory for the lanes' scratch (8 GiB) */
+    tsplat_render_params params;
+} tsplat_server_config;
+
+typedef struct {
+    int64_t completed, batches, views_launched, retried, pending;
+    int64_t lane_bytes;             /* device scratch of one lane */
+    int32_t lanes, reserved;
+    double p50_ms, p99_ms, max_ms;  /* request latency, submission to completion */
+    double views_per_s;             /* completed / (last completion - first submission) */
+} tsplat_server_stats;
+
+void tsplat_server_config_default(tsplat_server_config *cfg);
+tsplat_status tsplat_server_create(const tsplat_server_config *cfg, tsplat_server **out);
+/* Waits for the batches in flight, drops pending requests. */
+tsplat_status tsplat_server_destroy(tsplat_server *s);
+/* Gaussians that the batches admitted from now on render (the frame; keep
+ * it alive and unmodified while batches use it -- double-buffer frames).
+ * Batches wait on the device for the work queued, at the time of this call,
+ * on the stream that last built `g`. */
+tsplat_status tsplat_server_update_frame(tsplat_server *s, const tsplat_gaussians *g);
+/* Captures, on every lane, the graphs of all batch sizes for the store `g`
+ * (which need not be the current frame), so that no capture happens while
+ * requests wait; blocks until done or timeout_ms passed.  Graphs are kept
+ * for the two most recently used stores of each lane. */
+tsplat_status tsplat_server_prepare(tsplat_server *s, const tsplat_gaussians *g, double timeout_ms);
+/* Blocks until no batch in flight renders `g` (a frame replaced by a later
+ * tsplat_server_update_frame), so that it may be rebuilt; TSPLAT_ERR_TIMEOUT
+ * after timeout_ms; TSPLAT_ERR_INVALID_ARG if `g` is the current frame. */
+tsplat_status tsplat_server_release_frame(tsplat_server *s, const tsplat_gaussians *g, double timeout_ms);
+tsplat_status tsplat_server_submit(tsplat_server *s, const tsplat_camera *cam, float *out_feat,
+                                   float *out_alpha, uint64_t *req_id);
+/* TSPLAT_OK when done (latency in ms), TSPLAT_ERR_NOT_READY before. */
+tsplat_status tsplat_server_poll(tsplat_server *s, uint64_t req_id, double *latency_ms);
+/* Blocks until done or timeout_ms passed (TSPLAT_ERR_TIMEOUT). */
+tsplat_status tsplat_server_wait(tsplat_server *s, uint64_t req_id, double timeout_ms, double *latency_ms);
+tsplat_status tsplat_server_get_stats(tsplat_server *s, tsplat_server_stats *out);
+/* Clears statistics and forgets completed requests. */
+tsplat_status tsplat_server_reset_stats(tsplat_server *s);
 
 /* Mean stage durations, in milliseconds, of the renders on `ctx` that used
  * TSPLAT_RENDER_PROFILE since the previous call (at most the last 256),

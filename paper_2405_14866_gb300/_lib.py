@@ -40,6 +40,19 @@ class CSrcView(Structure):
                 ("cam", CCamera)]
 
 
+class CServerConfig(Structure):
+    _fields_ = [("max_views_per_batch", c_int32), ("max_lanes", c_int32), ("max_width", c_int32),
+                ("max_height", c_int32), ("max_gaussians", c_int64), ("C", c_int32), ("feat_dtype", c_int32),
+                ("pairs_per_gaussian", c_float), ("pairs_per_pixel", c_float), ("flags", c_int32),
+                ("reserved", c_int32), ("budget_bytes", c_int64), ("params", CParams)]
+
+
+class CServerStats(Structure):
+    _fields_ = [("completed", c_int64), ("batches", c_int64), ("views_launched", c_int64), ("retried", c_int64),
+                ("pending", c_int64), ("lane_bytes", c_int64), ("lanes", c_int32), ("reserved", c_int32), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double), ("views_per_s", ctypes.c_double)]
+
+
 class CStats(Structure):
     _fields_ = [("n_gaussians", c_int64), ("n_visible", c_int64), ("n_pairs", c_int64),
                 ("pair_capacity", c_int64), ("tiles_x", c_int32), ("tiles_y", c_int32), ("width", c_int32),
@@ -66,10 +79,23 @@ _SIGS = {
     "tsplat_ctx_status": (c_int32, [c_void_p]),
     "tsplat_ctx_export": (c_int32, [c_void_p, c_int32, c_void_p, c_size_t, c_void_p]),
     "tsplat_render": (c_int32, [c_void_p, POINTER(CCamera), POINTER(CParams), c_void_p, c_void_p, c_void_p, c_void_p]),
+    "tsplat_render_batch": (c_int32, [c_void_p, POINTER(CCamera), c_int32, POINTER(CParams), POINTER(c_void_p),
+                                      POINTER(c_void_p), c_void_p, c_void_p]),
     "tsplat_rasterize": (c_int32, [c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int32,
                                    c_int32, c_int32, c_int32, POINTER(CParams), c_void_p, c_void_p, c_void_p,
                                    c_void_p]),
     "tsplat_backward": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "tsplat_server_config_default": (None, [POINTER(CServerConfig)]),
+    "tsplat_server_create": (c_int32, [POINTER(CServerConfig), POINTER(c_void_p)]),
+    "tsplat_server_destroy": (c_int32, [c_void_p]),
+    "tsplat_server_update_frame": (c_int32, [c_void_p, c_void_p]),
+    "tsplat_server_submit": (c_int32, [c_void_p, POINTER(CCamera), c_void_p, c_void_p, POINTER(ctypes.c_uint64)]),
+    "tsplat_server_poll": (c_int32, [c_void_p, ctypes.c_uint64, POINTER(ctypes.c_double)]),
+    "tsplat_server_wait": (c_int32, [c_void_p, ctypes.c_uint64, ctypes.c_double, POINTER(ctypes.c_double)]),
+    "tsplat_server_release_frame": (c_int32, [c_void_p, c_void_p, ctypes.c_double]),
+    "tsplat_server_prepare": (c_int32, [c_void_p, c_void_p, ctypes.c_double]),
+    "tsplat_server_get_stats": (c_int32, [c_void_p, POINTER(CServerStats)]),
+    "tsplat_server_reset_stats": (c_int32, [c_void_p]),
     "tsplat_ctx_timings": (c_int32, [c_void_p, POINTER(c_float), c_int32, POINTER(c_int32)]),
     "tsplat_launch_count": (ctypes.c_uint64, []),
 }

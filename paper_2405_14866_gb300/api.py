@@ -15,6 +15,7 @@ import torch
 from . import _lib as L
 
 F32, BF16 = L.F32, L.BF16
+SERVER_NO_GRAPH = 1  # TSPLAT_SERVER_NO_GRAPH
 
 
 def _ptr(t: Optional[torch.Tensor]):
@@ -201,6 +202,22 @@ class Context:
         self.n = None
         return out_feat, out_alpha
 
+    def render_batch(self, g: Gaussians, cams, params: Optional[L.CParams] = None, async_=False, out_feat=None,
+                     out_alpha=None, stream=None, profile=False):
+        """Render several views of `g` in one pass; returns lists (F_v, A_v)."""
+        K = len(cams)
+        cc = (L.CCamera * K)(*[ccamera(c) for c in cams])
+        if out_feat is None:
+            out_feat = [torch.empty((g.C, c.height, c.width), device="cuda") for c in cc]
+        if out_alpha is None:
+            out_alpha = [torch.empty((c.height, c.width), device="cuda") for c in cc]
+        fp = (ctypes.c_void_p * K)(*[t.data_ptr() for t in out_feat])
+        ap = (ctypes.c_void_p * K)(*[t.data_ptr() for t in out_alpha])
+        p = _with_flags(params, False, async_, profile)
+        L.call("tsplat_render_batch", g.handle, cc, K, ctypes.byref(p), fp, ap, self.handle, _stream(stream))
+        self.n = None
+        return out_feat, out_alpha
+
     def rasterize(self, mean2d, conic, opac, depth, radius, feat, width: int, height: int,
                   params: Optional[L.CParams] = None, save=False, async_=False, out_feat=None, out_alpha=None,
                   stream=None):
@@ -263,6 +280,81 @@ class Context:
     def close(self):
         if self.handle:
             L.lib().tsplat_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching view server (tsplat_server): submit target views
+    of the current frame; a worker thread batches them into CUDA-graph
+    replays on up to `max_lanes` overlapping lanes."""
+
+    def __init__(self, max_views_per_batch=8, max_lanes=3, max_width=1024, max_height=1024, max_gaussians=1 << 22,
+                 C=32, feat_dtype=BF16, pairs_per_gaussian=2.5, pairs_per_pixel=1.0, budget_bytes=8 << 30,
+                 params: Optional[L.CParams] = None,
+                 graphs: bool = True):
+        cfg = L.CServerConfig()
+        L.lib().tsplat_server_config_default(ctypes.byref(cfg))
+        cfg.max_views_per_batch, cfg.max_lanes = max_views_per_batch, max_lanes
+        cfg.max_width, cfg.max_height, cfg.max_gaussians = max_width, max_height, max_gaussians
+        cfg.C, cfg.feat_dtype, cfg.pairs_per_pixel, cfg.budget_bytes = C, feat_dtype, pairs_per_pixel, budget_bytes
+        cfg.pairs_per_gaussian = pairs_per_gaussian
+        cfg.flags = 0 if graphs else SERVER_NO_GRAPH
+        if params is not None:
+            cfg.params = params
+        h = ctypes.c_void_p()
+        L.call("tsplat_server_create", ctypes.byref(cfg), ctypes.byref(h))
+        self.handle = h
+        self.C = C
+
+    def update_frame(self, g: Gaussians):
+        L.call("tsplat_server_update_frame", self.handle, g.handle)
+
+    def prepare(self, g: Gaussians, timeout_ms: float = 60000.0):
+        """Capture the graphs of every batch size for the store `g` ahead of use."""
+        L.call("tsplat_server_prepare", self.handle, g.handle, timeout_ms)
+
+    def release_frame(self, g: Gaussians, timeout_ms: float = 30000.0):
+        """Block until no batch in flight renders the (replaced) frame `g`."""
+        L.call("tsplat_server_release_frame", self.handle, g.handle, timeout_ms)
+
+    def submit(self, cam, out_feat, out_alpha=None) -> int:
+        cc = cam if isinstance(cam, L.CCamera) else ccamera(cam)
+        rid = ctypes.c_uint64()
+        L.call("tsplat_server_submit", self.handle, ctypes.byref(cc), _ptr(out_feat), _ptr(out_alpha), ctypes.byref(rid))
+        return int(rid.value)
+
+    def poll(self, rid: int):
+        """Latency in ms when done, else None."""
+        lat = ctypes.c_double()
+        st = L.lib().tsplat_server_poll(self.handle, rid, ctypes.byref(lat))
+        if st == 6:
+            return None
+        if st != 0:
+            raise L.TsplatError("tsplat_server_poll", st, L.lib().tsplat_last_error().decode())
+        return float(lat.value)
+
+    def wait(self, rid: int, timeout_ms: float = 30000.0) -> float:
+        lat = ctypes.c_double()
+        L.call("tsplat_server_wait", self.handle, rid, timeout_ms, ctypes.byref(lat))
+        return float(lat.value)
+
+    def stats(self) -> Dict[str, float]:
+        s = L.CServerStats()
+        L.call("tsplat_server_get_stats", self.handle, ctypes.byref(s))
+        return {k: getattr(s, k) for k, _ in L.CServerStats._fields_ if k != "reserved"}
+
+    def reset_stats(self):
+        L.call("tsplat_server_reset_stats", self.handle)
+
+    def close(self):
+        if self.handle:
+            L.lib().tsplat_server_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -22,8 +22,8 @@ class SplatFn(torch.autograd.Function):
     @staticmethod
     def forward(ctx, mean2d, conic, opac, feat, depth, radius, width, height, params, context: Context):
         F, A = context.rasterize(mean2d.detach().contiguous(), conic.detach().contiguous(),
-                                 opac.detach().contiguous(), feat.detach().contiguous(), depth.detach().contiguous(),
-                                 radius.contiguous(), width, height, params, save=True)
+                                 opac.detach().contiguous(), depth.detach().contiguous(), radius.contiguous(),
+                                 feat.detach().contiguous(), width, height, params, save=True)
         ctx.context = context
         ctx.n, ctx.C = feat.shape
         ctx.feat_dtype = feat.dtype

@@ -109,8 +109,8 @@ struct tsplat_ctx {
     DBuf hdr, rect, ntiles, dkey, radius, skeys0, skeys1, svals0, svals1, hist_n, emit_blk;
     // P-sized
     DBuf pk0, pk1, pv0, pv1, hist_p;
-    // tiles / pixels
-    DBuf ranges, tfinal, last;
+    // tiles / pixels / view table
+    DBuf ranges, tfinal, last, views;
     // small words: kminmax[2], n_vis, npass, p_dev, p_eff, status, n_dev, totals[4*256]
     DBuf small;
     uint32_t *host_small = nullptr;  // pinned mirror
@@ -134,7 +134,7 @@ struct tsplat_ctx {
 
 namespace {
 enum { SM_KMIN = 0, SM_KMAX = 1, SM_NVIS = 2, SM_NPASS = 3, SM_P = 4, SM_PEFF = 5, SM_STATUS = 6, SM_TILECTR = 7,
-       SM_N = 8, SM_TOTALS = 16, SM_WORDS = 16 + 4 * 256 };
+       SM_N = 8, SM_NINST = 9, SM_TOTALS = 16, SM_WORDS = 16 + 4 * 256 };
 uint32_t *small_ptr(tsplat_ctx *c, int w) { return c->small.as<uint32_t>() + w; }
 }  // namespace
 
@@ -150,8 +150,21 @@ void gaussians_store(tsplat_gaussians *g, GaussianStore &out, cudaStream_t write
     out.n_dev = g->n_dev.as<uint32_t>();
     g->last_stream = writer;
 }
+void gaussians_peek(const tsplat_gaussians *g, GaussianStore &out, cudaStream_t *last_writer) {
+    out.cap = g->cap;
+    out.C = g->C;
+    out.dtype = g->dtype;
+    out.xyzo = g->xyzo.as<float4>();
+    out.cova = g->cova.as<float4>();
+    out.covb = g->covb.as<float2>();
+    out.feat = g->feat.p;
+    out.n_dev = g->n_dev.as<uint32_t>();
+    if (last_writer) *last_writer = g->last_stream;
+}
 tsplat_status record_error(tsplat_status st, const char *msg) { return fail(st, "%s", msg); }
 }  // namespace tsp
+
+
 
 extern "C" {
 
@@ -322,7 +335,7 @@ tsplat_status tsplat_ctx_destroy(tsplat_ctx *c) {
     cudaDeviceSynchronize();
     DBuf *bufs[] = {&c->hdr, &c->rect, &c->ntiles, &c->dkey, &c->radius, &c->skeys0, &c->skeys1, &c->svals0,
                     &c->svals1, &c->hist_n, &c->emit_blk, &c->pk0, &c->pk1, &c->pv0, &c->pv1, &c->hist_p,
-                    &c->ranges, &c->tfinal, &c->last, &c->small};
+                    &c->ranges, &c->tfinal, &c->last, &c->views, &c->small};
     for (DBuf *b : bufs) release(*b);
     for (auto &row : c->ev)
         for (cudaEvent_t e : row)
@@ -364,6 +377,7 @@ static tsplat_status ensure_p(tsplat_ctx *c, int64_t p, cudaStream_t s) {
 
 static tsplat_status ensure_pix(tsplat_ctx *c, int W, int H, int n_tiles, bool save, cudaStream_t s) {
     TRY(grow(c->ranges, (size_t)std::max(n_tiles, 1) * 8, s));
+    TRY(grow(c->views, sizeof(RenderView) * MAX_BATCH, s));
     if (save) {
         TRY(grow(c->tfinal, (size_t)W * H * 4, s));
         TRY(grow(c->last, (size_t)W * H * 4, s));
@@ -395,14 +409,24 @@ static tsplat_status mark(tsplat_ctx *c, bool prof, int i, cudaStream_t s) {
 }
 
 // A2 (done by the caller of this function) .. A7
-static tsplat_status render_tail(tsplat_ctx *c, int64_t n_cap, const uint32_t *n_dev, const void *feat, int C,
-                                 int dtype, int W, int H, const tsplat_render_params &par, float *out_feat,
-                                 float *out_alpha, cudaStream_t s) {
-    const int tiles_x = (W + TILE - 1) / TILE, tiles_y = (H + TILE - 1) / TILE, n_tiles = tiles_x * tiles_y;
+// n_cap: Gaussian count bound (grid sizing); n_dev: Gaussian count N on
+// the device; the render has n_views * N instances (instance i = view * N + id).
+static tsplat_status render_tail(tsplat_ctx *c, int64_t n_cap, const uint32_t *n_dev,
+                                 const ViewBatch &vb, const void *feat, int C, int dtype,
+                                 const tsplat_render_params &par, cudaStream_t s) {
+    const int n_tiles = (int)vb.n_tiles_total;
+    const int W = vb.v[0].width, H = vb.v[0].height;
+    const int tiles_x = vb.v[0].tiles_x, tiles_y = vb.v[0].tiles_y;
     const bool async_mode = (par.flags & TSPLAT_RENDER_ASYNC) != 0;
     const bool save = (par.flags & TSPLAT_RENDER_SAVE) != 0;
     const bool prof = (par.flags & TSPLAT_RENDER_PROFILE) != 0;
     uint32_t *sm = c->small.as<uint32_t>();
+    const int64_t inst_cap = n_cap * vb.n_views;
+    const uint32_t *n_inst = n_dev;
+    if (vb.n_views > 1) {
+        launch_scale_u32(n_dev, (uint32_t)vb.n_views, sm + SM_NINST, s);
+        n_inst = sm + SM_NINST;
+    }
     TRY(mark(c, prof, 1, s));
 
     // depth order of the Gaussians (radix passes only over the differing bytes)
@@ -415,12 +439,12 @@ static tsplat_status render_tail(tsplat_ctx *c, int64_t n_cap, const uint32_t *n
     ds.keys[1] = c->skeys1.as<uint32_t>();
     ds.vals[0] = c->svals0.as<uint32_t>();
     ds.vals[1] = c->svals1.as<uint32_t>();
-    ds.n_dev = n_dev;
+    ds.n_dev = n_inst;
     ds.npass_dev = sm + SM_NPASS;
     ds.kmin = sm + SM_KMIN;
     ds.hist = c->hist_n.as<uint32_t>();
     ds.totals = sm + SM_TOTALS;
-    ds.nblocks = (int)((std::max<int64_t>(n_cap, 1) + RS_TILE - 1) / RS_TILE);
+    ds.nblocks = (int)((std::max<int64_t>(inst_cap, 1) + RS_TILE - 1) / RS_TILE);
     launch_radix_sort(ds, 4, s);
     TRY(mark(c, prof, 2, s));
 
@@ -431,12 +455,12 @@ static tsplat_status render_tail(tsplat_ctx *c, int64_t n_cap, const uint32_t *n
     em.order.vals[0] = ds.vals[0];
     em.order.vals[1] = ds.vals[1];
     em.order.npass_dev = sm + SM_NPASS;
-    em.n_dev = n_dev;
-    em.n_cap = n_cap;
+    em.n_dev = n_inst;
+    em.n_cap = inst_cap;
     em.ntiles = c->ntiles.as<uint32_t>();
     em.rect = c->rect.as<uint2>();
-    em.tiles_x = tiles_x;
-    em.tile_base = 0;
+    em.views = c->views.as<RenderView>();
+    em.n_stride = n_dev;
     em.blk_sum = c->emit_blk.as<uint32_t>();
     em.p_dev = sm + SM_P;
     em.status = sm + SM_STATUS;
@@ -490,22 +514,18 @@ static tsplat_status render_tail(tsplat_ctx *c, int64_t n_cap, const uint32_t *n
     ca.ids = ids_sorted;
     ca.hdr = c->hdr.as<Header>();
     ca.feat = feat;
+    ca.n_stride = n_dev;
     ca.C = C;
     ca.feat_dtype = dtype;
-    ca.W = W;
-    ca.H = H;
-    ca.tiles_x = tiles_x;
-    ca.tiles_y = tiles_y;
+    ca.views = c->views.as<RenderView>();
+    ca.n_views = vb.n_views;
+    ca.n_tiles_total = vb.n_tiles_total;
     ca.alpha_max = par.alpha_max;
     ca.alpha_min = par.alpha_min;
     ca.t_min = par.t_min;
     ca.log2_alpha_min = (float)log2((double)par.alpha_min);
     ca.status = sm + SM_STATUS;
     ca.tile_counter = sm + SM_TILECTR;
-    ca.out_feat = out_feat;
-    ca.out_alpha = out_alpha;
-    ca.out_T = save ? c->tfinal.as<float>() : nullptr;
-    ca.out_last = save ? c->last.as<uint32_t>() : nullptr;
     launch_composite(ca, s);
     TRY(check_launch("render: composite"));
     TRY(mark(c, prof, 6, s));
@@ -530,6 +550,35 @@ static tsplat_status check_common(tsplat_ctx *c, int W, int H, int C, int dtype,
     if (C < 1 || C > 64) return fail(TSPLAT_ERR_INVALID_ARG, "render: C = %d", C);
     if (dtype != TSPLAT_F32 && dtype != TSPLAT_BF16) return fail(TSPLAT_ERR_INVALID_ARG, "render: feat_dtype %d", dtype);
     return TSPLAT_OK;
+}
+
+static RenderView make_view(const tsplat_camera &cam, uint32_t tile_base, float *out_feat, float *out_alpha,
+                            float *out_T, uint32_t *out_last) {
+    RenderView v;
+    memset(&v, 0, sizeof(v));
+    v.cam = cam;
+    v.tile_base = tile_base;
+    v.tiles_x = (cam.width + TILE - 1) / TILE;
+    v.tiles_y = (cam.height + TILE - 1) / TILE;
+    v.width = cam.width;
+    v.height = cam.height;
+    v.out_feat = out_feat;
+    v.out_alpha = out_alpha;
+    v.out_T = out_T;
+    v.out_last = out_last;
+    return v;
+}
+
+static ProjectOut project_out(tsplat_ctx *c) {
+    ProjectOut o;
+    o.hdr = c->hdr.as<Header>();
+    o.rect = c->rect.as<uint2>();
+    o.ntiles = c->ntiles.as<uint32_t>();
+    o.dkey = c->dkey.as<uint32_t>();
+    o.radius = c->radius.as<float>();
+    o.kminmax = small_ptr(c, SM_KMIN);
+    o.n_vis = small_ptr(c, SM_NVIS);
+    return o;
 }
 
 static void init_small(tsplat_ctx *c, cudaStream_t s) {
@@ -557,20 +606,71 @@ tsplat_status tsplat_render(const tsplat_gaussians *g, const tsplat_camera *cam,
     }
     init_small(ctx, s);
     TRY(mark(ctx, (params->flags & TSPLAT_RENDER_PROFILE) != 0, 0, s));
-    ProjectOut o;
-    o.hdr = ctx->hdr.as<Header>();
-    o.rect = ctx->rect.as<uint2>();
-    o.ntiles = ctx->ntiles.as<uint32_t>();
-    o.dkey = ctx->dkey.as<uint32_t>();
-    o.radius = ctx->radius.as<float>();
-    o.kminmax = small_ptr(ctx, SM_KMIN);
-    o.n_vis = small_ptr(ctx, SM_NVIS);
+    const bool save = (params->flags & TSPLAT_RENDER_SAVE) != 0;
+    ViewBatch vb;
+    memset(&vb, 0, sizeof(vb));
+    vb.n_views = 1;
+    vb.n_tiles_total = (uint32_t)(tiles_x * tiles_y);
+    vb.v[0] = make_view(*cam, 0, out_feat, out_alpha, save ? ctx->tfinal.as<float>() : nullptr,
+                        save ? ctx->last.as<uint32_t>() : nullptr);
+    ProjectOut o = project_out(ctx);
     launch_project(g->xyzo.as<float4>(), g->cova.as<float4>(), g->covb.as<float2>(), g->n_dev.as<uint32_t>(), g->cap,
-                   *cam, *params, tiles_x, tiles_y, o, s);
+                   vb, ctx->views.as<RenderView>(), *params, o, s);
     TRY(check_launch("render: project"));
-    return render_tail(ctx, g->cap, g->n_dev.as<uint32_t>(), g->feat.p, g->C, g->dtype, W, H, *params, out_feat,
-                       out_alpha, s);
+    return render_tail(ctx, g->cap, g->n_dev.as<uint32_t>(), vb, g->feat.p, g->C, g->dtype, *params, s);
 }
+
+tsplat_status tsplat_render_batch(const tsplat_gaussians *g, const tsplat_camera *cams, int32_t n_views,
+                                  const tsplat_render_params *params, float *const *out_feat,
+                                  float *const *out_alpha, tsplat_ctx *ctx, void *stream) {
+    return render_batch_impl(g, cams, n_views, params, out_feat, out_alpha, ctx, stream, false);
+}
+}  // extern "C"
+
+namespace tsp {
+void make_view_batch(const tsplat_camera *cams, int32_t n_views, float *const *out_feat, float *const *out_alpha,
+                     ViewBatch &vb) {
+    memset(&vb, 0, sizeof(vb));
+    vb.n_views = n_views;
+    uint32_t tiles = 0;
+    for (int v = 0; v < n_views; ++v) {
+        vb.v[v] = make_view(cams[v], tiles, out_feat[v], out_alpha ? out_alpha[v] : nullptr, nullptr, nullptr);
+        tiles += (uint32_t)(vb.v[v].tiles_x * vb.v[v].tiles_y);
+    }
+    vb.n_tiles_total = tiles;
+}
+
+tsplat_status render_batch_impl(const tsplat_gaussians *g, const tsplat_camera *cams, int32_t n_views,
+                                const tsplat_render_params *params, float *const *out_feat,
+                                float *const *out_alpha, tsplat_ctx *ctx, void *stream, bool table_on_device) {
+    if (!g || !cams || !out_feat) return fail(TSPLAT_ERR_INVALID_ARG, "render_batch: NULL argument");
+    if (n_views < 1 || n_views > MAX_BATCH) return fail(TSPLAT_ERR_INVALID_ARG, "render_batch: n_views = %d not in [1, %d]", n_views, MAX_BATCH);
+    if (params && (params->flags & TSPLAT_RENDER_SAVE)) return fail(TSPLAT_ERR_UNSUPPORTED, "render_batch: TSPLAT_RENDER_SAVE is single-view only");
+    for (int v = 0; v < n_views; ++v)
+        TRY(check_common(ctx, cams[v].width, cams[v].height, g->C, g->dtype, params, out_feat[v]));
+    ViewBatch vb;
+    make_view_batch(cams, n_views, out_feat, out_alpha, vb);
+    const uint32_t tiles = vb.n_tiles_total;
+    cudaStream_t s = S(stream);
+    const int64_t inst = std::max<int64_t>(g->cap, 1) * n_views;
+    if (params->flags & TSPLAT_RENDER_ASYNC) {
+        if (ctx->hdr.bytes < (size_t)inst * sizeof(Header) || ctx->ranges.bytes < (size_t)tiles * 8)
+            return fail(TSPLAT_ERR_CAPACITY, "render_batch: TSPLAT_RENDER_ASYNC needs tsplat_ctx_reserve for these sizes");
+    } else {
+        TRY(ensure_n(ctx, inst, s));
+        TRY(ensure_pix(ctx, 0, 0, (int)tiles, false, s));
+    }
+    init_small(ctx, s);
+    TRY(mark(ctx, (params->flags & TSPLAT_RENDER_PROFILE) != 0, 0, s));
+    ProjectOut o = project_out(ctx);
+    launch_project(g->xyzo.as<float4>(), g->cova.as<float4>(), g->covb.as<float2>(), g->n_dev.as<uint32_t>(), g->cap,
+                   vb, ctx->views.as<RenderView>(), *params, o, s, table_on_device);
+    TRY(check_launch("render_batch: project"));
+    return render_tail(ctx, g->cap, g->n_dev.as<uint32_t>(), vb, g->feat.p, g->C, g->dtype, *params, s);
+}
+}  // namespace tsp
+
+extern "C" {
 
 tsplat_status tsplat_rasterize(int64_t n, const float *mean2d, const float *conic, const float *opac,
                                const float *depth, const int32_t *radius, const void *feat, int32_t C,
@@ -595,17 +695,21 @@ tsplat_status tsplat_rasterize(int64_t n, const float *mean2d, const float *coni
     init_small(ctx, s);
     launch_fill_u32(small_ptr(ctx, SM_N), (uint32_t)n, 1, s);
     TRY(mark(ctx, (params->flags & TSPLAT_RENDER_PROFILE) != 0, 0, s));
-    ProjectOut o;
-    o.hdr = ctx->hdr.as<Header>();
-    o.rect = ctx->rect.as<uint2>();
-    o.ntiles = ctx->ntiles.as<uint32_t>();
-    o.dkey = ctx->dkey.as<uint32_t>();
-    o.radius = ctx->radius.as<float>();
-    o.kminmax = small_ptr(ctx, SM_KMIN);
-    o.n_vis = small_ptr(ctx, SM_NVIS);
-    launch_prepare_2d(n, mean2d, conic, opac, depth, radius, *params, tiles_x, tiles_y, o, s);
+    const bool save = (params->flags & TSPLAT_RENDER_SAVE) != 0;
+    tsplat_camera cam;
+    memset(&cam, 0, sizeof(cam));
+    cam.width = width;
+    cam.height = height;
+    ViewBatch vb;
+    memset(&vb, 0, sizeof(vb));
+    vb.n_views = 1;
+    vb.n_tiles_total = (uint32_t)(tiles_x * tiles_y);
+    vb.v[0] = make_view(cam, 0, out_feat, out_alpha, save ? ctx->tfinal.as<float>() : nullptr,
+                        save ? ctx->last.as<uint32_t>() : nullptr);
+    ProjectOut o = project_out(ctx);
+    launch_prepare_2d(n, mean2d, conic, opac, depth, radius, *params, vb, ctx->views.as<RenderView>(), o, s);
     TRY(check_launch("rasterize: prepare"));
-    return render_tail(ctx, n, small_ptr(ctx, SM_N), feat, C, feat_dtype, width, height, *params, out_feat, out_alpha, s);
+    return render_tail(ctx, n, small_ptr(ctx, SM_N), vb, feat, C, feat_dtype, *params, s);
 }
 
 tsplat_status tsplat_backward(tsplat_ctx *c, const float *dL_dfeat, const float *dL_dalpha, float *d_mean2d,
@@ -733,3 +837,17 @@ tsplat_status tsplat_ctx_export(tsplat_ctx *c, int32_t what, void *dst, size_t b
 }
 
 }  // extern "C"
+
+namespace tsp {
+tsplat_status ctx_reserve_batch(tsplat_ctx *c, int64_t instances, int64_t pairs, int64_t tiles) {
+    TRY(ensure_n(c, instances, nullptr));
+    TRY(ensure_p(c, pairs, nullptr));
+    TRY(grow(c->ranges, (size_t)std::max<int64_t>(tiles, 1) * 8, nullptr));
+    TRY(grow(c->views, sizeof(RenderView) * MAX_BATCH, nullptr));
+    TRY_CUDA(cudaStreamSynchronize(nullptr));
+    return TSPLAT_OK;
+}
+RenderView *ctx_view_table(tsplat_ctx *c) { return c->views.as<RenderView>(); }
+int64_t ctx_pair_capacity(const tsplat_ctx *c) { return c->p_cap; }
+uint32_t *ctx_status_word(tsplat_ctx *c) { return small_ptr(c, SM_STATUS); }
+}  // namespace tsp

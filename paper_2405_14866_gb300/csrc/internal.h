@@ -52,6 +52,29 @@ void launch_gaussians_get(const uint32_t *n_dev, int64_t cap, int C, int dtype, 
                           const float4 *cova, const float2 *covb, const void *feat_in, float *mean,
                           float *cov, float *opac, void *feat_out, cudaStream_t s);
 
+// ------------------------------------------------------------ view table
+// One target view of a (possibly batched) render.  Its tiles occupy the
+// global tile ids [tile_base, tile_base + tiles_x * tiles_y).
+constexpr int MAX_BATCH = 8;
+struct RenderView {
+    tsplat_camera cam;
+    uint32_t tile_base;
+    int32_t tiles_x, tiles_y;
+    int32_t width, height;
+    int32_t pad_;
+    float *out_feat;      // C x H x W
+    float *out_alpha;     // H x W, may be NULL
+    float *out_T;         // H x W, may be NULL
+    uint32_t *out_last;   // H x W, may be NULL
+};
+// The table travels by value as a parameter of the first kernel of a render,
+// which copies it to device memory for the kernels after it.
+struct ViewBatch {
+    RenderView v[MAX_BATCH];
+    int32_t n_views;
+    uint32_t n_tiles_total;
+};
+
 // --------------------------------------------------------------- A2 project
 struct ProjectOut {
     Header *hdr;        // [N]
@@ -62,14 +85,16 @@ struct ProjectOut {
     uint32_t *kminmax;  // [2] min / max depth key of rendered Gaussians (pre-set to ~0u / 0)
     uint32_t *n_vis;    // [1] rendered Gaussians (pre-set to 0)
 };
+// Instances: view v's copy of Gaussian g is instance v * N + g, N = *n_dev
+// (n_cap >= N bounds the grid).  Also writes the view table to views_dev.
 void launch_project(const float4 *xyzo, const float4 *cova, const float2 *covb,
-                    const uint32_t *n_dev, int64_t n_cap, const tsplat_camera &cam,
-                    const tsplat_render_params &par, int tiles_x, int tiles_y,
-                    const ProjectOut &o, cudaStream_t s);
-// Same outputs from already projected 2D Gaussians (tsplat_rasterize).
+                    const uint32_t *n_dev, int64_t n_cap, const ViewBatch &vb, RenderView *views_dev,
+                    const tsplat_render_params &par, const ProjectOut &o, cudaStream_t s,
+                    bool table_on_device = false);
+// Same outputs from already projected 2D Gaussians (tsplat_rasterize, one view).
 void launch_prepare_2d(int64_t n, const float *mean2d, const float *conic, const float *opac,
                        const float *depth, const int32_t *radius, const tsplat_render_params &par,
-                       int tiles_x, int tiles_y, const ProjectOut &o, cudaStream_t s);
+                       const ViewBatch &vb, RenderView *views_dev, const ProjectOut &o, cudaStream_t s);
 
 // ------------------------------------------------------ A3..A6 sort / bins
 constexpr int RS_THREADS = 256;
@@ -116,8 +141,8 @@ struct EmitArgs {
     int64_t n_cap;
     const uint32_t *ntiles;
     const uint2 *rect;
-    int tiles_x;
-    uint32_t tile_base;        // added to tile ids (batched views)
+    const RenderView *views;   // instance i belongs to view i / N
+    const uint32_t *n_stride;  // N (device)
     uint32_t *blk_sum;         // [nblocks]
     uint32_t *p_dev;           // total pairs (output)
     uint32_t *pair_tile;       // [P_cap]
@@ -134,21 +159,20 @@ void launch_ranges(const uint32_t *tiles_sorted, const uint32_t *p_dev, int64_t 
 
 // ------------------------------------------------------------ A7 composite
 struct CompositeArgs {
-    const uint2 *ranges;
-    const uint32_t *ids;
-    const Header *hdr;
-    const void *feat;
+    const uint2 *ranges;       // per global tile
+    const uint32_t *ids;       // sorted pairs: instance ids
+    const Header *hdr;         // per instance
+    const void *feat;          // per Gaussian (instance % N)
+    const uint32_t *n_stride;  // N (device)
     int C;
     int feat_dtype;
-    int W, H, tiles_x, tiles_y;
+    const RenderView *views;   // device view table
+    int n_views;
+    uint32_t n_tiles_total;
     float alpha_max, alpha_min, t_min;
     float log2_alpha_min;  // blend test: log2(o) + q log2(e) >= log2(alpha_min)
     uint32_t *status;      // TSPLAT_ERR_TIMEOUT if a bounded wait expired
     uint32_t *tile_counter;  // next tile to hand out (0 at launch)
-    float *out_feat;
-    float *out_alpha;
-    float *out_T;        // may be NULL
-    uint32_t *out_last;  // may be NULL
 };
 void launch_composite(const CompositeArgs &a, cudaStream_t s);
 
@@ -188,11 +212,31 @@ struct GaussianStore {
     uint32_t *n_dev;
 };
 void gaussians_store(tsplat_gaussians *g, GaussianStore &out, cudaStream_t writer);
+// Read-only view of the store; *last_writer = the stream that last wrote it.
+void gaussians_peek(const tsplat_gaussians *g, GaussianStore &out, cudaStream_t *last_writer);
 // Record the thread-local message returned by tsplat_last_error; returns st.
 tsplat_status record_error(tsplat_status st, const char *msg);
 
+// Serving support: size a context for batched renders (instances, pairs,
+// tiles over all views); its device view table; its pair capacity and
+// status word.
+tsplat_status ctx_reserve_batch(tsplat_ctx *c, int64_t instances, int64_t pairs, int64_t tiles);
+RenderView *ctx_view_table(tsplat_ctx *c);
+int64_t ctx_pair_capacity(const tsplat_ctx *c);
+uint32_t *ctx_status_word(tsplat_ctx *c);  // device word written by the kernels of a render
+// tsplat_render_batch; with table_on_device the projection reads the view
+// table from ctx_view_table(ctx), written there by the caller before the
+// launch (so that a captured graph can be replayed for other views).
+tsplat_status render_batch_impl(const tsplat_gaussians *g, const tsplat_camera *cams, int32_t n_views,
+                                const tsplat_render_params *params, float *const *out_feat,
+                                float *const *out_alpha, tsplat_ctx *ctx, void *stream, bool table_on_device);
+// The view table of a batch: views laid out in order, tile ids concatenated.
+void make_view_batch(const tsplat_camera *cams, int32_t n_views, float *const *out_feat, float *const *out_alpha,
+                     ViewBatch &vb);
+
 // small utilities
 void launch_fill_u32(uint32_t *p, uint32_t v, int64_t n, cudaStream_t s);
+void launch_scale_u32(const uint32_t *src, uint32_t k, uint32_t *dst, cudaStream_t s);  // *dst = *src * k
 // *dst = *src if it fits in cap, else 0 (an overflowing render emits no pairs)
 void launch_pairs_effective(const uint32_t *src, uint32_t cap, uint32_t *dst, cudaStream_t s);
 void launch_zero_f32_n(float *p, const uint32_t *n_dev, int mult, int64_t n_cap, cudaStream_t s);  // p[0 .. n*mult)

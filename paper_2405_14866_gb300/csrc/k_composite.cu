@@ -65,6 +65,7 @@ struct CompSmem {
     uint32_t base[RING];       // list position of the slot's first Gaussian
     int32_t done_seq[NCW];     // per consumer warp: sequence number of the last tile it is done with
     uint8_t list[NCW][SB];     // per consumer warp: slot indices of its surviving Gaussians, in order
+    RenderView views[MAX_BATCH];
 };
 
 __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
@@ -77,16 +78,17 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
 // and zero-padded by the producer lane itself.
 template <int CP, bool F32F>
 __device__ __forceinline__ void produce_one(CompSmem<CP, F32F> &S, const CompositeArgs &a, int slot, int k,
-                                            uint32_t id) {
+                                            uint32_t id, uint32_t ns) {
     const uint4 *hs = reinterpret_cast<const uint4 *>(a.hdr + id);
     cp_async16(&S.hdr[slot][k], hs);
     cp_async16(reinterpret_cast<char *>(&S.hdr[slot][k]) + 16, hs + 1);
+    const size_t gi = id % ns;  // features are stored once per Gaussian, records per (view, Gaussian)
     if (!F32F && a.C == CP) {
-        const uint4 *fs = reinterpret_cast<const uint4 *>(reinterpret_cast<const __nv_bfloat16 *>(a.feat) + (size_t)id * CP);
+        const uint4 *fs = reinterpret_cast<const uint4 *>(reinterpret_cast<const __nv_bfloat16 *>(a.feat) + gi * CP);
 #pragma unroll
         for (int c = 0; c < CP / 8; ++c) cp_async16(&S.fhi[slot][k][8 * c], fs + c);
     } else if (F32F) {
-        const float *src = reinterpret_cast<const float *>(a.feat) + (size_t)id * a.C;
+        const float *src = reinterpret_cast<const float *>(a.feat) + gi * a.C;
 #pragma unroll 4
         for (int c = 0; c < CP; c += 2) {
             const float v0 = c < a.C ? __ldg(src + c) : 0.0f;
@@ -97,7 +99,7 @@ __device__ __forceinline__ void produce_one(CompSmem<CP, F32F> &S, const Composi
             *reinterpret_cast<uint32_t *>(&S.flo[F32F ? slot : 0][F32F ? k : 0][c]) = lo;
         }
     } else {
-        const __nv_bfloat16 *src = reinterpret_cast<const __nv_bfloat16 *>(a.feat) + (size_t)id * a.C;
+        const __nv_bfloat16 *src = reinterpret_cast<const __nv_bfloat16 *>(a.feat) + gi * a.C;
         for (int c = 0; c < CP; ++c) S.fhi[slot][k][c] = c < a.C ? src[c] : __float2bfloat16_rn(0.0f);
     }
 }
@@ -112,7 +114,11 @@ __device__ __forceinline__ void produce_one(CompSmem<CP, F32F> &S, const Composi
 template <int CP, bool F32F>
 __device__ void producer(CompSmem<CP, F32F> &S, const CompositeArgs &a, int lane) {
     constexpr int RING = CompSmem<CP, F32F>::RING;
-    const uint32_t n_tiles = (uint32_t)(a.tiles_x * a.tiles_y);
+    // the tile count comes from the view table in device memory, so a replayed
+    // graph may render a different mix of view sizes
+    const RenderView &lastv = S.views[a.n_views - 1];
+    const uint32_t n_tiles = lastv.tile_base + (uint32_t)(lastv.tiles_x * lastv.tiles_y);
+    const uint32_t ns = *a.n_stride;
     uint32_t i = 0;  // slots produced so far (ring position and phase)
     bool timed_out = false;
     for (int32_t seq = 0;; ++seq) {
@@ -145,8 +151,8 @@ __device__ void producer(CompSmem<CP, F32F> &S, const CompositeArgs &a, int lane
                 const int nb = b + SB;
                 nid0 = nb + lane < n ? a.ids[first + nb + lane] : 0u;
                 nid1 = nb + lane + 32 < n ? a.ids[first + nb + lane + 32] : 0u;
-                if (lane < cnt) produce_one<CP, F32F>(S, a, slot, lane, id0);
-                if (lane + 32 < cnt) produce_one<CP, F32F>(S, a, slot, lane + 32, id1);
+                if (lane < cnt) produce_one<CP, F32F>(S, a, slot, lane, id0, ns);
+                if (lane + 32 < cnt) produce_one<CP, F32F>(S, a, slot, lane + 32, id1, ns);
             }
             // every lane, every slot: counts against the barrier's expected
             // arrivals (.noinc) and fires once this lane's copies have landed
@@ -194,6 +200,7 @@ __global__ __launch_bounds__(NTHR, 2) void k_composite(CompositeArgs a) {
         mbar_init_fence();
     }
     if (tid < NCW) S.done_seq[tid] = -1;
+    if (tid < a.n_views) S.views[tid] = a.views[tid];
     for (int c = tid; c < CP; c += NTHR) S.zero[c] = __float2bfloat16_rn(0.0f);
     __syncthreads();
 
@@ -204,7 +211,6 @@ __global__ __launch_bounds__(NTHR, 2) void k_composite(CompositeArgs a) {
 
     // ---------------------------------------------------------- consumers
     const float amax = a.alpha_max, l2min = a.log2_alpha_min, tmin = a.t_min;
-    const size_t HW = (size_t)a.W * a.H;
     // ldmatrix address pattern: lane supplies row (lane & 7) of matrix lane / 8
     const int kl = ((lane >> 3) & 1) * 8 + (lane & 7);  // group entry whose B row this lane addresses
     const int arow = kl, acol = (lane >> 4) * 8, bcol = (lane >> 4) * 8;
@@ -215,6 +221,7 @@ __global__ __launch_bounds__(NTHR, 2) void k_composite(CompositeArgs a) {
     uint32_t last = 0;
     bool done = true, wdone = true;
     int bx0 = 0, by0 = 0;          // this warp's 8x4 block in the current tile
+    int cv = 0, W = 0, H = 0;      // view of the current tile and its size
     float fpx = 0.f, fpy = 0.f;    // this lane's pixel centre
     uint32_t cur = FINAL_TILE;     // tile in progress
     int32_t seq = -1;
@@ -231,7 +238,12 @@ __global__ __launch_bounds__(NTHR, 2) void k_composite(CompositeArgs a) {
         if (t != cur) {  // first slot of a new tile: reset the per-pixel state
             cur = t;
             ++seq;
-            const int tx = (int)(t % (uint32_t)a.tiles_x), ty = (int)(t / (uint32_t)a.tiles_x);
+            cv = 0;
+            for (int k = 1; k < a.n_views; ++k) cv = t >= S.views[k].tile_base ? k : cv;
+            const uint32_t local = t - S.views[cv].tile_base;
+            W = S.views[cv].width;
+            H = S.views[cv].height;
+            const int tx = (int)(local % (uint32_t)S.views[cv].tiles_x), ty = (int)(local / (uint32_t)S.views[cv].tiles_x);
             bx0 = tx * TILE + (warp & 1) * 8;
             by0 = ty * TILE + (warp >> 1) * 4;
             fpx = (float)(bx0 + (lane & 7));
@@ -244,21 +256,23 @@ __global__ __launch_bounds__(NTHR, 2) void k_composite(CompositeArgs a) {
                     for (int e = 0; e < 4; ++e) acc[m][u][e] = 0.0f;
             T = 1.0f;
             last = 0;
-            done = !(bx0 + (lane & 7) < a.W && by0 + (lane >> 3) < a.H);
+            done = !(bx0 + (lane & 7) < W && by0 + (lane >> 3) < H);
             wdone = __all_sync(FULL, done);
             if (wdone && lane == 0) *reinterpret_cast<volatile int32_t *>(&S.done_seq[warp]) = seq;
         }
         if (cnt == 0) {
             // end of the tile: write this warp's block (the accumulator of lane l
             // holds pixels l/4 (+8, +16, +24) and channels 8u + 2(l%4) (+1))
+            const RenderView &vw = S.views[cv];
+            const size_t HW = (size_t)W * H;
 #pragma unroll
             for (int m = 0; m < 2; ++m)
 #pragma unroll
                 for (int hh = 0; hh < 2; ++hh) {
                     const int p = m * 16 + hh * 8 + (lane >> 2);
                     const int x = bx0 + (p & 7), y = by0 + (p >> 3);
-                    if (x < a.W && y < a.H) {
-                        float *dst = a.out_feat + (size_t)y * a.W + x;
+                    if (x < W && y < H) {
+                        float *dst = vw.out_feat + (size_t)y * W + x;
 #pragma unroll
                         for (int u = 0; u < NT8; ++u) {
                             const int c = u * 8 + 2 * (lane & 3);
@@ -268,11 +282,11 @@ __global__ __launch_bounds__(NTHR, 2) void k_composite(CompositeArgs a) {
                     }
                 }
             const int px = bx0 + (lane & 7), py = by0 + (lane >> 3);
-            if (px < a.W && py < a.H) {
-                const size_t pix = (size_t)py * a.W + px;
-                if (a.out_alpha) a.out_alpha[pix] = 1.0f - T;
-                if (a.out_T) a.out_T[pix] = T;
-                if (a.out_last) a.out_last[pix] = last;
+            if (px < W && py < H) {
+                const size_t pix = (size_t)py * W + px;
+                if (vw.out_alpha) vw.out_alpha[pix] = 1.0f - T;
+                if (vw.out_T) vw.out_T[pix] = T;
+                if (vw.out_last) vw.out_last[pix] = last;
             }
             if (lane == 0) *reinterpret_cast<volatile int32_t *>(&S.done_seq[warp]) = seq;
             cur = FINAL_TILE;
@@ -576,7 +590,7 @@ void run_composite(const CompositeArgs &a, cudaStream_t s) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_composite<CP, F32F>, NTHR, smem);
         grid = std::max(1, sms) * std::max(1, per_sm);
     }
-    k_composite<CP, F32F><<<std::min(grid, std::max(1, a.tiles_x * a.tiles_y)), NTHR, smem, s>>>(a);
+    k_composite<CP, F32F><<<std::min(grid, std::max(1, (int)a.n_tiles_total)), NTHR, smem, s>>>(a);
     note_launches(1);
 }
 
@@ -595,7 +609,7 @@ void run_backward(const BackwardArgs &a, cudaStream_t s) {
 }  // namespace
 
 void launch_composite(const CompositeArgs &a, cudaStream_t s) {
-    if (a.tiles_x * a.tiles_y == 0) return;
+    if (a.n_tiles_total == 0) return;
     const bool f32 = a.feat_dtype == TSPLAT_F32;
     if (a.C <= 16) { if (f32) run_composite<16, true>(a, s); else run_composite<16, false>(a, s); }
     else if (a.C <= 32) { if (f32) run_composite<32, true>(a, s); else run_composite<32, false>(a, s); }

@@ -6,6 +6,9 @@
 // operation at a time (__f*_rn), in a fixed order, so that an independent
 // implementation following the same order obtains the same bits.
 #include <math.h>
+#include <string.h>
+
+#include <algorithm>
 
 #include "common.cuh"
 #include "internal.h"
@@ -92,18 +95,33 @@ __device__ __forceinline__ int tile_rect(float mx, float my, float r, int tiles_
     return (x1 - x0) * (y1 - y0);
 }
 
+// Copy the view table to device memory for the kernels after this one.
+__device__ __forceinline__ void publish_views(const ViewBatch &vb, RenderView *views_dev) {
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x < (unsigned)vb.n_views) views_dev[threadIdx.x] = vb.v[threadIdx.x];
+}
+
+// grid (ceil(n_cap / 256), n_views): view blockIdx.y, Gaussian gi;
+// instance i = view * N + gi.
 __global__ __launch_bounds__(256) void k_project(const float4 *__restrict__ xyzo,
                                                  const float4 *__restrict__ cova,
                                                  const float2 *__restrict__ covb,
-                                                 const uint32_t *n_dev, tsplat_camera cam,
-                                                 tsplat_render_params par, int tiles_x, int tiles_y,
-                                                 ProjectOut o) {
-    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool active = i < (uint64_t)*n_dev;
+                                                 const uint32_t *n_dev,
+                                                 const __grid_constant__ ViewBatch vb, RenderView *views_dev,
+                                                 int table_on_device, tsplat_render_params par, ProjectOut o) {
+    // the view table comes with the launch and is published for the later
+    // kernels, or (graph replays) it is already in device memory
+    if (!table_on_device) publish_views(vb, views_dev);
+    const RenderView &view = table_on_device ? views_dev[blockIdx.y] : vb.v[blockIdx.y];
+    const tsplat_camera &cam = view.cam;
+    const int tiles_x = view.tiles_x, tiles_y = view.tiles_y;
+    const uint64_t n = *n_dev;
+    const uint64_t gi = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t i = (uint64_t)blockIdx.y * n + gi;
+    const bool active = gi < n;
     bool vis = false;
     uint32_t key = CULLED_KEY;
     if (active) {
-    const float4 g = xyzo[i];
+    const float4 g = xyzo[gi];
     const float *R = cam.R;
     const float px = fadd(fadd(fadd(fmul(R[0], g.x), fmul(R[1], g.y)), fmul(R[2], g.z)), cam.t[0]);
     const float py = fadd(fadd(fadd(fmul(R[3], g.x), fmul(R[4], g.y)), fmul(R[5], g.z)), cam.t[1]);
@@ -124,8 +142,8 @@ __global__ __launch_bounds__(256) void k_project(const float4 *__restrict__ xyzo
             T0[j] = fadd(fmul(j00, R[0 * 3 + j]), fmul(j02, R[2 * 3 + j]));
             T1[j] = fadd(fmul(j11, R[1 * 3 + j]), fmul(j12, R[2 * 3 + j]));
         }
-        const float4 ca = cova[i];
-        const float2 cb = covb[i];
+        const float4 ca = cova[gi];
+        const float2 cb = covb[gi];
         const float V[3][3] = {{ca.x, ca.y, ca.z}, {ca.y, ca.w, cb.x}, {ca.z, cb.x, cb.y}};
         float U0[3], U1[3];
 #pragma unroll
@@ -175,8 +193,11 @@ __global__ __launch_bounds__(256) void k_prepare_2d(uint64_t n, const float *__r
                                                     const float *__restrict__ opac,
                                                     const float *__restrict__ depth,
                                                     const int32_t *__restrict__ radius,
-                                                    tsplat_render_params par, int tiles_x,
-                                                    int tiles_y, ProjectOut o) {
+                                                    tsplat_render_params par,
+                                                    const __grid_constant__ ViewBatch vb,
+                                                    RenderView *views_dev, ProjectOut o) {
+    publish_views(vb, views_dev);
+    const int tiles_x = vb.v[0].tiles_x, tiles_y = vb.v[0].tiles_y;
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = i < n;
     bool vis = false;
@@ -245,20 +266,18 @@ void launch_export_rect(const uint2 *rect, const uint32_t *n_dev, int64_t n_cap,
 }
 
 void launch_project(const float4 *xyzo, const float4 *cova, const float2 *covb, const uint32_t *n_dev,
-                    int64_t n_cap, const tsplat_camera &cam, const tsplat_render_params &par,
-                    int tiles_x, int tiles_y, const ProjectOut &o, cudaStream_t s) {
-    if (n_cap <= 0) return;
-    k_project<<<(unsigned)((n_cap + 255) / 256), 256, 0, s>>>(xyzo, cova, covb, n_dev, cam, par, tiles_x,
-                                                              tiles_y, o);
+                    int64_t n_cap, const ViewBatch &vb, RenderView *views_dev,
+                    const tsplat_render_params &par, const ProjectOut &o, cudaStream_t s, bool table_on_device) {
+    const dim3 grid((unsigned)std::max<int64_t>(1, (n_cap + 255) / 256), (unsigned)vb.n_views);
+    k_project<<<grid, 256, 0, s>>>(xyzo, cova, covb, n_dev, vb, views_dev, table_on_device ? 1 : 0, par, o);
     note_launches(1);
 }
 
 void launch_prepare_2d(int64_t n, const float *mean2d, const float *conic, const float *opac,
                        const float *depth, const int32_t *radius, const tsplat_render_params &par,
-                       int tiles_x, int tiles_y, const ProjectOut &o, cudaStream_t s) {
-    if (n <= 0) return;
-    k_prepare_2d<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((uint64_t)n, mean2d, conic, opac, depth, radius,
-                                                             par, tiles_x, tiles_y, o);
+                       const ViewBatch &vb, RenderView *views_dev, const ProjectOut &o, cudaStream_t s) {
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, (n + 255) / 256);
+    k_prepare_2d<<<blocks, 256, 0, s>>>((uint64_t)n, mean2d, conic, opac, depth, radius, par, vb, views_dev, o);
     note_launches(1);
 }
 

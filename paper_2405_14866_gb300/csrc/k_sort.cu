@@ -288,18 +288,24 @@ __global__ __launch_bounds__(EM_THREADS) void k_emit_write(EmitArgs a) {
         return;
     }
     const uint64_t n = *a.n_dev;
+    const uint32_t ns = *a.n_stride;
     const int np = sv_passes(a.order);
     const int lane = threadIdx.x & 31;
     uint64_t running = a.blk_sum[blockIdx.x];
     const uint64_t base = (uint64_t)blockIdx.x * EM_TILE;
     for (int r = 0; r < EM_ITEMS; ++r) {
         const uint64_t k = base + (uint64_t)r * EM_THREADS + threadIdx.x;
-        uint32_t id = 0, cnt = 0;
-        int x0 = 0, y0 = 0, x1 = 0, y1 = 0;
+        uint32_t id = 0, cnt = 0, vbase = 0;
+        int x0 = 0, y0 = 0, x1 = 0, y1 = 0, vtx = 0;
         if (k < n) {
             id = sorted_val(a.order, np, k);
             cnt = a.ntiles[id];
-            if (cnt) unpack_rect(a.rect[id], x0, y0, x1, y1);
+            if (cnt) {
+                unpack_rect(a.rect[id], x0, y0, x1, y1);
+                const RenderView &vw = a.views[id / ns];
+                vbase = vw.tile_base;
+                vtx = vw.tiles_x;
+            }
         }
         uint32_t tot;
         const uint32_t excl = block_excl_scan<EM_THREADS / 32>(cnt, sw, tot);
@@ -320,10 +326,12 @@ __global__ __launch_bounds__(EM_THREADS) void k_emit_write(EmitArgs a) {
             const uint32_t so = __shfl_sync(FULL, start, o);
             const int ox0 = __shfl_sync(FULL, x0, o), oy0 = __shfl_sync(FULL, y0, o), ow = __shfl_sync(FULL, w, o);
             const uint32_t oid = __shfl_sync(FULL, id, o);
+            const uint32_t ovb = __shfl_sync(FULL, vbase, o);
+            const int otx = __shfl_sync(FULL, vtx, o);
             if (e < wtot) {
                 const int loc = (int)(e - so);
                 const int ty = oy0 + loc / ow, tx = ox0 + loc % ow;
-                a.pair_tile[wfirst + e] = a.tile_base + (uint32_t)(ty * a.tiles_x + tx);
+                a.pair_tile[wfirst + e] = ovb + (uint32_t)(ty * otx + tx);
                 a.pair_id[wfirst + e] = oid;
             }
         }
@@ -341,6 +349,8 @@ __global__ void k_ranges(const uint32_t *tiles, const uint32_t *p_dev, uint64_t 
     if (k == 0 || tiles[k - 1] != t) ranges[t].x = (uint32_t)k;
     if (k == P - 1 || tiles[k + 1] != t) ranges[t].y = (uint32_t)(k + 1);
 }
+
+__global__ void k_scale_u32(const uint32_t *src, uint32_t k, uint32_t *dst) { *dst = *src * k; }
 
 __global__ void k_fill_u32(uint32_t *p, uint32_t v, uint64_t n) {
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -413,6 +423,11 @@ void launch_zero_f32_n(float *p, const uint32_t *n_dev, int mult, int64_t n_cap,
     if (!p || n_cap <= 0) return;
     const int64_t tot = n_cap * mult;
     k_zero_f32_n<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(p, n_dev, mult);
+    note_launches(1);
+}
+
+void launch_scale_u32(const uint32_t *src, uint32_t k, uint32_t *dst, cudaStream_t s) {
+    k_scale_u32<<<1, 1, 0, s>>>(src, k, dst);
     note_launches(1);
 }
 

@@ -1,0 +1,209 @@
+"""Batched multi-view rendering and the continuous-batching server (A9).
+
+Tele-Aloha renders a left and a right eye view per viewer every frame
+(Sec. 4.2) and runs its pipeline as CUDA graphs (Sec. 5.3).  The batched
+render and the server must give every view exactly the result of rendering
+it alone (bit-identical: the per-tile lists and the per-pixel arithmetic are
+the same), while requests that arrive during other work are batched and
+their batches overlap on the device.
+"""
+import threading
+import time
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2405_14866_gb300 import _lib as L
+from paper_2405_14866_gb300 import api, gen
+from tests import parity as P
+
+pytestmark = pytest.mark.gpu
+
+
+def _frame(seed=41, res=96, C=8):
+    sc = gen.scene_precision(seed=seed, res=res, C=C)
+    g, keep = P.gpu_build(sc)
+    return sc, g, keep
+
+
+def _cams(rng, n, sizes):
+    cams = []
+    for k in range(n):
+        w, h = sizes[k % len(sizes)]
+        eye = np.array([rng.uniform(-0.2, 0.2), rng.uniform(-0.05, 0.05), rng.uniform(-0.1, 0.1)])
+        c = gen.make_camera(float(w), w, h, eye, gen.look_at_c2w(eye, (0.0, 0.0, 1.2)))
+        cams.append(c)
+    return cams
+
+
+def _solo(g, cam, C):
+    ctx = api.Context()
+    F, A = ctx.render(g, cam)
+    torch.cuda.synchronize()
+    return F, A
+
+
+def test_render_batch_equals_single_views():
+    sc, g, keep = _frame()
+    rng = np.random.default_rng(1)
+    cams = _cams(rng, 5, [(64, 64), (80, 48), (96, 96), (64, 100), (32, 32)])
+    ctx = api.Context()
+    Fs, As = ctx.render_batch(g, cams)
+    torch.cuda.synchronize()
+    for cam, F, A in zip(cams, Fs, As):
+        F1, A1 = _solo(g, cam, sc.C)
+        assert torch.equal(F, F1) and torch.equal(A, A1)
+
+
+def test_server_same_result_alone_and_in_the_mix():
+    sc, g, keep = _frame(seed=42)
+    srv = api.Server(max_views_per_batch=4, max_lanes=3, max_width=128, max_height=128,
+                     max_gaussians=g.capacity, C=sc.C, feat_dtype=sc.feat_dtype, budget_bytes=4 << 30)
+    srv.update_frame(g)
+    rng = np.random.default_rng(2)
+    cams = _cams(rng, 24, [(128, 128), (96, 64), (64, 64), (112, 80)])
+    ref = cams[5]
+    outs = []
+    # alone
+    Fa, Aa = torch.empty((sc.C, ref.height, ref.width), device="cuda"), torch.empty((ref.height, ref.width), device="cuda")
+    srv.wait(srv.submit(ref, Fa, Aa))
+    # in the mix: a producer thread submits bursts of 6 while earlier batches run
+    ids = [None] * len(cams)
+    bufs = [(torch.empty((sc.C, c.height, c.width), device="cuda"), torch.empty((c.height, c.width), device="cuda"))
+            for c in cams]
+
+    def feeder():
+        for k, cam in enumerate(cams):
+            outs.append(bufs[k])
+            ids[k] = srv.submit(cam, *bufs[k])
+            if k % 6 == 5:
+                time.sleep(0.001)
+
+    torch.cuda.synchronize()
+    th = threading.Thread(target=feeder)
+    th.start()
+    th.join()
+    for k in range(len(cams)):
+        srv.wait(ids[k])
+    st = srv.stats()
+    assert st["completed"] == len(cams) + 1 and st["lanes"] >= 2
+    assert st["views_launched"] > st["batches"]  # requests were batched
+    assert torch.equal(outs[5][0], Fa) and torch.equal(outs[5][1], Aa)
+    for cam, (F, A) in zip(cams, outs):
+        F1, A1 = _solo(g, cam, sc.C)
+        assert torch.equal(F, F1) and torch.equal(A, A1)
+    assert st["p99_ms"] >= st["p50_ms"] > 0
+    srv.close()
+
+
+def test_server_admission_overflow_is_retried_one_view_at_a_time():
+    sc, g, keep = _frame(seed=43)
+    ctx = api.Context()
+    cam0 = _cams(np.random.default_rng(3), 1, [(96, 96)])[0]
+    ctx.render(g, cam0)
+    per_px = ctx.stats()["n_pairs"] / (96 * 96)
+    # underestimate the pairs: admitted batches overflow and are re-run solo
+    kw = dict(max_views_per_batch=8, max_width=96, max_height=96, max_gaussians=g.capacity, C=sc.C,
+              feat_dtype=sc.feat_dtype, pairs_per_gaussian=0.0, pairs_per_pixel=0.35 * per_px)
+    probe = api.Server(max_lanes=4, budget_bytes=1 << 34, **kw)
+    lane = probe.stats()["lane_bytes"]
+    assert probe.stats()["lanes"] == 4
+    probe.close()
+    # admission by memory: the budget decides how many lanes exist
+    with pytest.raises(L.TsplatError):
+        api.Server(max_lanes=4, budget_bytes=lane // 2, **kw)
+    two = api.Server(max_lanes=4, budget_bytes=int(2.5 * lane), **kw)
+    assert two.stats()["lanes"] == 2
+    two.close()
+    srv = api.Server(max_lanes=4, budget_bytes=int(1.5 * lane), **kw)
+    srv.update_frame(g)
+    cams = _cams(np.random.default_rng(4), 8, [(96, 96)])
+    outs = [(torch.empty((sc.C, 96, 96), device="cuda"), torch.empty((96, 96), device="cuda")) for _ in cams]
+    torch.cuda.synchronize()
+    ids = [srv.submit(c, F, A) for c, (F, A) in zip(cams, outs)]
+    for i in ids:
+        srv.wait(i)
+    st = srv.stats()
+    assert st["lanes"] == 1 and st["retried"] > 0 and st["completed"] == 8
+    for cam, (F, A) in zip(cams, outs):
+        F1, A1 = _solo(g, cam, sc.C)
+        assert torch.equal(F, F1) and torch.equal(A, A1)
+    srv.close()
+
+
+def test_server_rejects_and_times_out_on_the_host():
+    sc, g, keep = _frame(seed=44, res=64)
+    srv = api.Server(max_views_per_batch=2, max_lanes=1, max_width=64, max_height=64, max_gaussians=g.capacity,
+                     C=sc.C, feat_dtype=sc.feat_dtype, budget_bytes=1 << 28)
+    big = gen.make_camera(128.0, 128, 128, (0, 0, 0), np.eye(3))
+    with pytest.raises(L.TsplatError):
+        srv.submit(big, torch.empty((sc.C, 128, 128), device="cuda"))
+    # no frame yet: the request stays pending and a bounded wait times out
+    cam = gen.make_camera(64.0, 64, 64, (0, 0, 0), np.eye(3))
+    F = torch.empty((sc.C, 64, 64), device="cuda")
+    rid = srv.submit(cam, F)
+    with pytest.raises(L.TsplatError) as e:
+        srv.wait(rid, timeout_ms=50)
+    assert e.value.status == 4
+    srv.update_frame(g)
+    srv.wait(rid)
+    F1, _ = _solo(g, cam, sc.C)
+    assert torch.equal(F, F1)
+    srv.close()
+
+
+def test_server_double_buffered_frames():
+    """Two frame stores prepared ahead of use; requests admitted after
+    update_frame render the new frame; release_frame returns once no batch
+    renders the old one, which may then be rebuilt."""
+    scA, gA, _ = _frame(seed=45)
+    scB, gB, _ = _frame(seed=46)
+    cap = max(gA.capacity, gB.capacity)
+    srv = api.Server(max_views_per_batch=4, max_lanes=2, max_width=96, max_height=96, max_gaussians=cap,
+                     C=scA.C, feat_dtype=scA.feat_dtype, budget_bytes=2 << 30)
+    srv.prepare(gA)
+    srv.prepare(gB)
+    cams = _cams(np.random.default_rng(6), 6, [(96, 96), (64, 48)])
+    outs = [(torch.empty((scA.C, c.height, c.width), device="cuda"), torch.empty((c.height, c.width), device="cuda"))
+            for c in cams]
+    torch.cuda.synchronize()
+    srv.update_frame(gA)
+    ids = [srv.submit(c, F, A) for c, (F, A) in zip(cams[:3], outs[:3])]
+    for i in ids:
+        srv.wait(i)
+    srv.update_frame(gB)
+    ids = [srv.submit(c, F, A) for c, (F, A) in zip(cams[3:], outs[3:])]
+    srv.release_frame(gA)
+    with pytest.raises(L.TsplatError):
+        srv.release_frame(gB)  # the current frame
+    for i in ids:
+        srv.wait(i)
+    st = srv.stats()
+    assert st["completed"] == 6 and st["retried"] == 0
+    for k, (cam, (F, A)) in enumerate(zip(cams, outs)):
+        F1, A1 = _solo(gA if k < 3 else gB, cam, scA.C)
+        assert torch.equal(F, F1) and torch.equal(A, A1)
+    srv.close()
+
+
+def test_plain_mode_matches():
+    """The unbatched baseline (one view per launch sequence, no graph) gives
+    the same results as the batched graph replays."""
+    sc, g, _ = _frame(seed=47)
+    plain = api.Server(max_views_per_batch=1, max_lanes=1, max_width=96, max_height=96, max_gaussians=g.capacity,
+                       C=sc.C, feat_dtype=sc.feat_dtype, budget_bytes=1 << 30, graphs=False)
+    plain.update_frame(g)
+    cams = _cams(np.random.default_rng(8), 4, [(96, 96), (80, 64)])
+    outs = [(torch.empty((sc.C, c.height, c.width), device="cuda"), torch.empty((c.height, c.width), device="cuda"))
+            for c in cams]
+    torch.cuda.synchronize()
+    ids = [plain.submit(c, F, A) for c, (F, A) in zip(cams, outs)]
+    for i in ids:
+        plain.wait(i)
+    st = plain.stats()
+    assert st["batches"] == 4 and st["lanes"] == 1
+    for cam, (F, A) in zip(cams, outs):
+        F1, A1 = _solo(g, cam, sc.C)
+        assert torch.equal(F, F1) and torch.equal(A, A1)
+    plain.close()
