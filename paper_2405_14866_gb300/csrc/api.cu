@@ -134,7 +134,7 @@ struct tsplat_ctx {
 
 namespace {
 enum { SM_KMIN = 0, SM_KMAX = 1, SM_NVIS = 2, SM_NPASS = 3, SM_P = 4, SM_PEFF = 5, SM_STATUS = 6, SM_TILECTR = 7,
-       SM_N = 8, SM_NINST = 9, SM_TOTALS = 16, SM_WORDS = 16 + 4 * 256 };
+       SM_N = 8, SM_NINST = 9, SM_SORTCTR = 10 /* 4 words */, SM_TOTALS = 16, SM_WORDS = 16 + 4 * 256 };
 uint32_t *small_ptr(tsplat_ctx *c, int w) { return c->small.as<uint32_t>() + w; }
 }  // namespace
 
@@ -357,7 +357,7 @@ static tsplat_status ensure_n(tsplat_ctx *c, int64_t n, cudaStream_t s) {
     TRY(grow(c->skeys1, N * 4, s));
     TRY(grow(c->svals0, N * 4, s));
     TRY(grow(c->svals1, N * 4, s));
-    TRY(grow(c->hist_n, nb * 256 * 4, s));
+    TRY(grow(c->hist_n, nb * 256 * 4 * RS_MAX_PASSES, s));
     TRY(grow(c->emit_blk, nb * 4, s));
     return TSPLAT_OK;
 }
@@ -370,7 +370,7 @@ static tsplat_status ensure_p(tsplat_ctx *c, int64_t p, cudaStream_t s) {
     TRY(grow(c->pk1, (size_t)cap * 4, s));
     TRY(grow(c->pv0, (size_t)cap * 4, s));
     TRY(grow(c->pv1, (size_t)cap * 4, s));
-    TRY(grow(c->hist_p, nb * 256 * 4, s));
+    TRY(grow(c->hist_p, nb * 256 * 4 * RS_MAX_PASSES, s));
     c->p_cap = cap;
     return TSPLAT_OK;
 }
@@ -442,7 +442,9 @@ static tsplat_status render_tail(tsplat_ctx *c, int64_t n_cap, const uint32_t *n
     ds.n_dev = n_inst;
     ds.npass_dev = sm + SM_NPASS;
     ds.kmin = sm + SM_KMIN;
-    ds.hist = c->hist_n.as<uint32_t>();
+    ds.status = c->hist_n.as<uint32_t>();
+    ds.tile_ctr = sm + SM_SORTCTR;
+    ds.err = sm + SM_STATUS;
     ds.totals = sm + SM_TOTALS;
     ds.nblocks = (int)((std::max<int64_t>(inst_cap, 1) + RS_TILE - 1) / RS_TILE);
     launch_radix_sort(ds, 4, s);
@@ -495,7 +497,9 @@ static tsplat_status render_tail(tsplat_ctx *c, int64_t n_cap, const uint32_t *n
     ts.npass_dev = nullptr;
     ts.npass_host = tpass;
     ts.kmin = nullptr;
-    ts.hist = c->hist_p.as<uint32_t>();
+    ts.status = c->hist_p.as<uint32_t>();
+    ts.tile_ctr = sm + SM_SORTCTR;
+    ts.err = sm + SM_STATUS;
     ts.totals = sm + SM_TOTALS;
     ts.nblocks = (int)((c->p_cap + RS_TILE - 1) / RS_TILE);
     // effective pair count: P, or 0 when the pairs did not fit

@@ -107,7 +107,12 @@ constexpr int RS_TILE = RS_THREADS * RS_ITEMS;  // keys per radix block
 // kmin is given) and writes keys[p & 1] / vals[p & 1].  The number of
 // passes is *npass_dev when given, else npass_host; passes beyond it do
 // nothing, so the result lives in buffer (npass-1) & 1, or is the input
-// when npass is 0.
+// when npass is 0.  One histogram launch counts the digits of every pass;
+// then each pass is one launch in which blocks take key tiles in order from
+// a counter and obtain each digit's global offset by looking back over the
+// earlier tiles' published counts (bounded waits; a wait that expires sets
+// TSPLAT_ERR_TIMEOUT in *err).  Launch cost does not depend on n_cap.
+constexpr int RS_MAX_PASSES = 4;
 struct RadixSort {
     const uint32_t *keys_in;
     const uint32_t *vals_in;
@@ -117,9 +122,11 @@ struct RadixSort {
     const uint32_t *npass_dev;
     int npass_host;
     const uint32_t *kmin;
-    uint32_t *hist;    // [256 * nblocks]
-    uint32_t *totals;  // [4 * 256], zeroed by the launcher
-    int nblocks;       // ceil(n_cap / RS_TILE)
+    uint32_t *status;    // [RS_MAX_PASSES][nblocks][256] look-back words
+    uint32_t *totals;    // [RS_MAX_PASSES][256], zeroed by the launcher
+    uint32_t *tile_ctr;  // [RS_MAX_PASSES] tile tickets, zeroed by the histogram launch
+    uint32_t *err;       // status word
+    int nblocks;         // ceil(n_cap / RS_TILE)
 };
 void launch_radix_sort(const RadixSort &rs, int max_passes, cudaStream_t s);
 void launch_depth_npass(const uint32_t *kminmax, uint32_t *npass, cudaStream_t s);

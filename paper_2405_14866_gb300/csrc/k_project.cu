@@ -56,12 +56,12 @@ __device__ __forceinline__ void write_culled(const ProjectOut &o, uint64_t i) {
 // Rendered-Gaussian bookkeeping: depth-key range (for the radix sort's pass
 // count) and the visible count, reduced per block before one set of
 // atomics.  Called by every thread of a 256-thread block.
-__device__ __forceinline__ void account(const ProjectOut &o, bool vis, uint32_t key) {
+__device__ __forceinline__ void account_n(const ProjectOut &o, uint32_t tmin, uint32_t tmax, uint32_t tn) {
     __shared__ uint32_t s_min[8], s_max[8], s_n[8];
     const uint32_t m = 0xffffffffu;
-    const uint32_t kmin = __reduce_min_sync(m, vis ? key : CULLED_KEY);
-    const uint32_t kmax = __reduce_max_sync(m, vis ? key : 0u);
-    const uint32_t nv = __popc(__ballot_sync(m, vis));
+    const uint32_t kmin = __reduce_min_sync(m, tmin);
+    const uint32_t kmax = __reduce_max_sync(m, tmax);
+    const uint32_t nv = __reduce_add_sync(m, tn);
     const int warp = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0) {
         s_min[warp] = kmin;
@@ -84,6 +84,10 @@ __device__ __forceinline__ void account(const ProjectOut &o, bool vis, uint32_t 
     }
 }
 
+__device__ __forceinline__ void account(const ProjectOut &o, bool vis, uint32_t key) {
+    account_n(o, vis ? key : CULLED_KEY, vis ? key : 0u, vis ? 1u : 0u);
+}
+
 // Tile rect from mean2d and radius, as the cited rasterizer defines it.
 __device__ __forceinline__ int tile_rect(float mx, float my, float r, int tiles_x, int tiles_y, int &x0,
                                          int &y0, int &x1, int &y1) {
@@ -100,8 +104,8 @@ __device__ __forceinline__ void publish_views(const ViewBatch &vb, RenderView *v
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x < (unsigned)vb.n_views) views_dev[threadIdx.x] = vb.v[threadIdx.x];
 }
 
-// grid (ceil(n_cap / 256), n_views): view blockIdx.y, Gaussian gi;
-// instance i = view * N + gi.
+// grid (gx, n_views): view blockIdx.y; blocks stride over the Gaussians gi
+// (gx is at most a few waves, whatever the capacity); instance i = view * N + gi.
 __global__ __launch_bounds__(256) void k_project(const float4 *__restrict__ xyzo,
                                                  const float4 *__restrict__ cova,
                                                  const float2 *__restrict__ covb,
@@ -115,12 +119,13 @@ __global__ __launch_bounds__(256) void k_project(const float4 *__restrict__ xyzo
     const tsplat_camera &cam = view.cam;
     const int tiles_x = view.tiles_x, tiles_y = view.tiles_y;
     const uint64_t n = *n_dev;
-    const uint64_t gi = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t tmin = CULLED_KEY, tmax = 0u, tn = 0u;
+    for (uint64_t gi = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; gi < n;
+         gi += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t i = (uint64_t)blockIdx.y * n + gi;
-    const bool active = gi < n;
     bool vis = false;
     uint32_t key = CULLED_KEY;
-    if (active) {
+    {
     const float4 g = xyzo[gi];
     const float *R = cam.R;
     const float px = fadd(fadd(fadd(fmul(R[0], g.x), fmul(R[1], g.y)), fmul(R[2], g.z)), cam.t[0]);
@@ -183,9 +188,16 @@ __global__ __launch_bounds__(256) void k_project(const float4 *__restrict__ xyzo
             }
         }
     }
-    if (!vis) write_culled(o, i);
+    if (!vis) {
+        write_culled(o, i);
+    } else {
+        tmin = min(tmin, key);
+        tmax = max(tmax, key);
+        ++tn;
     }
-    account(o, vis, key);
+    }
+    }
+    account_n(o, tmin, tmax, tn);
 }
 
 __global__ __launch_bounds__(256) void k_prepare_2d(uint64_t n, const float *__restrict__ mean2d,
@@ -268,7 +280,16 @@ void launch_export_rect(const uint2 *rect, const uint32_t *n_dev, int64_t n_cap,
 void launch_project(const float4 *xyzo, const float4 *cova, const float2 *covb, const uint32_t *n_dev,
                     int64_t n_cap, const ViewBatch &vb, RenderView *views_dev,
                     const tsplat_render_params &par, const ProjectOut &o, cudaStream_t s, bool table_on_device) {
-    const dim3 grid((unsigned)std::max<int64_t>(1, (n_cap + 255) / 256), (unsigned)vb.n_views);
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        sms = std::max(sms, 1);
+    }
+    // about four waves of 256-thread blocks over all views
+    const int64_t gx = std::max<int64_t>(1, std::min<int64_t>((n_cap + 255) / 256, (int64_t)sms * 32 / vb.n_views));
+    const dim3 grid((unsigned)gx, (unsigned)vb.n_views);
     k_project<<<grid, 256, 0, s>>>(xyzo, cova, covb, n_dev, vb, views_dev, table_on_device ? 1 : 0, par, o);
     note_launches(1);
 }
