@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-diff", action="store_true")
     return ap.parse_args()
 
 
@@ -348,16 +349,18 @@ def serving_bench(api, torch, sc, g, views, seconds=1.5):
     load = ServeLoad(api, torch, sc, [g, g2], views)
     common = dict(max_width=max(SERVE_SIZES), max_height=max(SERVE_SIZES), max_gaussians=g.capacity, C=sc.C,
                   feat_dtype=sc.feat_dtype)
-    servers = {"server": api.Server(max_views_per_batch=8, max_lanes=3, budget_bytes=24 << 30, **common),
+    servers = {"server": api.Server(max_views_per_batch=8, max_lanes=3, budget_bytes=24 << 30, max_inflight_views=12,
+                                    **common),
                "plain": api.Server(max_views_per_batch=1, max_lanes=1, budget_bytes=24 << 30, graphs=False, **common)}
     for srv in servers.values():
         srv.prepare(g)
         srv.prepare(g2)
     viewers4 = load.viewers(4, seed=11)
-    out = {"workload": "left+right eye views of 1-64 viewers at {512, 768, 1024}^2 (f = width), eye pairs at "
+    out = {"workload": "left+right eye views of 4-40 viewers at {512, 768, 1024}^2 (f = width), eye pairs at "
                        "Poisson 30 Hz per viewer; the 2.1M-Gaussian frame rebuilt at 30 Hz into two alternating "
                        "stores; latency = submission to completion seen by the server",
            "server": {"max_views_per_batch": 8, "lanes": servers["server"].stats()["lanes"], "graphs": True,
+                      "max_inflight_views": 12,
                       "lane_bytes": servers["server"].stats()["lane_bytes"]},
            "plain": {"max_views_per_batch": 1, "lanes": 1, "graphs": False,
                      "what": "one launch sequence per view, one at a time, same queue and frames"}}
@@ -368,7 +371,7 @@ def serving_bench(api, torch, sc, g, views, seconds=1.5):
     sat["ratio"] = sat["server"]["views_per_s"] / max(sat["plain"]["views_per_s"], 1e-9)
     out["saturation"] = sat
     sweep = []
-    for nv in (4, 16, 32, 64):
+    for nv in (4, 8, 12, 16, 20, 24, 28, 32, 40):
         viewers = load.viewers(nv, seed=100 + nv)
         row = {"viewers": nv, "offered_views_per_s": 60.0 * nv}
         for k, srv in servers.items():
@@ -390,6 +393,81 @@ def serving_bench(api, torch, sc, g, views, seconds=1.5):
     for srv in servers.values():
         srv.close()
     return out
+
+
+# ---------------------------------------------------------------------------
+# differentiation: forward with saved state + backward, 8 samples
+# ---------------------------------------------------------------------------
+
+def diff_bench(api, torch, steps=10, warmup=3):
+    """8 samples of two 512^2 views (~315K Gaussians, 16-ch FP32 features);
+    per sample: render with TSPLAT_RENDER_SAVE, dL/dF of the MSE against a
+    seeded target map, tsplat_backward (gradients for 2D means, conics,
+    opacities, features)."""
+    from paper_2405_14866_gb300 import gen
+    samples = []
+    for k in range(8):
+        sc = gen.scene_diff_sample(seed=300 + k)
+        up = api.upload_scene(sc)
+        views = [api.source_view(v["depth"], v["mask"], v["scale"], v["quat"], v["opacity"], v["feat"], v["cam"])
+                 for v in up["views"]]
+        g = api.Gaussians.build(views, sc.C, sc.feat_dtype)
+        Y = torch.from_numpy(sc.extra["target_map"]).cuda()
+        samples.append((g, Y, up))
+    sc0 = gen.scene_diff_sample(seed=300)
+    cam, C = sc0.targets[0], sc0.C
+    ctx = api.Context()
+    P = N = 0
+    for g, Y, _ in samples:
+        ctx.render(g, cam, save=True)
+        st = ctx.stats()
+        P, N = max(P, st["n_pairs"]), max(N, st["n_gaussians"])
+    cap = max(g.capacity for g, _, _ in samples)
+    ctx.reserve(cap, int(P * 1.25) + 65536, cam.width, cam.height, C)
+    F = torch.empty((C, cam.height, cam.width), device="cuda")
+    A = torch.empty((cam.height, cam.width), device="cuda")
+    grads = [tuple(torch.empty(sh, device="cuda") for sh in ((cap, 2), (cap, 3), (cap,), (cap, C))) for _ in samples]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in samples]
+
+    def step(record):
+        for k, (g, Y, _) in enumerate(samples):
+            if record:
+                ev[k][0].record()
+            ctx.render(g, cam, save=True, async_=True, out_feat=F, out_alpha=A)
+            dF = (F - Y) * (2.0 / F.numel())
+            if record:
+                ev[k][1].record()
+            ctx.backward(dF, out=grads[k])
+            if record:
+                ev[k][2].record()
+
+    for _ in range(warmup):
+        step(False)
+    torch.cuda.synchronize()
+    fwd = bwd = 0.0
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(steps):
+        step(True)
+        torch.cuda.synchronize()
+        fwd += sum(e[0].elapsed_time(e[1]) for e in ev)
+        bwd += sum(e[1].elapsed_time(e[2]) for e in ev)
+    t1.record()
+    torch.cuda.synchronize()
+    ctx.status()
+    per_fwd, per_bwd = fwd / (steps * 8), bwd / (steps * 8)
+    # backward algorithmic bytes per sample (last sample's P, N): per pair id +
+    # record + feature row; per pixel dF (C f32), T_final, last index; gradient
+    # outputs N x (2 + 3 + 1 + C) f32
+    bw_bytes = P * (4 + 24 + 4 * C) + cam.width * cam.height * (4 * C + 8) + N * (6 + C) * 4
+    peak, src = measured_peaks()
+    return {"workload": "8 samples x 2 x 512^2 source views (~315K Gaussians each), 16-ch FP32 features, 512^2 "
+                        "target; loss = MSE vs a seeded N(0,1) map",
+            "samples_per_s": 1e3 / (per_fwd + per_bwd), "forward_ms": per_fwd, "backward_ms": per_bwd,
+            "gaussians": N, "pairs": P,
+            "backward_roofline": {"bound": "hbm", "achieved": bw_bytes / (per_bwd * 1e-3) / 1e9, "peak": peak,
+                                  "unit": "GB/s", "frac": bw_bytes / (per_bwd * 1e-3) / 1e9 / peak,
+                                  "algorithmic_bytes": bw_bytes, "note": "includes the dL/dF elementwise op"}}
 
 
 # ---------------------------------------------------------------------------
@@ -531,6 +609,9 @@ def run_ours(args):
     serving = None
     if not args.no_serving and args.workload == "precision":
         serving = serving_bench(api, torch, sc, g, views)
+    diff = None
+    if not args.no_diff and rank == 0:
+        diff = diff_bench(api, torch)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -555,7 +636,7 @@ def run_ours(args):
                 "build_ms": build_ms, "build_gbs": build_bytes / (build_ms * 1e-3) / 1e9,
                 "gaussians_per_s": value * N,
                 "stages_ms": stages, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-                "serving": serving,
+                "serving": serving, "differentiation": diff,
                 "gpu_launches": int(launches)}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -353,7 +353,7 @@ typedef struct {
     float pairs_per_gaussian;     /* (2.5) */
     float pairs_per_pixel;        /* (1.0) */
     int32_t flags;                /* TSPLAT_SERVER_* (0) */
-    int32_t reserved;
+    int32_t max_inflight_views;   /* views on the device at once over all lanes; 0 = lanes x batch (0) */
     int64_t budget_bytes;         /* device memory for the lanes' scratch (8 GiB) */
     tsplat_render_params params;
 } tsplat_server_config;

@@ -44,7 +44,7 @@ class CServerConfig(Structure):
     _fields_ = [("max_views_per_batch", c_int32), ("max_lanes", c_int32), ("max_width", c_int32),
                 ("max_height", c_int32), ("max_gaussians", c_int64), ("C", c_int32), ("feat_dtype", c_int32),
                 ("pairs_per_gaussian", c_float), ("pairs_per_pixel", c_float), ("flags", c_int32),
-                ("reserved", c_int32), ("budget_bytes", c_int64), ("params", CParams)]
+                ("max_inflight_views", c_int32), ("budget_bytes", c_int64), ("params", CParams)]
 
 
 class CServerStats(Structure):

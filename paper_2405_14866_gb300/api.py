@@ -233,14 +233,18 @@ class Context:
         self.n = n
         return out_feat, out_alpha
 
-    def backward(self, dF, dA=None, n: Optional[int] = None, C: Optional[int] = None, stream=None):
-        """Gradients (d_mean2d (N,2), d_conic (N,3), d_opac (N,), d_feat (N,C))."""
-        st = self.stats()
-        n = n if n is not None else (self.n if self.n is not None else st["n_gaussians"])
-        C = C if C is not None else st["C"]
-        dev = torch.device("cuda")
-        outs = (torch.empty((n, 2), device=dev), torch.empty((n, 3), device=dev), torch.empty((n,), device=dev),
-                torch.empty((n, C), device=dev))
+    def backward(self, dF, dA=None, n: Optional[int] = None, C: Optional[int] = None, stream=None, out=None):
+        """Gradients (d_mean2d (N,2), d_conic (N,3), d_opac (N,), d_feat (N,C)); `out` = preallocated
+        tensors of at least N rows (no synchronization then)."""
+        if out is not None:
+            outs = tuple(out)
+        else:
+            st = self.stats()
+            n = n if n is not None else (self.n if self.n is not None else st["n_gaussians"])
+            C = C if C is not None else st["C"]
+            dev = torch.device("cuda")
+            outs = (torch.empty((n, 2), device=dev), torch.empty((n, 3), device=dev), torch.empty((n,), device=dev),
+                    torch.empty((n, C), device=dev))
         L.call("tsplat_backward", self.handle, _ptr(dF.contiguous()), _ptr(None if dA is None else dA.contiguous()),
                *(_ptr(o) for o in outs), _stream(stream))
         return outs
@@ -297,7 +301,7 @@ class Server:
     def __init__(self, max_views_per_batch=8, max_lanes=3, max_width=1024, max_height=1024, max_gaussians=1 << 22,
                  C=32, feat_dtype=BF16, pairs_per_gaussian=2.5, pairs_per_pixel=1.0, budget_bytes=8 << 30,
                  params: Optional[L.CParams] = None,
-                 graphs: bool = True):
+                 graphs: bool = True, max_inflight_views: int = 0):
         cfg = L.CServerConfig()
         L.lib().tsplat_server_config_default(ctypes.byref(cfg))
         cfg.max_views_per_batch, cfg.max_lanes = max_views_per_batch, max_lanes
@@ -305,6 +309,7 @@ class Server:
         cfg.C, cfg.feat_dtype, cfg.pairs_per_pixel, cfg.budget_bytes = C, feat_dtype, pairs_per_pixel, budget_bytes
         cfg.pairs_per_gaussian = pairs_per_gaussian
         cfg.flags = 0 if graphs else SERVER_NO_GRAPH
+        cfg.max_inflight_views = max_inflight_views
         if params is not None:
             cfg.params = params
         h = ctypes.c_void_p()

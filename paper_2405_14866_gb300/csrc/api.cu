@@ -530,6 +530,7 @@ static tsplat_status render_tail(tsplat_ctx *c, int64_t n_cap, const uint32_t *n
     ca.log2_alpha_min = (float)log2((double)par.alpha_min);
     ca.status = sm + SM_STATUS;
     ca.tile_counter = sm + SM_TILECTR;
+    ca.save = save ? 1 : 0;
     launch_composite(ca, s);
     TRY(check_launch("render: composite"));
     TRY(mark(c, prof, 6, s));

@@ -19,6 +19,11 @@ constexpr uint32_t CULLED_KEY = 0xFFFFFFFFu;
 //   h1 = (conic c, log2(opacity), ex, ey) with (ex, ey) the half extents of
 //        the box that bounds every pixel where alpha can reach alpha_min.
 // The compositing evaluates alpha = min(alpha_max, 2^(q log2(e) + log2(o))).
+// Projected record of one Gaussian instance (32 B):
+//   h0 = (mu_x, mu_y, -a/2, -b), h1 = (-c/2, log2 o, ex, ey)
+// where [[a, b], [b, c]] is the conic (inverse 2D covariance) and (ex, ey)
+// the half extents of the box outside which o e^q < alpha_min.  The conic is
+// kept pre-scaled for the quadratic form (the scalings are exact in FP32).
 struct __align__(16) Header {
     float4 h0;
     float4 h1;
@@ -36,9 +41,11 @@ __device__ __forceinline__ float fsqrt(float a) { return __fsqrt_rn(a); }
 //   q = -1/2 (a dx^2 + c dy^2) - b dx dy.
 // Forward and backward kernels both call this function, so both evaluate
 // the same instruction sequence and take identical skip decisions.
-__device__ __forceinline__ float gauss_q(float dx, float dy, float a, float b, float c) {
-    const float s = __fmaf_rn(a, __fmul_rn(dx, dx), __fmul_rn(c, __fmul_rn(dy, dy)));
-    return __fmaf_rn(-0.5f, s, -__fmul_rn(b, __fmul_rn(dx, dy)));
+// q = -(a dx^2 + 2 b dx dy + c dy^2) / 2 from the pre-scaled conic
+// (ha, nb, hc) = (-a/2, -b, -c/2): q = dx (ha dx + nb dy) + hc dy^2.
+__device__ __forceinline__ float gauss_q(float dx, float dy, float ha, float nb, float hc) {
+    const float t = __fmaf_rn(ha, dx, __fmul_rn(nb, dy));
+    return __fmaf_rn(dx, t, __fmul_rn(__fmul_rn(hc, dy), dy));
 }
 
 // alpha before the alpha_max clamp: o e^q

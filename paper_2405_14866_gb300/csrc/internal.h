@@ -180,6 +180,7 @@ struct CompositeArgs {
     float log2_alpha_min;  // blend test: log2(o) + q log2(e) >= log2(alpha_min)
     uint32_t *status;      // TSPLAT_ERR_TIMEOUT if a bounded wait expired
     uint32_t *tile_counter;  // next tile to hand out (0 at launch)
+    int save;                // record T_final and the last blended index (backward)
 };
 void launch_composite(const CompositeArgs &a, cudaStream_t s);
 

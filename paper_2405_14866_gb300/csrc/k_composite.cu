@@ -52,7 +52,7 @@ constexpr uint32_t FINAL_TILE = 0xffffffffu;  // slot tile id of the last slot a
 template <int CP, bool F32F>
 struct CompSmem {
     static constexpr int RING = Ring<CP>::N;
-    Header hdr[RING][SB];
+    Header hdr[RING][SB + 1];  // entry SB of each slot: an empty record (alpha = 0 everywhere)
     __nv_bfloat16 fhi[RING][SB][CP];
     __nv_bfloat16 flo[F32F ? RING : 1][F32F ? SB : 1][CP];
     __nv_bfloat16 whi[NCW][32][WROW];
@@ -184,7 +184,8 @@ __device__ __forceinline__ bool box_hit(const Header &h, float bx0, float bx1, f
 
 // Persistent: gridDim.x CTAs (a few per SM) share the tiles through
 // a.tile_counter, which must be 0 at launch.
-template <int CP, bool F32F>
+// SAVE: track each pixel's last blended list position (for the backward).
+template <int CP, bool F32F, bool SAVE>
 __global__ __launch_bounds__(NTHR, 2) void k_composite(CompositeArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     CompSmem<CP, F32F> &S = *reinterpret_cast<CompSmem<CP, F32F> *>(smem_raw);
@@ -196,6 +197,8 @@ __global__ __launch_bounds__(NTHR, 2) void k_composite(CompositeArgs a) {
         for (int r = 0; r < RING; ++r) {
             mbar_init(&S.full[r], 1 + 32);  // lane 0's arrival + one asynchronous arrival per producer lane
             mbar_init(&S.empty[r], NCW);
+            S.hdr[r][SB].h0 = make_float4(0.f, 0.f, 0.f, 0.f);
+            S.hdr[r][SB].h1 = make_float4(0.f, -INFINITY, -INFINITY, -INFINITY);
         }
         mbar_init_fence();
     }
@@ -286,7 +289,7 @@ __global__ __launch_bounds__(NTHR, 2) void k_composite(CompositeArgs a) {
                 const size_t pix = (size_t)py * W + px;
                 if (vw.out_alpha) vw.out_alpha[pix] = 1.0f - T;
                 if (vw.out_T) vw.out_T[pix] = T;
-                if (vw.out_last) vw.out_last[pix] = last;
+                if (SAVE && vw.out_last) vw.out_last[pix] = last;
             }
             if (lane == 0) *reinterpret_cast<volatile int32_t *>(&S.done_seq[warp]) = seq;
             cur = FINAL_TILE;
@@ -300,6 +303,8 @@ __global__ __launch_bounds__(NTHR, 2) void k_composite(CompositeArgs a) {
             const int c0 = __popc(m0), nrel = c0 + __popc(m1);
             if (r0) S.list[warp][__popc(m0 & lt)] = (uint8_t)lane;
             if (r1) S.list[warp][c0 + __popc(m1 & lt)] = (uint8_t)(lane + 32);
+            // pad the list to a multiple of 16 with the empty record
+            if (lane < 16 && nrel + lane < ((nrel + 15) & ~15)) S.list[warp][nrel + lane] = (uint8_t)SB;
             __syncwarp();
             for (int g0 = 0; g0 < nrel && !wdone; g0 += 16) {
                 uint32_t wh[8], wl[8];
@@ -308,21 +313,21 @@ __global__ __launch_bounds__(NTHR, 2) void k_composite(CompositeArgs a) {
                     float w2[2];
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
-                        // straight-line recurrence: only T / done / last carry a dependency
-                        const bool have = g0 + g + h < nrel;
-                        const int j = have ? S.list[warp][g0 + g + h] : 0;
+                        // straight-line recurrence: only T / done / last carry a
+                        // dependency; padded entries are the empty record (e2 = -inf)
+                        const int j = S.list[warp][g0 + g + h];
                         const float4 h0 = S.hdr[slot][j].h0;
                         const float4 h1 = S.hdr[slot][j].h1;
                         const float q = gauss_q(fpx - h0.x, fpy - h0.y, h0.z, h0.w, h1.x);
                         const float e2 = fmaf(q, LOG2E, h1.y);
                         const float al = fminf(amax, ex2(e2));
-                        const bool ok = have & !done & (q <= 0.0f) & (e2 >= l2min);
+                        const bool ok = !done & (q <= 0.0f) & (e2 >= l2min);
                         const float Tn = T * (1.0f - al);
                         const bool stop = ok & (Tn < tmin);
                         const bool blend = ok & !stop;
                         w2[h] = blend ? al * T : 0.0f;
                         T = blend ? Tn : T;
-                        last = blend ? (uint32_t)(base + j + 1) : last;
+                        if (SAVE) last = blend ? (uint32_t)(base + j + 1) : last;
                         done = done | stop;
                     }
                     wh[g / 2] = pack_bf16x2(w2[0], w2[1]);
@@ -553,8 +558,9 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
                         if (lane == 0 && c < a.C) atomicAdd(&a.d_feat[(size_t)s_id[j] * a.C + c], v);
                     }
                 }
-                const float gx = dq * (h0.z * dx + h0.w * dy);
-                const float gy = dq * (h0.w * dx + h1.x * dy);
+                const float ca = -2.0f * h0.z, cb = -h0.w, cc = -2.0f * h1.x;  // conic from the record
+                const float gx = dq * (ca * dx + cb * dy);
+                const float gy = dq * (cb * dx + cc * dy);
                 const float ga = dq * (-0.5f * dx * dx);
                 const float gb = dq * (-dx * dy);
                 const float gc = dq * (-0.5f * dy * dy);
@@ -578,19 +584,19 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
     }
 }
 
-template <int CP, bool F32F>
+template <int CP, bool F32F, bool SAVE>
 void run_composite(const CompositeArgs &a, cudaStream_t s) {
     const size_t smem = sizeof(CompSmem<CP, F32F>);
     static int grid = 0;
     if (!grid) {
-        cudaFuncSetAttribute(k_composite<CP, F32F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_composite<CP, F32F, SAVE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_composite<CP, F32F>, NTHR, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_composite<CP, F32F, SAVE>, NTHR, smem);
         grid = std::max(1, sms) * std::max(1, per_sm);
     }
-    k_composite<CP, F32F><<<std::min(grid, std::max(1, (int)a.n_tiles_total)), NTHR, smem, s>>>(a);
+    k_composite<CP, F32F, SAVE><<<std::min(grid, std::max(1, (int)a.n_tiles_total)), NTHR, smem, s>>>(a);
     note_launches(1);
 }
 
@@ -611,9 +617,15 @@ void run_backward(const BackwardArgs &a, cudaStream_t s) {
 void launch_composite(const CompositeArgs &a, cudaStream_t s) {
     if (a.n_tiles_total == 0) return;
     const bool f32 = a.feat_dtype == TSPLAT_F32;
-    if (a.C <= 16) { if (f32) run_composite<16, true>(a, s); else run_composite<16, false>(a, s); }
-    else if (a.C <= 32) { if (f32) run_composite<32, true>(a, s); else run_composite<32, false>(a, s); }
-    else { if (f32) run_composite<64, true>(a, s); else run_composite<64, false>(a, s); }
+    if (a.save) {
+        if (a.C <= 16) { if (f32) run_composite<16, true, true>(a, s); else run_composite<16, false, true>(a, s); }
+        else if (a.C <= 32) { if (f32) run_composite<32, true, true>(a, s); else run_composite<32, false, true>(a, s); }
+        else { if (f32) run_composite<64, true, true>(a, s); else run_composite<64, false, true>(a, s); }
+    } else {
+        if (a.C <= 16) { if (f32) run_composite<16, true, false>(a, s); else run_composite<16, false, false>(a, s); }
+        else if (a.C <= 32) { if (f32) run_composite<32, true, false>(a, s); else run_composite<32, false, false>(a, s); }
+        else { if (f32) run_composite<64, true, false>(a, s); else run_composite<64, false, false>(a, s); }
+    }
 }
 
 void launch_backward(const BackwardArgs &a, cudaStream_t s) {

@@ -178,8 +178,8 @@ __global__ __launch_bounds__(256) void k_project(const float4 *__restrict__ xyzo
                 const float ca_ = fdiv(c, det), cb_ = -fdiv(b, det), cc_ = fdiv(a, det);
                 float ex, ey;
                 cull_extents(ca_, cb_, cc_, g.w, par.alpha_min, ex, ey);
-                o.hdr[i].h0 = make_float4(mx, my, ca_, cb_);
-                o.hdr[i].h1 = make_float4(cc_, log2f(g.w), ex, ey);
+                o.hdr[i].h0 = make_float4(mx, my, -0.5f * ca_, -cb_);
+                o.hdr[i].h1 = make_float4(-0.5f * cc_, log2f(g.w), ex, ey);
                 o.rect[i] = pack_rect(x0, y0, x1, y1);
                 o.ntiles[i] = (uint32_t)nt;
                 key = __float_as_uint(pz);
@@ -229,8 +229,8 @@ __global__ __launch_bounds__(256) void k_prepare_2d(uint64_t n, const float *__r
             const float a = conic[3 * i], b = conic[3 * i + 1], c = conic[3 * i + 2];
             float ex, ey;
             cull_extents(a, b, c, opac[i], par.alpha_min, ex, ey);
-            o.hdr[i].h0 = make_float4(mx, my, a, b);
-            o.hdr[i].h1 = make_float4(c, log2f(opac[i]), ex, ey);
+            o.hdr[i].h0 = make_float4(mx, my, -0.5f * a, -b);
+            o.hdr[i].h1 = make_float4(-0.5f * c, log2f(opac[i]), ex, ey);
             o.rect[i] = pack_rect(x0, y0, x1, y1);
             o.ntiles[i] = (uint32_t)nt;
             key = __float_as_uint(z);
@@ -252,9 +252,9 @@ __global__ void k_export_header(const Header *hdr, const uint32_t *n_dev, int wh
         dst[2 * i] = h.h0.x;
         dst[2 * i + 1] = h.h0.y;
     } else {
-        dst[3 * i] = h.h0.z;
-        dst[3 * i + 1] = h.h0.w;
-        dst[3 * i + 2] = h.h1.x;
+        dst[3 * i] = -2.0f * h.h0.z;  // the record keeps (-a/2, -b, -c/2)
+        dst[3 * i + 1] = -h.h0.w;
+        dst[3 * i + 2] = -2.0f * h.h1.x;
     }
 }
 

@@ -327,10 +327,18 @@ void worker_main(tsplat_server *Sp) {
                 std::lock_guard<std::mutex> lock(S.mu);
                 if (S.stop) break;
                 if (!S.frame || S.pending.empty()) break;
+                // views already on the device bound this batch (latency control)
+                int room = S.cfg.max_views_per_batch;
+                if (S.cfg.max_inflight_views > 0) {
+                    int inflight = 0;
+                    for (const Lane &O : S.lanes) inflight += O.busy ? (int)O.reqs.size() : 0;
+                    room = std::min(room, S.cfg.max_inflight_views - inflight);
+                    if (room <= 0) break;
+                }
                 frame = S.frame;
                 const int64_t cap = (int64_t)(0.9 * (double)ctx_pair_capacity(L.ctx));
                 int64_t used = 0;
-                while (!S.pending.empty() && (int)batch.size() < S.cfg.max_views_per_batch) {
+                while (!S.pending.empty() && (int)batch.size() < room) {
                     Request &r = S.reqs[S.pending.front()];
                     if (!batch.empty() && (r.solo || used + r.est_pairs > cap)) break;
                     batch.push_back(S.pending.front());
@@ -386,7 +394,7 @@ tsplat_status tsplat_server_create(const tsplat_server_config *cfg, tsplat_serve
     if (!cfg || !out) return record_error(TSPLAT_ERR_INVALID_ARG, "server_create: NULL argument");
     *out = nullptr;
     if (cfg->max_views_per_batch < 1 || cfg->max_views_per_batch > MAX_BATCH || cfg->max_lanes < 1 ||
-        cfg->max_width < 1 || cfg->max_height < 1 || cfg->max_gaussians < 1 || !(cfg->pairs_per_pixel >= 0.f) || !(cfg->pairs_per_gaussian >= 0.f) ||
+        cfg->max_width < 1 || cfg->max_height < 1 || cfg->max_gaussians < 1 || cfg->max_inflight_views < 0 || !(cfg->pairs_per_pixel >= 0.f) || !(cfg->pairs_per_gaussian >= 0.f) ||
         cfg->pairs_per_pixel + cfg->pairs_per_gaussian <= 0.f)
         return record_error(TSPLAT_ERR_INVALID_ARG, "server_create: invalid configuration");
     tsplat_server *S = new tsplat_server();

@@ -151,12 +151,21 @@ def test_fp32_central_differences_match_fp64_adjoint():
             if not stable:
                 skipped += 1
                 continue
-            up = {k: a.copy() for k, a in base.items()}
-            dn = {k: a.copy() for k, a in base.items()}
-            up[key][pos] = v + h
-            dn[key][pos] = v - h
-            fd = (loss(up) - loss(dn)) / (2 * h)
+            def central(step):
+                up = {k: a.copy() for k, a in base.items()}
+                dn = {k: a.copy() for k, a in base.items()}
+                up[key][pos] = v + step
+                dn[key][pos] = v - step
+                return (loss(up) - loss(dn)) / (2 * step)
+
+            fd, fd_half = central(h), central(0.5 * h)
             an = refs[key][pos]
+            # a single-precision threshold decision that flips inside the step
+            # (near alpha_min or t_min, where FP32 and FP64 may disagree) makes
+            # the forward jump: the two step sizes then disagree
+            if abs(fd - fd_half) > 5e-3 * max(abs(an), rho[key]):
+                skipped += 1
+                continue
             assert abs(fd - an) <= 1e-2 * max(abs(an), rho[key]), (key, j, idx, fd, an)
             checked += 1
     assert checked >= 60, (checked, skipped)
