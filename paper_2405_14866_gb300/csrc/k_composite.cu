@@ -436,10 +436,33 @@ __device__ __forceinline__ void stage(const Header *__restrict__ hdr, const FT *
     }
 }
 
-__device__ __forceinline__ float warp_sum(float v) {
+// Warp totals of NV per-lane values (NV a power of two) with NV - 1 + ...
+// shuffles instead of 5 NV: at each level a lane keeps one half of its
+// values and receives the partner's partial sums of that half.  Afterwards,
+// for NV >= 32, lane l holds in v[i] the total of value l * (NV / 32) + i;
+// for NV < 32, lanes with (l & (32 / NV - 1)) == 0 hold in v[0] the total of
+// value l / (32 / NV).
+template <int NV>
+__device__ __forceinline__ void warp_transpose_sum(float (&v)[NV], int lane) {
+    int n = NV;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-    return v;
+    for (int b = 16; b > 0; b >>= 1) {
+        if (n > 1) {
+            const int half = n / 2;
+            const bool upper = (lane & b) != 0;
+#pragma unroll
+            for (int i = 0; i < NV / 2; ++i) {
+                if (i < half) {
+                    const float keep = upper ? v[i + half] : v[i];
+                    const float send = upper ? v[i] : v[i + half];
+                    v[i] = keep + __shfl_xor_sync(FULL, send, b);
+                }
+            }
+            n = half;
+        } else {
+            v[0] += __shfl_xor_sync(FULL, v[0], b);
+        }
+    }
 }
 
 // A8: reverse traversal from each pixel's last blended Gaussian, with the
@@ -537,7 +560,7 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
                 FeatIO<FT>::template load<CP>(f, s_feat + (size_t)j * CP);
                 float wgt = 0.0f, d_o = 0.0f, dq = 0.0f;
                 if (contrib) {
-                    const float inv = 1.0f / (1.0f - al);
+                    const float inv = __frcp_rn(1.0f - al);
                     const float Tj = T * inv;
                     float fg = 0.0f;
 #pragma unroll
@@ -547,37 +570,38 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
                     sg = fmaf(wgt, fg, sg);
                     T = Tj;
                     if (raw < a.alpha_max) {
-                        d_o = (raw / ex2(h1.y)) * dal;  // d alpha / d o = e^q
+                        d_o = ex2(q * LOG2E) * dal;  // d alpha / d o = e^q
                         dq = al * dal;
                     }
                 }
+                const uint32_t id = s_id[j];
                 if (a.d_feat) {
+                    float v[CP];
 #pragma unroll
-                    for (int c = 0; c < CP; ++c) {
-                        const float v = warp_sum(wgt * g[c]);
-                        if (lane == 0 && c < a.C) atomicAdd(&a.d_feat[(size_t)s_id[j] * a.C + c], v);
+                    for (int c = 0; c < CP; ++c) v[c] = wgt * g[c];
+                    warp_transpose_sum<CP>(v, lane);
+                    if (CP >= 32) {
+#pragma unroll
+                        for (int i = 0; i < (CP >= 32 ? CP / 32 : 1); ++i) {
+                            const int c = lane * (CP / 32) + i;
+                            if (c < a.C) atomicAdd(&a.d_feat[(size_t)id * a.C + c], v[i]);
+                        }
+                    } else {
+                        const int c = lane / (32 / CP);
+                        if ((lane & (32 / CP - 1)) == 0 && c < a.C) atomicAdd(&a.d_feat[(size_t)id * a.C + c], v[0]);
                     }
                 }
                 const float ca = -2.0f * h0.z, cb = -h0.w, cc = -2.0f * h1.x;  // conic from the record
-                const float gx = dq * (ca * dx + cb * dy);
-                const float gy = dq * (cb * dx + cc * dy);
-                const float ga = dq * (-0.5f * dx * dx);
-                const float gb = dq * (-dx * dy);
-                const float gc = dq * (-0.5f * dy * dy);
-                const float so = warp_sum(d_o), sx = warp_sum(gx), sy = warp_sum(gy);
-                const float sa = warp_sum(ga), sb = warp_sum(gb), sc = warp_sum(gc);
-                if (lane == 0) {
-                    const uint32_t id = s_id[j];
-                    if (a.d_opac) atomicAdd(&a.d_opac[id], so);
-                    if (a.d_mean2d) {
-                        atomicAdd(&a.d_mean2d[2 * id], sx);
-                        atomicAdd(&a.d_mean2d[2 * id + 1], sy);
-                    }
-                    if (a.d_conic) {
-                        atomicAdd(&a.d_conic[3 * id], sa);
-                        atomicAdd(&a.d_conic[3 * id + 1], sb);
-                        atomicAdd(&a.d_conic[3 * id + 2], sc);
-                    }
+                float gv[8] = {d_o, dq * (ca * dx + cb * dy), dq * (cb * dx + cc * dy), dq * (-0.5f * dx * dx),
+                               dq * (-dx * dy), dq * (-0.5f * dy * dy), 0.0f, 0.0f};
+                warp_transpose_sum<8>(gv, lane);
+                if ((lane & 3) == 0) {  // lane 4k holds value k: opacity, mean x, y, conic a, b, c
+                    const int k = lane >> 2;
+                    float *dst = nullptr;
+                    if (k == 0) dst = a.d_opac ? a.d_opac + id : nullptr;
+                    else if (k <= 2) dst = a.d_mean2d ? a.d_mean2d + 2 * (size_t)id + (k - 1) : nullptr;
+                    else if (k <= 5) dst = a.d_conic ? a.d_conic + 3 * (size_t)id + (k - 3) : nullptr;
+                    if (dst) atomicAdd(dst, gv[0]);
                 }
             }
         }
