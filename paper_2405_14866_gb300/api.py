@@ -75,21 +75,26 @@ def launch_count() -> int:
     return int(L.lib().tsplat_launch_count())
 
 
-def source_view(depth, mask, scale, quat, opacity, feat, cam, feat_dtype=F32) -> L.CSrcView:
+def source_view(depth, mask, scale, quat, opacity, feat, cam, feat_dtype=None) -> L.CSrcView:
     """tsplat_src_view from CUDA tensors (H,W), (H,W) u8 or None, (H,W,3),
-    (H,W,4) or None, (H,W), (H,W,C).  The tensors must stay alive until the
-    build has run."""
+    (H,W,4) or None, (H,W), (H,W,C) f32 or bf16 (feat_dtype defaults to the
+    feature tensor's type).  The tensors must stay alive until the build has
+    run."""
     v = L.CSrcView()
     v.depth, v.mask, v.scale, v.quat = _ptr(depth), _ptr(mask), _ptr(scale), _ptr(quat)
     v.opacity, v.feat = _ptr(opacity), _ptr(feat)
+    if feat_dtype is None:
+        feat_dtype = BF16 if feat.dtype == torch.bfloat16 else F32
     v.feat_dtype = feat_dtype
     v.cam = ccamera(cam)
     return v
 
 
-def upload_scene(scene, device="cuda") -> Dict:
-    """Copy a gen.Scene's per-view maps to the device (features as FP32)."""
+def upload_scene(scene, device="cuda", feat_dtype=F32) -> Dict:
+    """Copy a gen.Scene's per-view maps to the device (feature maps as FP32,
+    or rounded to BF16 on the host with feat_dtype=BF16)."""
     views = []
+    fdt = torch.bfloat16 if feat_dtype == BF16 else torch.float32
     for v in scene.views:
         views.append(dict(
             depth=torch.from_numpy(np.ascontiguousarray(v.depth)).to(device),
@@ -97,7 +102,7 @@ def upload_scene(scene, device="cuda") -> Dict:
             scale=torch.from_numpy(np.ascontiguousarray(v.scale)).to(device),
             quat=torch.from_numpy(np.ascontiguousarray(v.quat)).to(device),
             opacity=torch.from_numpy(np.ascontiguousarray(v.opacity)).to(device),
-            feat=torch.from_numpy(np.ascontiguousarray(v.feat)).to(device),
+            feat=torch.from_numpy(np.ascontiguousarray(v.feat)).to(fdt).to(device),
             cam=v.cam))
     return dict(views=views, C=scene.C, feat_dtype=scene.feat_dtype)
 

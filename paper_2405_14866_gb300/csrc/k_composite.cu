@@ -53,8 +53,8 @@ template <int CP, bool F32F>
 struct CompSmem {
     static constexpr int RING = Ring<CP>::N;
     Header hdr[RING][SB + 1];  // entry SB of each slot: an empty record (alpha = 0 everywhere)
-    __nv_bfloat16 fhi[RING][SB][CP];
-    __nv_bfloat16 flo[F32F ? RING : 1][F32F ? SB : 1][CP];
+    __nv_bfloat16 fhi[RING][SB][CP + 8];  // rows padded by 16 B: spreads ldmatrix row reads over the banks
+    __nv_bfloat16 flo[F32F ? RING : 1][F32F ? SB : 1][CP + 8];
     __nv_bfloat16 whi[NCW][32][WROW];
     __nv_bfloat16 wlo[NCW][32][WROW];
     __nv_bfloat16 zero[CP];
@@ -65,6 +65,7 @@ struct CompSmem {
     uint32_t base[RING];       // list position of the slot's first Gaussian
     int32_t done_seq[NCW];     // per consumer warp: sequence number of the last tile it is done with
     uint8_t list[NCW][SB];     // per consumer warp: slot indices of its surviving Gaussians, in order
+    Header wrec[NCW][SB];      // per consumer warp: the survivors' records, compacted
     RenderView views[MAX_BATCH];
 };
 
@@ -306,6 +307,10 @@ __global__ __launch_bounds__(NTHR, 2) void k_composite(CompositeArgs a) {
             // pad the list to a multiple of 16 with the empty record
             if (lane < 16 && nrel + lane < ((nrel + 15) & ~15)) S.list[warp][nrel + lane] = (uint8_t)SB;
             __syncwarp();
+            // the survivors' records, copied in order, so that the recurrence
+            // reads them at fixed offsets
+            for (int k = lane; k < ((nrel + 15) & ~15); k += 32) S.wrec[warp][k] = S.hdr[slot][S.list[warp][k]];
+            __syncwarp();
             for (int g0 = 0; g0 < nrel && !wdone; g0 += 16) {
                 uint32_t wh[8], wl[8];
 #pragma unroll
@@ -315,9 +320,9 @@ __global__ __launch_bounds__(NTHR, 2) void k_composite(CompositeArgs a) {
                     for (int h = 0; h < 2; ++h) {
                         // straight-line recurrence: only T / done / last carry a
                         // dependency; padded entries are the empty record (e2 = -inf)
-                        const int j = S.list[warp][g0 + g + h];
-                        const float4 h0 = S.hdr[slot][j].h0;
-                        const float4 h1 = S.hdr[slot][j].h1;
+                        const float4 h0 = S.wrec[warp][g0 + g + h].h0;
+                        const float4 h1 = S.wrec[warp][g0 + g + h].h1;
+                        const int j = SAVE ? (int)S.list[warp][g0 + g + h] : 0;
                         const float q = gauss_q(fpx - h0.x, fpy - h0.y, h0.z, h0.w, h1.x);
                         const float e2 = fmaf(q, LOG2E, h1.y);
                         const float al = fminf(amax, ex2(e2));

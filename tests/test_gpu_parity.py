@@ -183,3 +183,20 @@ def test_async_mode_reports_capacity_overflow():
     ctx2.status()
     _, F3, A3 = _render(g, cam, save=False)
     assert torch.equal(F2, F3) and torch.equal(A2, A3)
+
+
+def test_build_from_bf16_feature_maps_equals_fp32_maps():
+    """Source feature maps given in BF16 (rounded on the host) build the same
+    BF16 store, bit for bit, as FP32 maps rounded during the lift."""
+    sc = gen.scene_precision(seed=51, res=64, C=32)
+    g1, _ = P.gpu_build(sc)
+    up = api.upload_scene(sc, feat_dtype=api.BF16)
+    views = [api.source_view(v["depth"], v["mask"], v["scale"], v["quat"], v["opacity"], v["feat"], v["cam"])
+             for v in up["views"]]
+    assert views[0].feat_dtype == api.BF16
+    g2 = api.Gaussians.build(views, sc.C, api.BF16)
+    torch.cuda.synchronize()
+    a, b = g1.get(), g2.get()
+    assert a.keys() == b.keys()
+    for k in a:
+        assert torch.equal(a[k], b[k]), k
