@@ -56,6 +56,23 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def max_over_ranks(ms: float, device) -> float:
+    """The largest of the ranks' timed-region durations (every rank calls it;
+    a single process returns its own)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, max_ms: float) -> float:
+    """Units all ranks processed per second over the slowest rank's time."""
+    return world * units_per_rank / (max_ms * 1e-3)
+
+
 def make_scene(workload, rank):
     from paper_2405_14866_gb300 import gen
     if workload == "precision":
@@ -534,13 +551,8 @@ def run_ours(args):
     ctx.status()                                   # no capacity overflow inside the timed region
     stages = ctx.timings()
     step_ms = np.array([ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)])
-    total_ms = float(ev[0].elapsed_time(ev[-1]))
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    value = world * args.steps / (total_ms * 1e-3)
+    total_ms = max_over_ranks(float(ev[0].elapsed_time(ev[-1])), dev)
+    value = whole_job_rate(args.steps, world, total_ms)
     clocks = sampler.summary(t0, t1)
 
     # render only (Gaussians resident), for context
