@@ -470,6 +470,68 @@ __device__ __forceinline__ void warp_transpose_sum(float (&v)[NV], int lane) {
     }
 }
 
+// Feature gradients of a group of up to 16 contributing Gaussians of one
+// warp as a tensor-core product: dF_j[c] = sum over the warp's 32 pixels of
+// w_j(p) g_p[c], i.e. D (16 x C) = W^T (16 x 32) G (32 x C), with W and G
+// split into bf16 hi + lo parts (three products, FP32 accumulation).
+// W is stored per pixel row ([32][BWROW]), G likewise ([32][CP16 + 8]).
+constexpr int BWROW = 24;
+template <int CP>
+struct BwdGroup {
+    static constexpr int GP = CP < 16 ? 16 : CP;  // channels padded to whole k16 / n16 blocks
+    __nv_bfloat16 wh[CT / 32][32][BWROW];
+    __nv_bfloat16 wl[CT / 32][32][BWROW];
+    __nv_bfloat16 gh[CT / 32][32][GP + 8];
+    __nv_bfloat16 gl[CT / 32][32][GP + 8];
+    uint32_t gid[CT / 32][16];
+};
+
+template <int CP>
+__device__ __forceinline__ void flush_feat_grads(BwdGroup<CP> &B, int warp, int lane, int cnt, int C,
+                                                 float *d_feat) {
+    constexpr int GP = BwdGroup<CP>::GP;
+    for (int k = cnt; k < 16; ++k) {  // unused columns contribute nothing
+        B.wh[warp][lane][k] = __float2bfloat16_rn(0.0f);
+        B.wl[warp][lane][k] = __float2bfloat16_rn(0.0f);
+    }
+    __syncwarp();
+    float acc[GP / 8][4];
+#pragma unroll
+    for (int t = 0; t < GP / 8; ++t)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[t][e] = 0.0f;
+    const int kl = ((lane >> 3) & 1) * 8 + (lane & 7);        // B: pixel row this lane addresses
+    const int arow = ((lane >> 4) & 1) * 8 + (lane & 7);      // A (transposed load): pixel row
+    const int acol = ((lane >> 3) & 1) * 8, bcol = (lane >> 4) * 8;
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks) {  // two k-steps of 16 pixels
+        uint32_t ah[4], al[4];
+        ldsm_x4_t(ah[0], ah[1], ah[2], ah[3], &B.wh[warp][ks * 16 + arow][acol]);
+        ldsm_x4_t(al[0], al[1], al[2], al[3], &B.wl[warp][ks * 16 + arow][acol]);
+#pragma unroll
+        for (int p = 0; p < GP / 16; ++p) {
+            uint32_t bh[4], bl[4];
+            ldsm_x4_t(bh[0], bh[1], bh[2], bh[3], &B.gh[warp][ks * 16 + kl][p * 16 + bcol]);
+            ldsm_x4_t(bl[0], bl[1], bl[2], bl[3], &B.gl[warp][ks * 16 + kl][p * 16 + bcol]);
+            mma_bf16(acc[2 * p], ah[0], ah[1], ah[2], ah[3], bh[0], bh[1]);
+            mma_bf16(acc[2 * p], al[0], al[1], al[2], al[3], bh[0], bh[1]);
+            mma_bf16(acc[2 * p], ah[0], ah[1], ah[2], ah[3], bl[0], bl[1]);
+            mma_bf16(acc[2 * p + 1], ah[0], ah[1], ah[2], ah[3], bh[2], bh[3]);
+            mma_bf16(acc[2 * p + 1], al[0], al[1], al[2], al[3], bh[2], bh[3]);
+            mma_bf16(acc[2 * p + 1], ah[0], ah[1], ah[2], ah[3], bl[2], bl[3]);
+        }
+    }
+    // D fragment: Gaussian rows lane/4 (+8), channel columns 2(lane%4) (+1)
+#pragma unroll
+    for (int t = 0; t < GP / 8; ++t)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int j = (lane >> 2) + ((e >> 1) << 3), c = t * 8 + 2 * (lane & 3) + (e & 1);
+            if (j < cnt && c < C) atomicAdd(&d_feat[(size_t)B.gid[warp][j] * C + c], acc[t][e]);
+        }
+    __syncwarp();
+}
+
 // A8: reverse traversal from each pixel's last blended Gaussian, with the
 // transmittance in front of each Gaussian recomputed by division from the
 // saved final transmittance.  The blend decisions repeat the forward's
@@ -480,6 +542,7 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     Header *s_hdr = reinterpret_cast<Header *>(smem);
     FT *s_feat = reinterpret_cast<FT *>(smem + CT * sizeof(Header));
+    BwdGroup<CP> &BG = *reinterpret_cast<BwdGroup<CP> *>(smem + CT * sizeof(Header) + (size_t)CT * CP * sizeof(FT));
     __shared__ uint32_t s_max[CT / 32];
     __shared__ uint32_t s_id[CT];
     const FT *feat = reinterpret_cast<const FT *>(a.feat);
@@ -513,6 +576,15 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
         for (int c = 0; c < CP; ++c)
             if (c < a.C) g[c] = a.dF[c * HW + pix];
     }
+    // this pixel's row of G for the feature-gradient products (hi + lo)
+#pragma unroll
+    for (int c = 0; c < BwdGroup<CP>::GP; ++c) {
+        const float v = c < CP ? g[c] : 0.0f;
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        BG.gh[warp][lane][c] = h;
+        BG.gl[warp][lane][c] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
+    int gs = 0;  // contributing Gaussians collected in this warp's current group
     const uint32_t wmax = __reduce_max_sync(FULL, lastk);
     if (lane == 0) s_max[warp] = wmax;
     __syncthreads();
@@ -580,20 +652,14 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
                     }
                 }
                 const uint32_t id = s_id[j];
-                if (a.d_feat) {
-                    float v[CP];
-#pragma unroll
-                    for (int c = 0; c < CP; ++c) v[c] = wgt * g[c];
-                    warp_transpose_sum<CP>(v, lane);
-                    if (CP >= 32) {
-#pragma unroll
-                        for (int i = 0; i < (CP >= 32 ? CP / 32 : 1); ++i) {
-                            const int c = lane * (CP / 32) + i;
-                            if (c < a.C) atomicAdd(&a.d_feat[(size_t)id * a.C + c], v[i]);
-                        }
-                    } else {
-                        const int c = lane / (32 / CP);
-                        if ((lane & (32 / CP - 1)) == 0 && c < a.C) atomicAdd(&a.d_feat[(size_t)id * a.C + c], v[0]);
+                if (a.d_feat) {  // collect w for the group's tensor-core product
+                    const __nv_bfloat16 wh = __float2bfloat16_rn(wgt);
+                    BG.wh[warp][lane][gs] = wh;
+                    BG.wl[warp][lane][gs] = __float2bfloat16_rn(wgt - __bfloat162float(wh));
+                    if (lane == 0) BG.gid[warp][gs] = id;
+                    if (++gs == 16) {
+                        flush_feat_grads<CP>(BG, warp, lane, 16, a.C, a.d_feat);
+                        gs = 0;
                     }
                 }
                 const float ca = -2.0f * h0.z, cb = -h0.w, cc = -2.0f * h1.x;  // conic from the record
@@ -609,6 +675,10 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
                     if (dst) atomicAdd(dst, gv[0]);
                 }
             }
+        }
+        if (gs > 0) {  // before the next batch replaces the staged ids
+            flush_feat_grads<CP>(BG, warp, lane, gs, a.C, a.d_feat);
+            gs = 0;
         }
     }
 }
@@ -631,7 +701,7 @@ void run_composite(const CompositeArgs &a, cudaStream_t s) {
 
 template <int CP, typename FT>
 void run_backward(const BackwardArgs &a, cudaStream_t s) {
-    const size_t smem = CT * sizeof(Header) + (size_t)CT * CP * sizeof(FT);
+    const size_t smem = CT * sizeof(Header) + (size_t)CT * CP * sizeof(FT) + sizeof(BwdGroup<CP>);
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_backward<CP, FT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
