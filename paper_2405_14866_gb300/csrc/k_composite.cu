@@ -543,7 +543,6 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
     Header *s_hdr = reinterpret_cast<Header *>(smem);
     FT *s_feat = reinterpret_cast<FT *>(smem + CT * sizeof(Header));
     BwdGroup<CP> &BG = *reinterpret_cast<BwdGroup<CP> *>(smem + CT * sizeof(Header) + (size_t)CT * CP * sizeof(FT));
-    __shared__ uint32_t s_max[CT / 32];
     __shared__ uint32_t s_id[CT];
     const FT *feat = reinterpret_cast<const FT *>(a.feat);
 
@@ -586,40 +585,37 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
     }
     int gs = 0;  // contributing Gaussians collected in this warp's current group
     const uint32_t wmax = __reduce_max_sync(FULL, lastk);
-    if (lane == 0) s_max[warp] = wmax;
-    __syncthreads();
-    uint32_t nmax = 0;
-#pragma unroll
-    for (int w = 0; w < CT / 32; ++w) nmax = max(nmax, s_max[w]);
+    __syncthreads();  // zeroed feature padding visible to every warp
     float sg = 0.0f;  // <S, g>: blended features behind the current Gaussian
-
-    for (int hi = (int)nmax; hi > 0; hi -= CT) {
-        const int lo = max(0, hi - CT);
-        __syncthreads();
-        if (lo + tid < hi) {
-            const uint32_t id = a.ids[rg.x + lo + tid];
-            s_id[tid] = id;
-            stage<CP, FT>(a.hdr, feat, a.C, vec_ok, id, s_hdr, s_feat, tid);
-        }
-        __syncthreads();
-        const int cnt = hi - lo;
-        if (wmax <= (uint32_t)lo) continue;  // nothing of this batch blended in this warp
-        for (int c1 = cnt; c1 > 0; c1 -= 32) {
+    // Each warp walks its own list range [0, wmax) back to front in chunks of
+    // 32, staged into its own slice of shared memory: no block-wide barrier,
+    // so a warp whose pixels stopped early does not wait for the others.
+    Header *w_hdr = s_hdr + warp * 32;
+    FT *w_feat = s_feat + (size_t)warp * 32 * CP;
+    uint32_t *w_id = s_id + warp * 32;
+    {
+        for (int c1 = (int)wmax; c1 > 0; c1 -= 32) {
             const int c0 = max(0, c1 - 32);
+            __syncwarp();
+            if (c0 + lane < c1) {
+                const uint32_t gid = a.ids[rg.x + c0 + lane];
+                w_id[lane] = gid;
+                stage<CP, FT>(a.hdr, feat, a.C, vec_ok, gid, w_hdr, w_feat, lane);
+            }
+            __syncwarp();
             bool rel = false;
-            const int jj = c0 + lane;
-            if (jj < c1) {
-                const Header h = s_hdr[jj];
+            if (c0 + lane < c1) {
+                const Header h = w_hdr[lane];
                 rel = (h.h0.x + h.h1.z >= fbx0) && (h.h0.x - h.h1.z <= fbx1) && (h.h0.y + h.h1.w >= fby0) &&
                       (h.h0.y - h.h1.w <= fby1);
             }
             uint32_t m = __ballot_sync(FULL, rel);
             while (m) {
-                const int j = c0 + 31 - __clz(m);  // highest first: back to front
-                m &= ~(1u << (j - c0));
-                const uint32_t k = (uint32_t)(lo + j);
-                const float4 h0 = s_hdr[j].h0;
-                const float4 h1 = s_hdr[j].h1;
+                const int j = 31 - __clz(m);  // highest first: back to front
+                m &= ~(1u << j);
+                const uint32_t k = (uint32_t)(c0 + j);
+                const float4 h0 = w_hdr[j].h0;
+                const float4 h1 = w_hdr[j].h1;
                 const float dx = fpx - h0.x, dy = fpy - h0.y;
                 const float q = gauss_q(dx, dy, h0.z, h0.w, h1.x);
                 bool contrib = false;
@@ -634,7 +630,7 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
                 }
                 if (!__any_sync(FULL, contrib)) continue;
                 float f[CP];
-                FeatIO<FT>::template load<CP>(f, s_feat + (size_t)j * CP);
+                FeatIO<FT>::template load<CP>(f, w_feat + (size_t)j * CP);
                 float wgt = 0.0f, d_o = 0.0f, dq = 0.0f;
                 if (contrib) {
                     const float inv = __frcp_rn(1.0f - al);
@@ -651,7 +647,7 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
                         dq = al * dal;
                     }
                 }
-                const uint32_t id = s_id[j];
+                const uint32_t id = w_id[j];
                 if (a.d_feat) {  // collect w for the group's tensor-core product
                     const __nv_bfloat16 wh = __float2bfloat16_rn(wgt);
                     BG.wh[warp][lane][gs] = wh;
@@ -676,11 +672,8 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
                 }
             }
         }
-        if (gs > 0) {  // before the next batch replaces the staged ids
-            flush_feat_grads<CP>(BG, warp, lane, gs, a.C, a.d_feat);
-            gs = 0;
-        }
     }
+    if (gs > 0) flush_feat_grads<CP>(BG, warp, lane, gs, a.C, a.d_feat);
 }
 
 template <int CP, bool F32F, bool SAVE>
