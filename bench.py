@@ -624,9 +624,9 @@ def run_ours(args):
                         d[key].copy_(t, non_blocking=True)
                 ev_in[b].record(cs)
             ks.wait_event(ev_in[b])
-            ks.wait_event(ev_read[b])
             g.build_into(view_sets[b], stream=ks)
             ev_free[b].record(ks)
+            ks.wait_event(ev_read[b])  # the outputs of step k - 2 have been copied out
             ctx.render(g, cam, async_=True, out_feat=outs[b][0], out_alpha=outs[b][1], stream=ks)
             ev_out[b].record(ks)
             with torch.cuda.stream(ds):

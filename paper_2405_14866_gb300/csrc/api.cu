@@ -134,7 +134,7 @@ struct tsplat_ctx {
 
 namespace {
 enum { SM_KMIN = 0, SM_KMAX = 1, SM_NVIS = 2, SM_NPASS = 3, SM_P = 4, SM_PEFF = 5, SM_STATUS = 6, SM_TILECTR = 7,
-       SM_N = 8, SM_NINST = 9, SM_SORTCTR = 10 /* 4 words */, SM_TOTALS = 16, SM_WORDS = 16 + 4 * 256 };
+       SM_N = 8, SM_NINST = 9, SM_SORTCTR = 10 /* 4 words */, SM_BWDCTR = 14, SM_TOTALS = 16, SM_WORDS = 16 + 4 * 256 };
 uint32_t *small_ptr(tsplat_ctx *c, int w) { return c->small.as<uint32_t>() + w; }
 }  // namespace
 
@@ -746,6 +746,8 @@ tsplat_status tsplat_backward(tsplat_ctx *c, const float *dL_dfeat, const float 
     b.d_conic = d_conic;
     b.d_opac = d_opac;
     b.d_feat = d_feat;
+    b.unit_counter = small_ptr(c, SM_BWDCTR);
+    TRY_CUDA(cudaMemsetAsync(b.unit_counter, 0, sizeof(uint32_t), s));
     launch_backward(b, s);
     return check_launch("backward");
 }

@@ -203,6 +203,7 @@ struct BackwardArgs {
     float *d_conic;
     float *d_opac;
     float *d_feat;
+    uint32_t *unit_counter;  // next (tile, warp block) unit to hand out (0 at launch)
 };
 void launch_backward(const BackwardArgs &a, cudaStream_t s);
 

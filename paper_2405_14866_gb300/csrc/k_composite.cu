@@ -547,17 +547,26 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
     const FT *feat = reinterpret_cast<const FT *>(a.feat);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int tile = blockIdx.x;
+    // each warp zeroes the channel padding of its own staging rows
+    if (a.C < CP)
+        for (int i = lane; i < 32 * CP; i += 32) s_feat[(size_t)warp * 32 * CP + i] = FT(0.0f);
+    __syncwarp();
+    const int n_units = a.tiles_x * a.tiles_y * 8;
+    // Persistent: every warp takes (tile, 8x4 block) units from a counter, so
+    // the load balances at warp granularity whatever the tiles' list lengths.
+    for (;;) {
+    uint32_t unit = 0;
+    if (lane == 0) unit = atomicAdd(a.unit_counter, 1u);
+    unit = __shfl_sync(FULL, unit, 0);
+    if (unit >= (uint32_t)n_units) break;
+    const int tile = (int)(unit >> 3), wb = (int)(unit & 7);
     const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
-    const int bx0 = tx * TILE + (warp & 1) * 8, by0 = ty * TILE + (warp >> 1) * 4;
+    const int bx0 = tx * TILE + (wb & 1) * 8, by0 = ty * TILE + (wb >> 1) * 4;
     const int px = bx0 + (lane & 7), py = by0 + (lane >> 3);
     const bool inside = px < a.W && py < a.H;
     const float fpx = (float)px, fpy = (float)py;
     const float fbx0 = (float)bx0, fbx1 = (float)(bx0 + 7), fby0 = (float)by0, fby1 = (float)(by0 + 3);
     const size_t HW = (size_t)a.W * a.H, pix = (size_t)py * a.W + px;
-
-    if (a.C < CP)
-        for (int i = tid; i < CT * CP; i += CT) s_feat[i] = FT(0.0f);
     const uint2 rg = a.ranges[tile];
     const bool vec_ok = (a.C % FeatIO<FT>::VEC) == 0;
 
@@ -585,7 +594,6 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
     }
     int gs = 0;  // contributing Gaussians collected in this warp's current group
     const uint32_t wmax = __reduce_max_sync(FULL, lastk);
-    __syncthreads();  // zeroed feature padding visible to every warp
     float sg = 0.0f;  // <S, g>: blended features behind the current Gaussian
     // Each warp walks its own list range [0, wmax) back to front in chunks of
     // 32, staged into its own slice of shared memory: no block-wide barrier,
@@ -674,6 +682,7 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
         }
     }
     if (gs > 0) flush_feat_grads<CP>(BG, warp, lane, gs, a.C, a.d_feat);
+    }
 }
 
 template <int CP, bool F32F, bool SAVE>
@@ -700,7 +709,15 @@ void run_backward(const BackwardArgs &a, cudaStream_t s) {
         cudaFuncSetAttribute(k_backward<CP, FT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
     }
-    k_backward<CP, FT><<<a.tiles_x * a.tiles_y, CT, smem, s>>>(a);
+    static int grid = 0;
+    if (!grid) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_backward<CP, FT>, CT, smem);
+        grid = std::max(1, sms) * std::max(1, per_sm);
+    }
+    k_backward<CP, FT><<<std::min(grid, std::max(1, a.tiles_x * a.tiles_y)), CT, smem, s>>>(a);
     note_launches(1);
 }
 
