@@ -183,6 +183,16 @@ def project_f32(g32: Gaussians, cam, par=None) -> Projected:
     return out
 
 
+def zbuffer(mean: np.ndarray, cam):
+    """Point z-buffer of the (N,3) FP32 points: (depth (H,W) f32, 0 where
+    empty; id (H,W) int32, -1 where empty)."""
+    mean = np.ascontiguousarray(mean, np.float32)
+    depth = np.empty((cam.height, cam.width), np.float32)
+    ids = np.empty((cam.height, cam.width), np.int32)
+    lib().orc_zbuffer(_i64(mean.shape[0]), _p(mean), _p(cam_array(cam)), _p(depth), _p(ids))
+    return depth, ids
+
+
 def project_f64(g: Gaussians, cam, par=None):
     """Returns (mu (N,2), conic (N,3), depth (N,), visible (N,) bool) in FP64."""
     par = params_array() if par is None else par

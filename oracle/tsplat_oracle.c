@@ -272,6 +272,51 @@ void orc_project_f32(int64_t n, const float *mean, const float *cov, const float
     }
 }
 
+/* Point z-buffer.  Tele-Aloha lifts one view's depth map to points and
+ * rasterizes them into other cameras, reading the z-buffer out (Sec. 4.1,
+ * cascaded disparity initialisation), and warps the predicted depth maps
+ * onto the novel view (Sec. 4.3, fused depth).  A point is the Gaussian
+ * mean: its camera-space depth pz and image position (mx, my) follow the
+ * single-precision operations of orc_project_f32; it lands on the pixel whose
+ * centre is nearest, (floor(mx + 0.5), floor(my + 0.5)), when pz lies in
+ * (z_near, z_far) and the pixel is inside the image.  Each pixel keeps the
+ * point of smallest pz (FP32 bits compared as integers, the same order for
+ * positive depths), the lowest id among equal depths.
+ *   depth: H*W f32, 0 where no point landed; id: H*W int32, -1 there. */
+void orc_zbuffer(int64_t n, const float *mean, const float *cam, float *depth, int32_t *id)
+{
+    const float fx = cam[0], fy = cam[1], cx = cam[2], cy = cam[3];
+    const int W = (int)cam[4], H = (int)cam[5];
+    const float *R = cam + 6, *t = cam + 15;
+    const float znear = cam[18], zfar = cam[19];
+    uint32_t *best = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)W * (size_t)H);
+    for (int64_t p = 0; p < (int64_t)W * H; ++p) {
+        depth[p] = 0.0f;
+        id[p] = -1;
+        best[p] = 0xFFFFFFFFu;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        const float x = mean[3 * i], y = mean[3 * i + 1], z = mean[3 * i + 2];
+        const float px = ((R[0] * x + R[1] * y) + R[2] * z) + t[0];
+        const float py = ((R[3] * x + R[4] * y) + R[5] * z) + t[1];
+        const float pz = ((R[6] * x + R[7] * y) + R[8] * z) + t[2];
+        if (!(pz > znear && pz < zfar)) continue;
+        const float mx = (fx * px) / pz + cx;
+        const float my = (fy * py) / pz + cy;
+        const float fu = floorf(mx + 0.5f), fv = floorf(my + 0.5f);
+        if (!(fu >= 0.0f && fu < (float)W && fv >= 0.0f && fv < (float)H)) continue;
+        const int64_t p = (int64_t)fv * W + (int64_t)fu;
+        uint32_t bits;
+        memcpy(&bits, &pz, 4);
+        if (bits < best[p]) {  /* ids arrive in increasing order: ties keep the first */
+            best[p] = bits;
+            depth[p] = pz;
+            id[p] = (int32_t)i;
+        }
+    }
+    free(best);
+}
+
 /* The same projection in double precision (used for the compositing
  * values; binning decisions come from the key mode above).  `visible` is
  * set when the double-precision determinant is positive and finite. */

@@ -200,3 +200,27 @@ def test_build_from_bf16_feature_maps_equals_fp32_maps():
     assert a.keys() == b.keys()
     for k in a:
         assert torch.equal(a[k], b[k]), k
+
+
+def test_large_ragged_image_three_tile_digit_passes():
+    """4500 x 4500 target (282 x 282 = 79,524 tiles: 17-bit tile ids, so the
+    tile sort takes three digit passes; ragged last tile row and column):
+    bins bit-exact, feature map on sampled tiles, including the ragged ones."""
+    cam = gen.make_camera(2200.0, 4500, 4500, (0, 0, 0), np.eye(3))
+    gs = gen.random_gaussians(21, 30000, 3, center=(0, 0, 1.6), spread=0.75, sigma_range=(0.0005, 0.004))
+    g32 = O.Gaussians(gs.mean, gs.cov, gs.opac, gs.feat)
+    g = P.gpu_gaussians(g32)
+    ctx, F, A = _render(g, cam, save=False)
+    pr = O.project_f32(g32, cam, PAR)
+    bins = O.bin_gaussians(pr, cam.width, cam.height)
+    assert ctx.stats()["n_pairs"] == bins.P > 30000
+    assert np.array_equal(ctx.export("pairs").cpu().numpy().view(np.uint32), bins.ids)
+    assert np.array_equal(ctx.export("ranges").cpu().numpy().view(np.uint32), bins.ranges)
+    counts = bins.ranges[:, 1].astype(np.int64) - bins.ranges[:, 0]
+    tx = (cam.width + 15) // 16
+    rng = np.random.default_rng(3)
+    busy = np.argsort(-counts)[:6].tolist()
+    ragged = [tx * tx - 1, tx * (tx // 2) + tx - 1, (tx - 1) * tx + tx // 2]
+    tiles = sorted(set(busy + ragged + rng.choice(tx * tx, 6, replace=False).tolist()))
+    orc = O.render(g32, cam, PAR, tiles=tiles)
+    P.compare_render(F, A, orc, g32, cam, PAR, P.TOL_F32, tiles=tiles)

@@ -559,3 +559,57 @@ def test_adjoint_matches_central_differences_frozen():
             assert abs(fd - an) <= 1e-5 * max(abs(an), abs(fd), 1e-3), (j, k, idx, fd, an)
             nchk += 1
     assert nchk == 84
+
+
+# ---------------------------------------------------------------------------
+# point z-buffer (Sec. 4.1 z-buffers at other cameras; Sec. 4.3 fused depth)
+# ---------------------------------------------------------------------------
+
+def test_zbuffer_source_camera_returns_source_depth_map():
+    """Points lifted from a depth map and z-buffered into the same camera land
+    back on their own pixels: the z-buffer is the source depth map and the id
+    of each pixel is its own Gaussian (every pixel is foreground here)."""
+    sc = gen.scene_tiny()
+    v = sc.views[0]
+    g = O.lift_scene(sc, "f32")
+    depth, ids = O.zbuffer(g.mean, v.cam)
+    H, W = v.depth.shape
+    assert np.array_equal(ids.reshape(-1), np.arange(H * W))
+    assert np.array_equal(depth.view(np.uint32), np.ascontiguousarray(v.depth, np.float32).view(np.uint32))
+
+
+def test_zbuffer_rotated_source_camera_roundtrip():
+    """Same round trip through a rotated, translated camera: every point lands
+    on its own pixel; depths agree to single-precision rounding."""
+    sc = gen.scene_paper(seed=3, res=48, C=2)
+    v = sc.views[0]
+    g = O.lift_view(v, "f32")
+    depth, ids = O.zbuffer(g.mean, v.cam)
+    fg = np.argwhere(v.mask.reshape(-1) > 0)[:, 0]
+    assert np.array_equal(np.sort(ids[ids >= 0]), np.arange(len(fg)))
+    assert np.array_equal(np.argwhere(ids.reshape(-1) >= 0)[:, 0], fg)
+    d = v.depth.reshape(-1)[fg]
+    got = depth.reshape(-1)[fg]
+    assert np.allclose(got, d, rtol=2e-6, atol=0)
+
+
+def test_zbuffer_hand_worked():
+    cam = gen.make_camera(8.0, 8, 8, (0, 0, 0), np.eye(3), cx=4.0, cy=4.0)
+    pts = np.array([
+        [0.0, 0.0, 2.0],        # 0: pixel (4, 4), depth 2
+        [0.0, 0.0, 1.5],        # 1: same pixel, nearer: wins
+        [0.125, 0.0, 1.0],      # 2: x = 8 * 0.125 + 4 = 5 -> pixel (5, 4)
+        [0.125, 0.0, 1.0],      # 3: same pixel and depth: the lower id (2) stays
+        [0.0, 0.0, -1.0],       # 4: behind the camera
+        [1.0, 0.0, 1.0],        # 5: x = 12, outside the image
+        [-0.1875, 0.0, 1.0],    # 6: x = 2.5 exactly -> floor(3.0) = pixel (3, 4)
+        [0.0, 0.0, 0.1],        # 7: nearer than z_near = 0.2
+    ], np.float32)
+    depth, ids = O.zbuffer(pts, cam)
+    exp_ids = np.full((8, 8), -1, np.int32)
+    exp_depth = np.zeros((8, 8), np.float32)
+    exp_ids[4, 4], exp_depth[4, 4] = 1, 1.5
+    exp_ids[4, 5], exp_depth[4, 5] = 2, 1.0
+    exp_ids[4, 3], exp_depth[4, 3] = 6, 1.0
+    assert np.array_equal(ids, exp_ids)
+    assert np.array_equal(depth, exp_depth)
