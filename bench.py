@@ -666,6 +666,24 @@ def run_ours(args):
                "inputs": "four 1024^2 source views: depth, mask, scale, quaternion, opacity f32/u8, features BF16",
                "h2d_gbs_one_buffer": 4 * big.numel() / (c0.elapsed_time(c1) * 1e-3) / 1e9}
 
+    # point z-buffer of the frame's 2.1M means into the target (Sec. 4.1 / 4.3)
+    ZD = torch.empty((cam.height, cam.width), device="cuda")
+    ZI = torch.empty((cam.height, cam.width), device="cuda", dtype=torch.int32)
+    for _ in range(3):
+        ctx.zbuffer(g, cam, ZD, ZI)
+    z0, z1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    z0.record()
+    for _ in range(20):
+        ctx.zbuffer(g, cam, ZD, ZI)
+    z1.record()
+    torch.cuda.synchronize()
+    zb_ms = z0.elapsed_time(z1) / 20
+    zb_bytes = N * 16 + cam.width * cam.height * (8 + 8 + 8)  # means read; keys cleared, read; depth + id written
+    zbuffer = {"ms": zb_ms, "points_per_s": N / (zb_ms * 1e-3),
+               "roofline": {"bound": "hbm", "achieved": zb_bytes / (zb_ms * 1e-3) / 1e9, "peak": peak,
+                            "unit": "GB/s", "frac": zb_bytes / (zb_ms * 1e-3) / 1e9 / peak,
+                            "algorithmic_bytes": zb_bytes}}
+
     serving = None
     if not args.no_serving and args.workload == "precision":
         serving = serving_bench(api, torch, sc, g, views)
@@ -697,7 +715,7 @@ def run_ours(args):
                 "build_ms": build_ms, "build_gbs": build_bytes / (build_ms * 1e-3) / 1e9,
                 "gaussians_per_s": value * N,
                 "stages_ms": stages, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-                "serving": serving, "differentiation": diff,
+                "serving": serving, "differentiation": diff, "zbuffer": zbuffer,
                 "gpu_launches": int(launches)}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -299,6 +299,21 @@ tsplat_status tsplat_rasterize(int64_t n, const float *mean2d, const float *coni
                                float *out_feat, float *out_alpha, tsplat_ctx *ctx, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Point z-buffer (Sec. 4.1: the points lifted from one view's depth map are
+ * rasterized into other cameras and their z-buffer is read out; Sec. 4.3:
+ * predicted depth maps are warped onto the novel view).  Each Gaussian mean
+ * is projected into `cam` (the projection's single-precision operations)
+ * and lands on the pixel with the nearest centre, (floor(x + 0.5),
+ * floor(y + 0.5)), when its camera-space depth lies in (z_near, z_far).
+ * Each pixel keeps the nearest point, the lowest Gaussian id among equal
+ * depths.  out_depth: device H x W f32, 0 where no point landed;
+ * out_id: device H x W int32, -1 there, or NULL.  Scratch (8 B per pixel)
+ * comes from `ctx`.  Asynchronous on `stream`.
+ * ---------------------------------------------------------------------- */
+tsplat_status tsplat_zbuffer(const tsplat_gaussians *g, const tsplat_camera *cam, float *out_depth,
+                             int32_t *out_id, tsplat_ctx *ctx, void *stream);
+
+/* ------------------------------------------------------------------------
  * A8 -- backward of A7 (Sec. 4.2: R_G is differentiable; the encoder and
  * decoder are trained through it).  Needs a render or rasterize on `ctx`
  * with TSPLAT_RENDER_SAVE.  With g = dL/dF(p), gA = dL/dA(p), T_j the

@@ -93,6 +93,7 @@ _SIGS = {
     "tsplat_server_poll": (c_int32, [c_void_p, ctypes.c_uint64, POINTER(ctypes.c_double)]),
     "tsplat_server_wait": (c_int32, [c_void_p, ctypes.c_uint64, ctypes.c_double, POINTER(ctypes.c_double)]),
     "tsplat_server_release_frame": (c_int32, [c_void_p, c_void_p, ctypes.c_double]),
+    "tsplat_zbuffer": (c_int32, [c_void_p, POINTER(CCamera), c_void_p, c_void_p, c_void_p, c_void_p]),
     "tsplat_server_prepare": (c_int32, [c_void_p, c_void_p, ctypes.c_double]),
     "tsplat_server_get_stats": (c_int32, [c_void_p, POINTER(CServerStats)]),
     "tsplat_server_reset_stats": (c_int32, [c_void_p]),

@@ -254,6 +254,18 @@ class Context:
                *(_ptr(o) for o in outs), _stream(stream))
         return outs
 
+    def zbuffer(self, g: Gaussians, cam, out_depth=None, out_id=None, stream=None):
+        """Point z-buffer of g's means in `cam`: (depth (H,W) f32, 0 where empty;
+        id (H,W) int32, -1 where empty)."""
+        cc = ccamera(cam)
+        if out_depth is None:
+            out_depth = torch.empty((cc.height, cc.width), device="cuda")
+        if out_id is None:
+            out_id = torch.empty((cc.height, cc.width), device="cuda", dtype=torch.int32)
+        L.call("tsplat_zbuffer", g.handle, ctypes.byref(cc), _ptr(out_depth), _ptr(out_id), self.handle,
+               _stream(stream))
+        return out_depth, out_id
+
     def timings(self) -> Dict[str, float]:
         """Stage durations (ms) of the last profiled render (synchronizes)."""
         ms = (ctypes.c_float * len(L.STAGES))()

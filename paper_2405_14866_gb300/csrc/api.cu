@@ -111,6 +111,7 @@ struct tsplat_ctx {
     DBuf pk0, pk1, pv0, pv1, hist_p;
     // tiles / pixels / view table
     DBuf ranges, tfinal, last, views;
+    DBuf zkeys;  // point z-buffer scratch
     // small words: kminmax[2], n_vis, npass, p_dev, p_eff, status, n_dev, totals[4*256]
     DBuf small;
     uint32_t *host_small = nullptr;  // pinned mirror
@@ -335,7 +336,7 @@ tsplat_status tsplat_ctx_destroy(tsplat_ctx *c) {
     cudaDeviceSynchronize();
     DBuf *bufs[] = {&c->hdr, &c->rect, &c->ntiles, &c->dkey, &c->radius, &c->skeys0, &c->skeys1, &c->svals0,
                     &c->svals1, &c->hist_n, &c->emit_blk, &c->pk0, &c->pk1, &c->pv0, &c->pv1, &c->hist_p,
-                    &c->ranges, &c->tfinal, &c->last, &c->views, &c->small};
+                    &c->ranges, &c->tfinal, &c->last, &c->views, &c->zkeys, &c->small};
     for (DBuf *b : bufs) release(*b);
     for (auto &row : c->ev)
         for (cudaEvent_t e : row)
@@ -676,6 +677,18 @@ tsplat_status render_batch_impl(const tsplat_gaussians *g, const tsplat_camera *
 }  // namespace tsp
 
 extern "C" {
+
+tsplat_status tsplat_zbuffer(const tsplat_gaussians *g, const tsplat_camera *cam, float *out_depth, int32_t *out_id,
+                             tsplat_ctx *ctx, void *stream) {
+    if (!g || !cam || !out_depth || !ctx) return fail(TSPLAT_ERR_INVALID_ARG, "zbuffer: NULL argument");
+    if (cam->width <= 0 || cam->height <= 0 || cam->width > 16383 || cam->height > 16383)
+        return fail(TSPLAT_ERR_INVALID_ARG, "zbuffer: image %dx%d", cam->width, cam->height);
+    cudaStream_t s = S(stream);
+    TRY(grow(ctx->zkeys, (size_t)cam->width * cam->height * 8, s));
+    launch_zbuffer(g->xyzo.as<float4>(), g->n_dev.as<uint32_t>(), g->cap, *cam, ctx->zkeys.as<unsigned long long>(),
+                   out_depth, out_id, s);
+    return check_launch("zbuffer");
+}
 
 tsplat_status tsplat_rasterize(int64_t n, const float *mean2d, const float *conic, const float *opac,
                                const float *depth, const int32_t *radius, const void *feat, int32_t C,

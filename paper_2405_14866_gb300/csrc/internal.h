@@ -243,6 +243,11 @@ tsplat_status render_batch_impl(const tsplat_gaussians *g, const tsplat_camera *
 void make_view_batch(const tsplat_camera *cams, int32_t n_views, float *const *out_feat, float *const *out_alpha,
                      ViewBatch &vb);
 
+// Point z-buffer of the Gaussian means into `cam`: keys = W*H scratch words,
+// depth / id = W*H outputs (id may be NULL).
+void launch_zbuffer(const float4 *xyzo, const uint32_t *n_dev, int64_t n_cap, const tsplat_camera &cam,
+                    unsigned long long *keys, float *depth, int32_t *id, cudaStream_t s);
+
 // small utilities
 void launch_fill_u32(uint32_t *p, uint32_t v, int64_t n, cudaStream_t s);
 void launch_scale_u32(const uint32_t *src, uint32_t k, uint32_t *dst, cudaStream_t s);  // *dst = *src * k
