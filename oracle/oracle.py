@@ -183,6 +183,39 @@ def project_f32(g32: Gaussians, cam, par=None) -> Projected:
     return out
 
 
+def project_backward(mean, cov, cam, g_mu, g_conic, par=None):
+    """Adjoint of project_f64: (dL/dmean (N,3), dL/dcov (N,6)) from dL/dmu (N,2)
+    and dL/dconic (N,3)."""
+    par = params_array() if par is None else par
+    mean = np.ascontiguousarray(mean, np.float64)
+    cov = np.ascontiguousarray(cov, np.float64)
+    n = mean.shape[0]
+    gm = np.empty((n, 3)); gc = np.empty((n, 6))
+    lib().orc_project_backward_f64(_i64(n), _p(mean), _p(cov), _p(cam_array(cam)), _p(par),
+                                   _p(np.ascontiguousarray(g_mu, np.float64)),
+                                   _p(np.ascontiguousarray(g_conic, np.float64)), _p(gm), _p(gc))
+    return gm, gc
+
+
+def lift_backward(view, g_mean, g_cov, g_op, g_ft):
+    """Adjoint of lift_view (FP64) for one source view: per-pixel gradients
+    dict(depth (H,W), scale (H,W,3), quat (H,W,4) or None, opacity (H,W),
+    feat (H,W,C)) from the per-Gaussian gradients."""
+    H, W = view.depth.shape
+    C = view.feat.shape[-1]
+    f32 = lambda a: None if a is None else np.ascontiguousarray(a, np.float32)
+    out = dict(depth=np.empty((H, W)), scale=np.empty((H, W, 3)),
+               quat=None if view.quat is None else np.empty((H, W, 4)), opacity=np.empty((H, W)),
+               feat=np.empty((H, W, C)))
+    mask = None if view.mask is None else np.ascontiguousarray(view.mask, np.uint8)
+    lib().orc_lift_backward_f64(ctypes.c_int(H), ctypes.c_int(W), ctypes.c_int(C), _p(f32(view.depth)), _p(mask),
+                                _p(f32(view.scale)), _p(f32(view.quat)), _p(cam_array(view.cam)),
+                                _p(np.ascontiguousarray(g_mean, np.float64)), _p(np.ascontiguousarray(g_cov, np.float64)),
+                                _p(np.ascontiguousarray(g_op, np.float64)), _p(np.ascontiguousarray(g_ft, np.float64)),
+                                _p(out["depth"]), _p(out["scale"]), _p(out["quat"]), _p(out["opacity"]), _p(out["feat"]))
+    return out
+
+
 def zbuffer(mean: np.ndarray, cam):
     """Point z-buffer of the (N,3) FP32 points: (depth (H,W) f32, 0 where
     empty; id (H,W) int32, -1 where empty)."""

@@ -367,6 +367,192 @@ void orc_project_f64(int64_t n, const double *mean, const double *cov, const flo
     }
 }
 
+/* Adjoint of orc_project_f64 (Sec. 4.2: the rasterizer is differentiated
+ * end to end, so gradients reach the 3D Gaussians).  Given dL/dmu (N x 2)
+ * and dL/d(conic) (N x 3, w.r.t. the stored (A, B, C) of
+ * q = -(A dx^2 + 2 B dx dy + C dy^2) / 2), returns dL/dmean (N x 3, world
+ * space) and dL/dcov (N x 6, w.r.t. the six stored entries of the
+ * symmetric 3D covariance).  The chain: p = R x + t; mu = f p_xy / p_z + c;
+ * J from p (x/z and y/z clamped: no gradient through a clamped ratio);
+ * S = (J R) V (J R)^T + lowpass I; conic = S^-1.  Gaussians that the
+ * forward culls (p_z <= 0, det <= 0) get zero. */
+void orc_project_backward_f64(int64_t n, const double *mean, const double *cov, const float *cam,
+                              const float *par, const double *g_mu, const double *g_conic,
+                              double *g_mean, double *g_cov)
+{
+    const double fx = cam[0], fy = cam[1];
+    const double W = cam[4], H = cam[5];
+    double R[9], t[3];
+    for (int k = 0; k < 9; ++k) R[k] = cam[6 + k];
+    for (int k = 0; k < 3; ++k) t[k] = cam[15 + k];
+    const double lp = par[0], clampv = par[4];
+    const double limx = clampv * (0.5 * W / fx), limy = clampv * (0.5 * H / fy);
+    for (int64_t i = 0; i < n; ++i) {
+        double *gm = g_mean + 3 * i, *gc = g_cov + 6 * i;
+        for (int k = 0; k < 3; ++k) gm[k] = 0;
+        for (int k = 0; k < 6; ++k) gc[k] = 0;
+        const double *m = mean + 3 * i;
+        double p[3];
+        for (int r = 0; r < 3; ++r) p[r] = R[3 * r] * m[0] + R[3 * r + 1] * m[1] + R[3 * r + 2] * m[2] + t[r];
+        if (!(p[2] > 0)) continue;
+        const double z = p[2];
+        const double rx = p[0] / z, ry = p[1] / z;
+        const int cx_in = rx > -limx && rx < limx, cy_in = ry > -limy && ry < limy;
+        const double txz = fmin(limx, fmax(-limx, rx)), tyz = fmin(limy, fmax(-limy, ry));
+        const double J00 = fx / z, J02 = -fx * txz / z, J11 = fy / z, J12 = -fy * tyz / z;
+        double T[2][3];
+        for (int j = 0; j < 3; ++j) {
+            T[0][j] = J00 * R[0 * 3 + j] + J02 * R[2 * 3 + j];
+            T[1][j] = J11 * R[1 * 3 + j] + J12 * R[2 * 3 + j];
+        }
+        const double *cv = cov + 6 * i;
+        const double V[3][3] = {{cv[0], cv[1], cv[2]}, {cv[1], cv[3], cv[4]}, {cv[2], cv[4], cv[5]}};
+        double VT0[3], VT1[3];  /* V t0, V t1 */
+        for (int k = 0; k < 3; ++k) {
+            VT0[k] = V[k][0] * T[0][0] + V[k][1] * T[0][1] + V[k][2] * T[0][2];
+            VT1[k] = V[k][0] * T[1][0] + V[k][1] * T[1][1] + V[k][2] * T[1][2];
+        }
+        const double S00 = T[0][0] * VT0[0] + T[0][1] * VT0[1] + T[0][2] * VT0[2];
+        const double S01 = T[0][0] * VT1[0] + T[0][1] * VT1[1] + T[0][2] * VT1[2];
+        const double S11 = T[1][0] * VT1[0] + T[1][1] * VT1[1] + T[1][2] * VT1[2];
+        const double a = S00 + lp, b = S01, c = S11 + lp;
+        const double D = a * c - b * b;
+        /* mean: mu = f p / z + c */
+        double gp[3] = {fx / z * g_mu[2 * i], fy / z * g_mu[2 * i + 1],
+                        -fx * p[0] / (z * z) * g_mu[2 * i] - fy * p[1] / (z * z) * g_mu[2 * i + 1]};
+        if (D > 0 && isfinite(D)) {
+            const double gA = g_conic[3 * i], gB = g_conic[3 * i + 1], gC = g_conic[3 * i + 2];
+            const double D2 = D * D;
+            /* A = c / D, B = -b / D, C = a / D, D = a c - b^2 */
+            const double ga = -gA * c * c / D2 + gB * b * c / D2 + gC * (1.0 / D - a * c / D2);
+            const double gb = gA * 2 * b * c / D2 + gB * (-1.0 / D - 2 * b * b / D2) + gC * 2 * a * b / D2;
+            const double gcc = gA * (1.0 / D - a * c / D2) + gB * a * b / D2 - gC * a * a / D2;
+            /* S00 = t0^T V t0, S01 = t0^T V t1, S11 = t1^T V t1 */
+            static const int ii[6] = {0, 0, 0, 1, 1, 2}, jj[6] = {0, 1, 2, 1, 2, 2};
+            for (int e = 0; e < 6; ++e) {
+                const int u = ii[e], v = jj[e];
+                double d00 = T[0][u] * T[0][v], d01 = T[0][u] * T[1][v], d11 = T[1][u] * T[1][v];
+                if (u != v) {
+                    d00 += T[0][v] * T[0][u];
+                    d01 += T[0][v] * T[1][u];
+                    d11 += T[1][v] * T[1][u];
+                }
+                gc[e] = ga * d00 + gb * d01 + gcc * d11;
+            }
+            double gt0[3], gt1[3];
+            for (int k = 0; k < 3; ++k) {
+                gt0[k] = 2 * ga * VT0[k] + gb * VT1[k];
+                gt1[k] = gb * VT0[k] + 2 * gcc * VT1[k];
+            }
+            double gJ00 = 0, gJ02 = 0, gJ11 = 0, gJ12 = 0;
+            for (int k = 0; k < 3; ++k) {
+                gJ00 += gt0[k] * R[0 * 3 + k];
+                gJ02 += gt0[k] * R[2 * 3 + k];
+                gJ11 += gt1[k] * R[1 * 3 + k];
+                gJ12 += gt1[k] * R[2 * 3 + k];
+            }
+            /* J00 = fx / z; J02 = -fx txz / z with txz = p_x / z when not clamped */
+            gp[2] += -fx / (z * z) * gJ00 - fy / (z * z) * gJ11;
+            if (cx_in) {
+                gp[0] += -fx / (z * z) * gJ02;
+                gp[2] += 2 * fx * p[0] / (z * z * z) * gJ02;
+            } else {
+                gp[2] += fx * txz / (z * z) * gJ02;
+            }
+            if (cy_in) {
+                gp[1] += -fy / (z * z) * gJ12;
+                gp[2] += 2 * fy * p[1] / (z * z * z) * gJ12;
+            } else {
+                gp[2] += fy * tyz / (z * z) * gJ12;
+            }
+        }
+        for (int k = 0; k < 3; ++k) gm[k] = R[0 * 3 + k] * gp[0] + R[1 * 3 + k] * gp[1] + R[2 * 3 + k] * gp[2];
+    }
+}
+
+/* Adjoint of orc_lift_f64 for one view (Sec. 4.2: lifting with the source
+ * camera; trained end to end, the gradients reach the encoder's depth,
+ * scale, opacity and feature maps).  Gaussian n is the n-th foreground pixel
+ * in row-major order.  Inputs dL/dmean (N x 3), dL/dcov (N x 6), dL/dopac
+ * (N), dL/dfeat (N x C); outputs per pixel (zero outside the mask):
+ * g_depth (H x W), g_scale (H x W x 3), g_quat (H x W x 4, w.r.t. the
+ * unnormalised quaternion; may be NULL), g_opac (H x W), g_feat (H x W x C).
+ * mean = Rs^T (z ray - ts), ray = ((u - cx)/fx, (v - cy)/fy, 1);
+ * cov = M M^T with M = Rs^T R(q^) diag(s), q^ = q / |q|. */
+void orc_lift_backward_f64(int H, int W, int C, const float *depth, const uint8_t *mask, const float *scale,
+                           const float *quat, const float *cam, const double *g_mean, const double *g_cov,
+                           const double *g_op, const double *g_ft, double *g_depth, double *g_scale,
+                           double *g_quat, double *g_opac, double *g_feat)
+{
+    const double fx = cam[0], fy = cam[1], cx = cam[2], cy = cam[3];
+    double Rs[9];
+    for (int k = 0; k < 9; ++k) Rs[k] = cam[6 + k];
+    int64_t n = 0;
+    for (int v = 0; v < H; ++v)
+        for (int u = 0; u < W; ++u) {
+            const int64_t p = (int64_t)v * W + u;
+            g_depth[p] = 0;
+            g_opac[p] = 0;
+            for (int k = 0; k < 3; ++k) g_scale[3 * p + k] = 0;
+            if (g_quat) for (int k = 0; k < 4; ++k) g_quat[4 * p + k] = 0;
+            for (int c = 0; c < C; ++c) g_feat[p * C + c] = 0;
+            if (mask && !mask[p]) continue;
+            const double ray[3] = {(u - cx) / fx, (v - cy) / fy, 1.0};
+            const double *gm = g_mean + 3 * n;
+            /* d mean / d z = Rs^T ray */
+            double gz = 0;
+            for (int i = 0; i < 3; ++i)
+                gz += (Rs[0 * 3 + i] * ray[0] + Rs[1 * 3 + i] * ray[1] + Rs[2 * 3 + i] * ray[2]) * gm[i];
+            g_depth[p] = gz;
+            double w = 1, x = 0, y = 0, zq = 0, nq = 1;
+            if (quat) { w = quat[4 * p]; x = quat[4 * p + 1]; y = quat[4 * p + 2]; zq = quat[4 * p + 3]; }
+            nq = sqrt(w * w + x * x + y * y + zq * zq);
+            w /= nq; x /= nq; y /= nq; zq /= nq;
+            const double Rq[3][3] = {
+                {1 - 2 * (y * y + zq * zq), 2 * (x * y - w * zq), 2 * (x * zq + w * y)},
+                {2 * (x * y + w * zq), 1 - 2 * (x * x + zq * zq), 2 * (y * zq - w * x)},
+                {2 * (x * zq - w * y), 2 * (y * zq + w * x), 1 - 2 * (x * x + y * y)}};
+            double Rg[3][3], M[3][3];
+            const double s3[3] = {scale[3 * p], scale[3 * p + 1], scale[3 * p + 2]};
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) {
+                    Rg[i][j] = Rs[0 * 3 + i] * Rq[0][j] + Rs[1 * 3 + i] * Rq[1][j] + Rs[2 * 3 + i] * Rq[2][j];
+                    M[i][j] = Rg[i][j] * s3[j];
+                }
+            /* symmetric gradient G of cov = M M^T from the six stored entries */
+            const double *gc = g_cov + 6 * n;
+            const double G[3][3] = {{gc[0], gc[1] / 2, gc[2] / 2}, {gc[1] / 2, gc[3], gc[4] / 2},
+                                    {gc[2] / 2, gc[4] / 2, gc[5]}};
+            double gM[3][3];  /* dL/dM = 2 G M */
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) gM[i][j] = 2 * (G[i][0] * M[0][j] + G[i][1] * M[1][j] + G[i][2] * M[2][j]);
+            for (int j = 0; j < 3; ++j) g_scale[3 * p + j] = gM[0][j] * Rg[0][j] + gM[1][j] * Rg[1][j] + gM[2][j] * Rg[2][j];
+            if (g_quat) {
+                double gRq[3][3];  /* R_g = Rs^T Rq, dL/dRg[i][j] = gM[i][j] s_j */
+                for (int k = 0; k < 3; ++k)
+                    for (int j = 0; j < 3; ++j)
+                        gRq[k][j] = (Rs[k * 3 + 0] * gM[0][j] + Rs[k * 3 + 1] * gM[1][j] + Rs[k * 3 + 2] * gM[2][j]) * s3[j];
+                /* d Rq / d (w, x, y, z) of the normalised quaternion */
+                const double gw = 2 * (-zq * gRq[0][1] + y * gRq[0][2] + zq * gRq[1][0] - x * gRq[1][2] - y * gRq[2][0] + x * gRq[2][1]);
+                const double gx = 2 * (y * gRq[0][1] + zq * gRq[0][2] + y * gRq[1][0] - 2 * x * gRq[1][1] - w * gRq[1][2]
+                                       + zq * gRq[2][0] + w * gRq[2][1] - 2 * x * gRq[2][2]);
+                const double gy = 2 * (-2 * y * gRq[0][0] + x * gRq[0][1] + w * gRq[0][2] + x * gRq[1][0] + zq * gRq[1][2]
+                                       - w * gRq[2][0] + zq * gRq[2][1] - 2 * y * gRq[2][2]);
+                const double gz2 = 2 * (-2 * zq * gRq[0][0] - w * gRq[0][1] + x * gRq[0][2] + w * gRq[1][0] - 2 * zq * gRq[1][1]
+                                        + y * gRq[1][2] + x * gRq[2][0] + y * gRq[2][1]);
+                /* through q^ = q / |q| */
+                const double dot = gw * w + gx * x + gy * y + gz2 * zq;
+                g_quat[4 * p] = (gw - w * dot) / nq;
+                g_quat[4 * p + 1] = (gx - x * dot) / nq;
+                g_quat[4 * p + 2] = (gy - y * dot) / nq;
+                g_quat[4 * p + 3] = (gz2 - zq * dot) / nq;
+            }
+            g_opac[p] = g_op[n];
+            for (int c = 0; c < C; ++c) g_feat[p * C + c] = g_ft[n * C + c];
+            ++n;
+        }
+}
+
 /* ------------------------------------------------------------------------
  * Binning: count, exclusive scan, key emission, stable sort, tile ranges.
  * A Gaussian emits one (key, id) pair per tile of its rect, tiles in

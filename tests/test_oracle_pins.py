@@ -613,3 +613,81 @@ def test_zbuffer_hand_worked():
     exp_ids[4, 3], exp_depth[4, 3] = 6, 1.0
     assert np.array_equal(ids, exp_ids)
     assert np.array_equal(depth, exp_depth)
+
+
+# ---------------------------------------------------------------------------
+# adjoints of projection and lifting (gradients to the 3D Gaussians and on
+# to the source maps): central differences of the FP64 forward
+# ---------------------------------------------------------------------------
+
+def _proj_loss(mean, cov, cam, w_mu, w_con):
+    mu, con, _, vis = O.project_f64(O.Gaussians(mean, cov, np.zeros(len(mean)), np.zeros((len(mean), 1))), cam)
+    return float((w_mu * mu).sum() + (w_con * con).sum())
+
+
+def test_projection_adjoint_matches_central_differences():
+    rng = np.random.default_rng(41)
+    cam = gen.make_camera(300.0, 320, 240, (0.05, -0.02, -0.1), gen.rot_y(7.0) @ gen.rot_x(-4.0), cx=161.0, cy=118.5)
+    gs = gen.random_gaussians(5, 12, 1, center=(0.05, 0.0, 1.4), spread=0.25, sigma_range=(0.01, 0.05))
+    mean = gs.mean.astype(np.float64)
+    mean[0] = [1.2, 0.1, 1.0]      # far off axis: x/z clamped (no gradient through the ratio)
+    mean[1] = [-0.1, -1.0, 0.9]    # y/z clamped
+    cov = gs.cov.astype(np.float64)
+    w_mu, w_con = rng.standard_normal((12, 2)), rng.standard_normal((12, 3))
+    gm, gc = O.project_backward(mean, cov, cam, w_mu, w_con)
+    for arr, g in ((mean, gm), (cov, gc)):
+        for idx in np.ndindex(arr.shape):
+            # steps relative to the Gaussian's scale (metres for means, the
+            # largest variance for covariances)
+            h = 1e-6 * max(1.0, abs(arr[idx])) if arr is mean else 1e-4 * cov[idx[0], [0, 3, 5]].max()
+            up, dn = arr.copy(), arr.copy()
+            up[idx] += h
+            dn[idx] -= h
+            args_up = (up, cov) if arr is mean else (mean, up)
+            args_dn = (dn, cov) if arr is mean else (mean, dn)
+            fd = (_proj_loss(*args_up, cam, w_mu, w_con) - _proj_loss(*args_dn, cam, w_mu, w_con)) / (2 * h)
+            scale = max(abs(g[idx]), np.abs(g).max() * 1e-3, 1e-9)
+            assert abs(fd - g[idx]) <= 1e-5 * scale, (idx, fd, g[idx])
+
+
+def _lift_loss(view, w):
+    g = O.lift_view(view, "f64")
+    return float((w["mean"] * g.mean).sum() + (w["cov"] * g.cov).sum() + (w["op"] * g.opac).sum()
+                 + (w["ft"] * g.feat).sum())
+
+
+def test_lift_adjoint_matches_central_differences():
+    rng = np.random.default_rng(43)
+    H, W, C = 5, 6, 2
+    cam = gen.make_camera(6.0, W, H, (0.1, -0.05, 0.02), gen.rot_y(10.0) @ gen.rot_x(5.0), cx=2.7, cy=2.2)
+    mask = (rng.uniform(size=(H, W)) > 0.3).astype(np.uint8)
+    quat = rng.standard_normal((H, W, 4)) * 0.3 + np.array([1.3, 0, 0, 0])
+    view = gen.SourceView(rng.uniform(0.8, 1.6, (H, W)).astype(np.float32), mask,
+                          rng.uniform(0.01, 0.05, (H, W, 3)).astype(np.float32), quat.astype(np.float32),
+                          rng.uniform(0.3, 0.9, (H, W)).astype(np.float32),
+                          rng.standard_normal((H, W, C)).astype(np.float32), cam)
+    n = int(mask.sum())
+    w = dict(mean=rng.standard_normal((n, 3)), cov=rng.standard_normal((n, 6)) * 50, op=rng.standard_normal(n),
+             ft=rng.standard_normal((n, C)))
+    g = O.lift_backward(view, w["mean"], w["cov"], w["op"], w["ft"])
+    for name, key in (("depth", "depth"), ("scale", "scale"), ("quat", "quat"), ("opacity", "opacity"),
+                      ("feat", "feat")):
+        arr = getattr(view, name)
+        grad = g[key]
+        for idx in np.ndindex(arr.shape):
+            if not mask[idx[0], idx[1]]:
+                assert grad[idx] == 0.0
+                continue
+            v = float(arr[idx])
+            h = 1e-3 * max(abs(v), 0.05)
+            up, dn = arr.copy(), arr.copy()
+            up[idx] = np.float32(v + h)
+            dn[idx] = np.float32(v - h)
+            step = float(up[idx]) - float(dn[idx])
+            vu = gen.SourceView(*(up if f == name else getattr(view, f) for f in
+                                  ("depth", "mask", "scale", "quat", "opacity", "feat", "cam")))
+            vd = gen.SourceView(*(dn if f == name else getattr(view, f) for f in
+                                  ("depth", "mask", "scale", "quat", "opacity", "feat", "cam")))
+            fd = (_lift_loss(vu, w) - _lift_loss(vd, w)) / step
+            scale = max(abs(grad[idx]), np.abs(grad).max() * 1e-3)
+            assert abs(fd - grad[idx]) <= 1e-4 * scale, (name, idx, fd, grad[idx])
