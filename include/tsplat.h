@@ -299,6 +299,41 @@ tsplat_status tsplat_rasterize(int64_t n, const float *mean2d, const float *coni
                                float *out_feat, float *out_alpha, tsplat_ctx *ctx, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Backward through the projection and the lifting (Sec. 4.2: the encoder
+ * is trained end to end through R_G), continuing tsplat_backward.
+ *
+ * tsplat_backward_project: dL/dmean3d (N x 3, world space) and dL/dcov3d
+ * (N x 6: the stored entries s00 s01 s02 s11 s12 s22) of the Gaussians in
+ * `g` from dL/dmean2d (N x 2) and dL/dconic (N x 3, the raw conic (A, B, C)
+ * of q = -(A dx^2 + 2 B dx dy + C dy^2) / 2, as tsplat_backward returns
+ * them).  Needs the last call on `ctx` to be a tsplat_render of `g` with
+ * TSPLAT_RENDER_SAVE (its camera and parameters are used).  The chain goes
+ * through mu = f p / z + c, the Jacobian (x/z and y/z clamped: no gradient
+ * through a clamped ratio), S = (J R) V (J R)^T + lowpass I and conic = S^-1.
+ *
+ * tsplat_build_backward: per source pixel gradients of the maps the store
+ * `g` was built from (`views` must be those of its last build): depth
+ * (H x W), scale (H x W x 3), quat (H x W x 4, w.r.t. the unnormalised
+ * quaternion; ignored when the view has no quat map), opacity (H x W),
+ * features (H x W x C, f32), from dL/dmean3d, dL/dcov3d, dL/dopac (N) and
+ * dL/dfeat (N x C).  Background pixels get zeros.  All device f32 buffers,
+ * overwritten; asynchronous on `stream`.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    float *depth;    /* H x W */
+    float *scale;    /* H x W x 3 */
+    float *quat;     /* H x W x 4, 16-byte aligned, or NULL */
+    float *opacity;  /* H x W */
+    float *feat;     /* H x W x C */
+} tsplat_src_grads;
+
+tsplat_status tsplat_backward_project(tsplat_ctx *ctx, const tsplat_gaussians *g, const float *d_mean2d,
+                                      const float *d_conic, float *d_mean3d, float *d_cov3d, void *stream);
+tsplat_status tsplat_build_backward(tsplat_gaussians *g, const tsplat_src_view *views, int32_t n_views,
+                                    const float *d_mean3d, const float *d_cov3d, const float *d_opac,
+                                    const float *d_feat, const tsplat_src_grads *grads, void *stream);
+
+/* ------------------------------------------------------------------------
  * Point z-buffer (Sec. 4.1: the points lifted from one view's depth map are
  * rasterized into other cameras and their z-buffer is read out; Sec. 4.3:
  * predicted depth maps are warped onto the novel view).  Each Gaussian mean

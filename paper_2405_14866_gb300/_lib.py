@@ -40,6 +40,11 @@ class CSrcView(Structure):
                 ("cam", CCamera)]
 
 
+class CSrcGrads(Structure):
+    _fields_ = [("depth", c_void_p), ("scale", c_void_p), ("quat", c_void_p), ("opacity", c_void_p),
+                ("feat", c_void_p)]
+
+
 class CServerConfig(Structure):
     _fields_ = [("max_views_per_batch", c_int32), ("max_lanes", c_int32), ("max_width", c_int32),
                 ("max_height", c_int32), ("max_gaussians", c_int64), ("C", c_int32), ("feat_dtype", c_int32),
@@ -85,6 +90,9 @@ _SIGS = {
                                    c_int32, c_int32, c_int32, POINTER(CParams), c_void_p, c_void_p, c_void_p,
                                    c_void_p]),
     "tsplat_backward": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "tsplat_backward_project": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "tsplat_build_backward": (c_int32, [c_void_p, POINTER(CSrcView), c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
+                                        POINTER(CSrcGrads), c_void_p]),
     "tsplat_server_config_default": (None, [POINTER(CServerConfig)]),
     "tsplat_server_create": (c_int32, [POINTER(CServerConfig), POINTER(c_void_p)]),
     "tsplat_server_destroy": (c_int32, [c_void_p]),

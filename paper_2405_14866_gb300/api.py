@@ -153,6 +153,26 @@ class Gaussians:
         arr = (L.CSrcView * len(views))(*views)
         L.call("tsplat_build_into_noalloc", self.handle, arr, len(views), _stream(stream))
 
+    def build_backward(self, views: Sequence[L.CSrcView], d_mean3d, d_cov3d, d_opac, d_feat, stream=None):
+        """Per-view gradients of the source maps this store was built from:
+        a list of dicts depth (H,W), scale (H,W,3), quat (H,W,4) or None,
+        opacity (H,W), feat (H,W,C)."""
+        dev = torch.device("cuda")
+        outs, structs = [], []
+        for v in views:
+            H, W = v.cam.height, v.cam.width
+            o = dict(depth=torch.empty((H, W), device=dev), scale=torch.empty((H, W, 3), device=dev),
+                     quat=torch.empty((H, W, 4), device=dev) if v.quat else None,
+                     opacity=torch.empty((H, W), device=dev), feat=torch.empty((H, W, self.C), device=dev))
+            outs.append(o)
+            structs.append(L.CSrcGrads(_ptr(o["depth"]), _ptr(o["scale"]), _ptr(o["quat"]), _ptr(o["opacity"]),
+                                       _ptr(o["feat"])))
+        arr = (L.CSrcView * len(views))(*views)
+        garr = (L.CSrcGrads * len(views))(*structs)
+        L.call("tsplat_build_backward", self.handle, arr, len(views), _ptr(d_mean3d.contiguous()),
+               _ptr(d_cov3d.contiguous()), _ptr(d_opac.contiguous()), _ptr(d_feat.contiguous()), garr, _stream(stream))
+        return outs
+
     def count(self) -> int:
         n = ctypes.c_int64()
         L.call("tsplat_gaussians_count", self.handle, ctypes.byref(n))
@@ -253,6 +273,16 @@ class Context:
         L.call("tsplat_backward", self.handle, _ptr(dF.contiguous()), _ptr(None if dA is None else dA.contiguous()),
                *(_ptr(o) for o in outs), _stream(stream))
         return outs
+
+    def backward_project(self, g: Gaussians, d_mean2d, d_conic, stream=None):
+        """dL/dmean3d (cap,3), dL/dcov3d (cap,6) from the 2D gradients of the last
+        render (tsplat_render with save=True) of `g`."""
+        dev = torch.device("cuda")
+        dm = torch.empty((g.capacity, 3), device=dev)
+        dc = torch.empty((g.capacity, 6), device=dev)
+        L.call("tsplat_backward_project", self.handle, g.handle, _ptr(d_mean2d.contiguous()),
+               _ptr(d_conic.contiguous()), _ptr(dm), _ptr(dc), _stream(stream))
+        return dm, dc
 
     def zbuffer(self, g: Gaussians, cam, out_depth=None, out_id=None, stream=None):
         """Point z-buffer of g's means in `cam`: (depth (H,W) f32, 0 where empty;

@@ -125,6 +125,9 @@ struct tsplat_ctx {
     const void *feat = nullptr;
     const uint32_t *pairs = nullptr;  // sorted Gaussian ids
     bool saved = false;
+    bool has_cam = false;        // the last render had a camera (tsplat_render)
+    tsplat_camera cam;
+    tsplat_render_params par;
     float alpha_max = 0, alpha_min = 0;
     // stage events of profiled renders (TSPLAT_RENDER_PROFILE): a ring of
     // the last RING renders, averaged and reset by tsplat_ctx_timings
@@ -256,9 +259,11 @@ tsplat_status tsplat_gaussians_get(const tsplat_gaussians *g, float *mean, float
     return check_launch("gaussians_get");
 }
 
-static tsplat_status build_into(tsplat_gaussians *g, const tsplat_src_view *views, int32_t n_views, cudaStream_t s) {
+// The lifting's launch arguments for `views` into the store g (also used by
+// the adjoint, which walks the same pixels in the same order).
+static tsplat_status build_args(tsplat_gaussians *g, const tsplat_src_view *views, int32_t n_views, BuildArgs &a,
+                                cudaStream_t s) {
     if (n_views < 1 || n_views > MAX_VIEWS) return fail(TSPLAT_ERR_INVALID_ARG, "n_views = %d not in [1, %d]", n_views, MAX_VIEWS);
-    BuildArgs a;
     memset(&a, 0, sizeof(a));
     int64_t total = 0;
     for (int v = 0; v < n_views; ++v) {
@@ -288,6 +293,12 @@ static tsplat_status build_into(tsplat_gaussians *g, const tsplat_src_view *view
     a.blk_cnt = g->blk.as<uint32_t>();
     a.blk_off = a.blk_cnt + a.nblocks;
     a.n_dev = g->n_dev.as<uint32_t>();
+    return TSPLAT_OK;
+}
+
+static tsplat_status build_into(tsplat_gaussians *g, const tsplat_src_view *views, int32_t n_views, cudaStream_t s) {
+    BuildArgs a;
+    TRY(build_args(g, views, n_views, a, s));
     launch_build(a, s);
     g->last_stream = s;
     return check_launch("build");
@@ -623,7 +634,11 @@ tsplat_status tsplat_render(const tsplat_gaussians *g, const tsplat_camera *cam,
     launch_project(g->xyzo.as<float4>(), g->cova.as<float4>(), g->covb.as<float2>(), g->n_dev.as<uint32_t>(), g->cap,
                    vb, ctx->views.as<RenderView>(), *params, o, s);
     TRY(check_launch("render: project"));
-    return render_tail(ctx, g->cap, g->n_dev.as<uint32_t>(), vb, g->feat.p, g->C, g->dtype, *params, s);
+    TRY(render_tail(ctx, g->cap, g->n_dev.as<uint32_t>(), vb, g->feat.p, g->C, g->dtype, *params, s));
+    ctx->has_cam = true;
+    ctx->cam = *cam;
+    ctx->par = *params;
+    return TSPLAT_OK;
 }
 
 tsplat_status tsplat_render_batch(const tsplat_gaussians *g, const tsplat_camera *cams, int32_t n_views,
@@ -672,11 +687,53 @@ tsplat_status render_batch_impl(const tsplat_gaussians *g, const tsplat_camera *
     launch_project(g->xyzo.as<float4>(), g->cova.as<float4>(), g->covb.as<float2>(), g->n_dev.as<uint32_t>(), g->cap,
                    vb, ctx->views.as<RenderView>(), *params, o, s, table_on_device);
     TRY(check_launch("render_batch: project"));
+    ctx->has_cam = false;
     return render_tail(ctx, g->cap, g->n_dev.as<uint32_t>(), vb, g->feat.p, g->C, g->dtype, *params, s);
 }
 }  // namespace tsp
 
 extern "C" {
+
+tsplat_status tsplat_backward_project(tsplat_ctx *c, const tsplat_gaussians *g, const float *d_mean2d,
+                                      const float *d_conic, float *d_mean3d, float *d_cov3d, void *stream) {
+    if (!c || !g || !d_mean2d || !d_conic || !d_mean3d || !d_cov3d)
+        return fail(TSPLAT_ERR_INVALID_ARG, "backward_project: NULL argument");
+    if (!c->saved || !c->has_cam)
+        return fail(TSPLAT_ERR_INVALID_ARG, "backward_project: the last render on this context was not a tsplat_render with TSPLAT_RENDER_SAVE");
+    if (c->n_dev != g->n_dev.as<uint32_t>())
+        return fail(TSPLAT_ERR_INVALID_ARG, "backward_project: g is not the store of the last render");
+    launch_project_backward(g->xyzo.as<float4>(), g->cova.as<float4>(), g->covb.as<float2>(), g->n_dev.as<uint32_t>(),
+                            g->cap, c->cam, c->par, d_mean2d, d_conic, d_mean3d, d_cov3d, S(stream));
+    return check_launch("backward_project");
+}
+
+tsplat_status tsplat_build_backward(tsplat_gaussians *g, const tsplat_src_view *views, int32_t n_views,
+                                    const float *d_mean3d, const float *d_cov3d, const float *d_opac,
+                                    const float *d_feat, const tsplat_src_grads *grads, void *stream) {
+    if (!g || !views || !d_mean3d || !d_cov3d || !d_opac || !d_feat || !grads)
+        return fail(TSPLAT_ERR_INVALID_ARG, "build_backward: NULL argument");
+    cudaStream_t s = S(stream);
+    LiftBwdArgs a;
+    memset(&a, 0, sizeof(a));
+    TRY(build_args(g, views, n_views, a.b, s));
+    for (int v = 0; v < n_views; ++v) {
+        const tsplat_src_grads &gr = grads[v];
+        if (!gr.depth || !gr.scale || !gr.opacity || !gr.feat)
+            return fail(TSPLAT_ERR_INVALID_ARG, "build_backward: view %d: NULL gradient map", v);
+        if (gr.quat && ((uintptr_t)gr.quat & 15)) return fail(TSPLAT_ERR_INVALID_ARG, "build_backward: view %d: quat gradient not 16-byte aligned", v);
+        a.g[v].depth = gr.depth;
+        a.g[v].scale = gr.scale;
+        a.g[v].quat = views[v].quat ? gr.quat : nullptr;
+        a.g[v].opacity = gr.opacity;
+        a.g[v].feat = gr.feat;
+    }
+    a.d_mean = d_mean3d;
+    a.d_cov = d_cov3d;
+    a.d_opac = d_opac;
+    a.d_feat = d_feat;
+    launch_build_backward(a, s);
+    return check_launch("build_backward");
+}
 
 tsplat_status tsplat_zbuffer(const tsplat_gaussians *g, const tsplat_camera *cam, float *out_depth, int32_t *out_id,
                              tsplat_ctx *ctx, void *stream) {
@@ -727,6 +784,7 @@ tsplat_status tsplat_rasterize(int64_t n, const float *mean2d, const float *coni
     ProjectOut o = project_out(ctx);
     launch_prepare_2d(n, mean2d, conic, opac, depth, radius, *params, vb, ctx->views.as<RenderView>(), o, s);
     TRY(check_launch("rasterize: prepare"));
+    ctx->has_cam = false;
     return render_tail(ctx, n, small_ptr(ctx, SM_N), vb, feat, C, feat_dtype, *params, s);
 }
 

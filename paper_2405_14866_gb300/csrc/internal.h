@@ -243,6 +243,31 @@ tsplat_status render_batch_impl(const tsplat_gaussians *g, const tsplat_camera *
 void make_view_batch(const tsplat_camera *cams, int32_t n_views, float *const *out_feat, float *const *out_alpha,
                      ViewBatch &vb);
 
+// Adjoint of the projection (FP32, per Gaussian): d_mean3d (N x 3) and
+// d_cov3d (N x 6) from d_mean2d (N x 2) and d_conic (N x 3, raw conic).
+void launch_project_backward(const float4 *xyzo, const float4 *cova, const float2 *covb, const uint32_t *n_dev,
+                             int64_t n_cap, const tsplat_camera &cam, const tsplat_render_params &par,
+                             const float *d_mean2d, const float *d_conic, float *d_mean3d, float *d_cov3d,
+                             cudaStream_t s);
+
+// Adjoint of the lifting: per source pixel gradients of the maps.
+struct SrcGrads {
+    float *depth;    // H x W
+    float *scale;    // H x W x 3
+    float *quat;     // H x W x 4, or NULL
+    float *opacity;  // H x W
+    float *feat;     // H x W x C
+};
+struct LiftBwdArgs {
+    BuildArgs b;  // views, blk_cnt / blk_off scratch, n_dev
+    const float *d_mean;
+    const float *d_cov;
+    const float *d_opac;
+    const float *d_feat;
+    SrcGrads g[MAX_VIEWS];
+};
+void launch_build_backward(const LiftBwdArgs &a, cudaStream_t s);
+
 // Point z-buffer of the Gaussian means into `cam`: keys = W*H scratch words,
 // depth / id = W*H outputs (id may be NULL).
 void launch_zbuffer(const float4 *xyzo, const uint32_t *n_dev, int64_t n_cap, const tsplat_camera &cam,

@@ -237,6 +237,113 @@ __global__ __launch_bounds__(BT) void k_build_lift(BuildArgs a) {
     }
 }
 
+// Adjoint of the lifting (Tele-Aloha trains the encoder through R_G, Sec.
+// 4.2): same striping and Gaussian numbering as k_build_lift; each
+// foreground pixel turns its Gaussian's gradients into gradients of the
+// depth, scale, quaternion, opacity and feature maps; background pixels get
+// zeros.  mean = Rs^T (z ray - ts) gives dL/dz = (Rs^T ray) . dL/dmean;
+// cov = M M^T with M = Rs^T R(q / |q|) diag(s) gives dL/dM = 2 G M for the
+// symmetric gradient G of the covariance, then the scales, the rotation and
+// the quaternion through its normalisation.
+__global__ __launch_bounds__(BT) void k_build_backward(LiftBwdArgs a) {
+    __shared__ uint32_t s_wn[BT / 32];
+    const BuildArgs &b = a.b;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t base = (int64_t)blockIdx.x * BUILD_PIX_PER_BLOCK;
+    const int C = b.C;
+    int64_t running = b.blk_off[blockIdx.x];
+    for (int r = 0; r < BI; ++r) {
+        const int64_t g = base + (int64_t)r * BT + threadIdx.x;
+        const bool fg = is_fg(b, g);
+        const uint32_t bal = __ballot_sync(FULL, fg);
+        if (lane == 0) s_wn[warp] = __popc(bal);
+        __syncthreads();
+        uint32_t woff = 0, tot = 0;
+#pragma unroll
+        for (int w = 0; w < BT / 32; ++w) {
+            const uint32_t c = s_wn[w];
+            woff += w < warp ? c : 0u;
+            tot += c;
+        }
+        if (g < b.total_pix) {
+            const int vi = view_of(b, g);
+            const ViewDesc &vd = b.views[vi];
+            const SrcGrads &out = a.g[vi];
+            const int64_t p = g - vd.pix_off;
+            if (!fg) {
+                out.depth[p] = 0.0f;
+                out.opacity[p] = 0.0f;
+                for (int k = 0; k < 3; ++k) out.scale[3 * p + k] = 0.0f;
+                if (out.quat) for (int k = 0; k < 4; ++k) out.quat[4 * p + k] = 0.0f;
+                for (int c = 0; c < C; ++c) out.feat[p * C + c] = 0.0f;
+            } else {
+                const int64_t n = running + woff + __popc(bal & lanemask_lt());
+                const tsplat_camera &cam = vd.cam;
+                const float *Rs = cam.R;
+                const int u = (int)(p % vd.W), v = (int)(p / vd.W);
+                const float ray[3] = {(u - cam.cx) / cam.fx, (v - cam.cy) / cam.fy, 1.0f};
+                const float *gm = a.d_mean + 3 * n;
+                float gz = 0.0f;
+#pragma unroll
+                for (int i = 0; i < 3; ++i) gz += (Rs[0 * 3 + i] * ray[0] + Rs[1 * 3 + i] * ray[1] + Rs[2 * 3 + i] * ray[2]) * gm[i];
+                out.depth[p] = gz;
+                float w = 1.0f, x = 0.0f, y = 0.0f, z = 0.0f;
+                if (vd.quat) {
+                    const float4 q = *reinterpret_cast<const float4 *>(vd.quat + 4 * p);
+                    w = q.x; x = q.y; y = q.z; z = q.w;
+                }
+                const float nq = sqrtf(w * w + x * x + y * y + z * z);
+                w /= nq; x /= nq; y /= nq; z /= nq;
+                const float Rq[3][3] = {{1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)},
+                                        {2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)},
+                                        {2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)}};
+                const float s3[3] = {vd.scale[3 * p], vd.scale[3 * p + 1], vd.scale[3 * p + 2]};
+                float Rg[3][3], M[3][3];
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        Rg[i][j] = Rs[0 * 3 + i] * Rq[0][j] + Rs[1 * 3 + i] * Rq[1][j] + Rs[2 * 3 + i] * Rq[2][j];
+                        M[i][j] = Rg[i][j] * s3[j];
+                    }
+                const float *gc = a.d_cov + 6 * n;
+                const float G[3][3] = {{gc[0], 0.5f * gc[1], 0.5f * gc[2]},
+                                       {0.5f * gc[1], gc[3], 0.5f * gc[4]},
+                                       {0.5f * gc[2], 0.5f * gc[4], gc[5]}};
+                float gM[3][3];
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) gM[i][j] = 2.0f * (G[i][0] * M[0][j] + G[i][1] * M[1][j] + G[i][2] * M[2][j]);
+#pragma unroll
+                for (int j = 0; j < 3; ++j) out.scale[3 * p + j] = gM[0][j] * Rg[0][j] + gM[1][j] * Rg[1][j] + gM[2][j] * Rg[2][j];
+                if (out.quat) {
+                    float gR[3][3];
+#pragma unroll
+                    for (int k = 0; k < 3; ++k)
+#pragma unroll
+                        for (int j = 0; j < 3; ++j)
+                            gR[k][j] = (Rs[k * 3 + 0] * gM[0][j] + Rs[k * 3 + 1] * gM[1][j] + Rs[k * 3 + 2] * gM[2][j]) * s3[j];
+                    const float gw = 2 * (-z * gR[0][1] + y * gR[0][2] + z * gR[1][0] - x * gR[1][2] - y * gR[2][0] + x * gR[2][1]);
+                    const float gx = 2 * (y * gR[0][1] + z * gR[0][2] + y * gR[1][0] - 2 * x * gR[1][1] - w * gR[1][2] +
+                                          z * gR[2][0] + w * gR[2][1] - 2 * x * gR[2][2]);
+                    const float gy = 2 * (-2 * y * gR[0][0] + x * gR[0][1] + w * gR[0][2] + x * gR[1][0] + z * gR[1][2] -
+                                          w * gR[2][0] + z * gR[2][1] - 2 * y * gR[2][2]);
+                    const float gzq = 2 * (-2 * z * gR[0][0] - w * gR[0][1] + x * gR[0][2] + w * gR[1][0] - 2 * z * gR[1][1] +
+                                           y * gR[1][2] + x * gR[2][0] + y * gR[2][1]);
+                    const float dot = gw * w + gx * x + gy * y + gzq * z;
+                    *reinterpret_cast<float4 *>(out.quat + 4 * p) =
+                        make_float4((gw - w * dot) / nq, (gx - x * dot) / nq, (gy - y * dot) / nq, (gzq - z * dot) / nq);
+                }
+                out.opacity[p] = a.d_opac[n];
+                for (int c = 0; c < C; ++c) out.feat[p * C + c] = a.d_feat[n * C + c];
+            }
+        }
+        running += tot;
+        __syncthreads();
+    }
+}
+
 __global__ void k_gaussians_set(uint64_t n, const float *mean, const float *cov, const float *opac,
                                 const void *feat, int dtype_in, int C, int dtype_out, float4 *xyzo,
                                 float4 *cova, float2 *covb, void *feat_out, uint32_t *n_dev) {
@@ -279,6 +386,14 @@ void launch_build(const BuildArgs &a, cudaStream_t s) {
     note_launches(1);
     k_build_lift<<<a.nblocks, BT, 0, s>>>(a);
     note_launches(1);
+}
+
+void launch_build_backward(const LiftBwdArgs &a, cudaStream_t s) {
+    if (a.b.nblocks <= 0) return;
+    k_build_count<<<a.b.nblocks, BT, 0, s>>>(a.b);
+    k_build_scan<<<1, 1024, 0, s>>>(a.b);
+    k_build_backward<<<a.b.nblocks, BT, 0, s>>>(a);
+    note_launches(3);
 }
 
 void launch_gaussians_set(int64_t n, const float *mean, const float *cov, const float *opac, const void *feat,

@@ -271,6 +271,118 @@ __global__ void k_export_rect(const uint2 *rect, const uint32_t *n_dev, int32_t 
 
 }  // namespace
 
+// Adjoint of the projection (Sec. 4.2, trained end to end): per Gaussian,
+// dL/dmean and dL/dcov from dL/dmu and dL/d(conic) (raw conic (A, B, C) of
+// q = -(A dx^2 + 2 B dx dy + C dy^2) / 2).  Chain: p = R x + t;
+// mu = f p_xy / p_z + c; J from p with x/z and y/z clamped (no gradient
+// through a clamped ratio); S = (J R) V (J R)^T + lowpass I; conic = S^-1.
+__global__ __launch_bounds__(256) void k_project_backward(const float4 *__restrict__ xyzo,
+                                                          const float4 *__restrict__ cova,
+                                                          const float2 *__restrict__ covb, const uint32_t *n_dev,
+                                                          const __grid_constant__ tsplat_camera cam,
+                                                          tsplat_render_params par, const float *d_mu,
+                                                          const float *d_conic, float *d_mean, float *d_cov) {
+    const uint64_t n = *n_dev;
+    const float *R = cam.R;
+    const float limx = par.frustum_clamp * (0.5f * (float)cam.width / cam.fx);
+    const float limy = par.frustum_clamp * (0.5f * (float)cam.height / cam.fy);
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        float gp[3] = {0.0f, 0.0f, 0.0f};
+        float gc[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        const float4 g = xyzo[i];
+        const float px = R[0] * g.x + R[1] * g.y + R[2] * g.z + cam.t[0];
+        const float py = R[3] * g.x + R[4] * g.y + R[5] * g.z + cam.t[1];
+        const float z = R[6] * g.x + R[7] * g.y + R[8] * g.z + cam.t[2];
+        if (z > 0.0f) {
+            const float gmx = d_mu[2 * i], gmy = d_mu[2 * i + 1];
+            const float iz = 1.0f / z, iz2 = iz * iz;
+            gp[0] = cam.fx * iz * gmx;
+            gp[1] = cam.fy * iz * gmy;
+            gp[2] = -(cam.fx * px * gmx + cam.fy * py * gmy) * iz2;
+            const float rx = px * iz, ry = py * iz;
+            const bool inx = rx > -limx && rx < limx, iny = ry > -limy && ry < limy;
+            const float txz = fminf(limx, fmaxf(-limx, rx)), tyz = fminf(limy, fmaxf(-limy, ry));
+            const float J00 = cam.fx * iz, J02 = -cam.fx * txz * iz, J11 = cam.fy * iz, J12 = -cam.fy * tyz * iz;
+            float T0[3], T1[3];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                T0[j] = J00 * R[0 * 3 + j] + J02 * R[2 * 3 + j];
+                T1[j] = J11 * R[1 * 3 + j] + J12 * R[2 * 3 + j];
+            }
+            const float4 ca = cova[i];
+            const float2 cb = covb[i];
+            const float V[3][3] = {{ca.x, ca.y, ca.z}, {ca.y, ca.w, cb.x}, {ca.z, cb.x, cb.y}};
+            float VT0[3], VT1[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                VT0[k] = V[k][0] * T0[0] + V[k][1] * T0[1] + V[k][2] * T0[2];
+                VT1[k] = V[k][0] * T1[0] + V[k][1] * T1[1] + V[k][2] * T1[2];
+            }
+            const float a = T0[0] * VT0[0] + T0[1] * VT0[1] + T0[2] * VT0[2] + par.lowpass;
+            const float b = T0[0] * VT1[0] + T0[1] * VT1[1] + T0[2] * VT1[2];
+            const float c = T1[0] * VT1[0] + T1[1] * VT1[1] + T1[2] * VT1[2] + par.lowpass;
+            const float D = a * c - b * b;
+            if (D > 0.0f && isfinite(D)) {
+                const float gA = d_conic[3 * i], gB = d_conic[3 * i + 1], gC = d_conic[3 * i + 2];
+                const float iD = 1.0f / D, iD2 = iD * iD;
+                const float ga = -gA * c * c * iD2 + gB * b * c * iD2 + gC * (iD - a * c * iD2);
+                const float gb = 2.0f * gA * b * c * iD2 - gB * (iD + 2.0f * b * b * iD2) + 2.0f * gC * a * b * iD2;
+                const float gcc = gA * (iD - a * c * iD2) + gB * a * b * iD2 - gC * a * a * iD2;
+                const int ii[6] = {0, 0, 0, 1, 1, 2}, jj[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+                for (int e = 0; e < 6; ++e) {
+                    const int u = ii[e], v = jj[e];
+                    float d00 = T0[u] * T0[v], d01 = T0[u] * T1[v], d11 = T1[u] * T1[v];
+                    if (u != v) {
+                        d00 += T0[v] * T0[u];
+                        d01 += T0[v] * T1[u];
+                        d11 += T1[v] * T1[u];
+                    }
+                    gc[e] = ga * d00 + gb * d01 + gcc * d11;
+                }
+                float gJ00 = 0.0f, gJ02 = 0.0f, gJ11 = 0.0f, gJ12 = 0.0f;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const float gt0 = 2.0f * ga * VT0[k] + gb * VT1[k];
+                    const float gt1 = gb * VT0[k] + 2.0f * gcc * VT1[k];
+                    gJ00 += gt0 * R[0 * 3 + k];
+                    gJ02 += gt0 * R[2 * 3 + k];
+                    gJ11 += gt1 * R[1 * 3 + k];
+                    gJ12 += gt1 * R[2 * 3 + k];
+                }
+                gp[2] -= (cam.fx * gJ00 + cam.fy * gJ11) * iz2;
+                if (inx) {
+                    gp[0] -= cam.fx * iz2 * gJ02;
+                    gp[2] += 2.0f * cam.fx * px * iz2 * iz * gJ02;
+                } else {
+                    gp[2] += cam.fx * txz * iz2 * gJ02;
+                }
+                if (iny) {
+                    gp[1] -= cam.fy * iz2 * gJ12;
+                    gp[2] += 2.0f * cam.fy * py * iz2 * iz * gJ12;
+                } else {
+                    gp[2] += cam.fy * tyz * iz2 * gJ12;
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) d_mean[3 * i + k] = R[0 * 3 + k] * gp[0] + R[1 * 3 + k] * gp[1] + R[2 * 3 + k] * gp[2];
+#pragma unroll
+        for (int e = 0; e < 6; ++e) d_cov[6 * i + e] = gc[e];
+    }
+}
+
+void launch_project_backward(const float4 *xyzo, const float4 *cova, const float2 *covb, const uint32_t *n_dev,
+                             int64_t n_cap, const tsplat_camera &cam, const tsplat_render_params &par,
+                             const float *d_mean2d, const float *d_conic, float *d_mean3d, float *d_cov3d,
+                             cudaStream_t s) {
+    if (n_cap <= 0) return;
+    const int64_t blocks = std::min<int64_t>((n_cap + 255) / 256, 152 * 16);
+    k_project_backward<<<(unsigned)blocks, 256, 0, s>>>(xyzo, cova, covb, n_dev, cam, par, d_mean2d, d_conic, d_mean3d,
+                                                       d_cov3d);
+    note_launches(1);
+}
+
 void launch_export_rect(const uint2 *rect, const uint32_t *n_dev, int64_t n_cap, int32_t *dst, cudaStream_t s) {
     if (n_cap <= 0) return;
     k_export_rect<<<(unsigned)((n_cap + 255) / 256), 256, 0, s>>>(rect, n_dev, dst);

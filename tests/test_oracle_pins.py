@@ -691,3 +691,65 @@ def test_lift_adjoint_matches_central_differences():
             fd = (_lift_loss(vu, w) - _lift_loss(vd, w)) / step
             scale = max(abs(grad[idx]), np.abs(grad).max() * 1e-3)
             assert abs(fd - grad[idx]) <= 1e-4 * scale, (name, idx, fd, grad[idx])
+
+
+def test_chained_adjoints_match_central_differences_of_source_maps():
+    """The three adjoints chained (compositing, projection, lifting) against
+    central differences of the FP64 forward (lift, project, composite with
+    the base decisions and tile lists frozen) w.r.t. entries of the source
+    depth, scale, quaternion, opacity and feature maps."""
+    sc = gen.scene_paper(seed=17, res=24, C=2)
+    cam = gen.make_camera(30.0, 32, 32, (0.01, 0.0, -0.02), gen.rot_y(3.0))
+    g32 = O.lift_scene(sc, "f32")
+    pr = O.project_f32(g32, cam, PAR)
+    bins = O.bin_gaussians(pr, 32, 32)
+    rng = np.random.default_rng(8)
+    gF = rng.standard_normal((2, 32, 32)); gA = rng.standard_normal((32, 32))
+
+    def forward(views):
+        g = O.Gaussians(*(np.concatenate([getattr(O.lift_view(v, "f64"), k) for v in views], 0)
+                          for k in ("mean", "cov", "opac", "feat")))
+        mu, conic, _, _ = O.project_f64(g, cam, PAR)
+        return g, mu, conic
+
+    g0, mu0, con0 = forward(sc.views)
+    r0, dec = O.composite(mu0, con0, g0.opac, g0.feat, 32, 32, bins, PAR, record=True)
+
+    def loss(views):
+        g, mu, conic = forward(views)
+        r = O.composite(mu, conic, g.opac, g.feat, 32, 32, bins, PAR, dec_in=dec)
+        return float((gF * r.F).sum() + (gA * r.A).sum())
+
+    d_mu, d_con, d_op, d_ft = O.backward(mu0, con0, g0.opac, g0.feat, 32, 32, bins, gF, gA, PAR)
+    g_mean, g_cov = O.project_backward(g0.mean, g0.cov, cam, d_mu, d_con)
+    n0 = int(sc.views[0].mask.sum())
+    grads = O.lift_backward(sc.views[0], g_mean[:n0], g_cov[:n0], d_op[:n0], d_ft[:n0])
+    # pixels of view 0 whose Gaussian lands in a used tile list
+    used = set(np.unique(bins.ids).tolist())
+    fg = np.argwhere(sc.views[0].mask.reshape(-1) > 0)[:, 0]
+    cand = [(p, k) for k, p in enumerate(fg) if k in used]
+    picks = [cand[i] for i in rng.choice(len(cand), size=8, replace=False)]
+    H, W = sc.views[0].depth.shape
+    checked = 0
+    for p, k in picks:
+        y, x = divmod(int(p), W)
+        for name, sub in (("depth", ()), ("scale", (0,)), ("scale", (2,)), ("quat", (1,)), ("quat", (0,)),
+                          ("opacity", ()), ("feat", (1,))):
+            arr = getattr(sc.views[0], name)
+            pos = (y, x) + sub
+            v0 = float(arr[pos])
+            h = 1e-3 * max(abs(v0), 0.05)
+            vals = []
+            for sgn in (1, -1):
+                a2 = arr.copy()
+                a2[pos] = np.float32(v0 + sgn * h)
+                vals.append((float(a2[pos]), loss([gen.SourceView(*(a2 if f == name else getattr(sc.views[0], f)
+                                                                      for f in ("depth", "mask", "scale", "quat",
+                                                                                "opacity", "feat", "cam")))]
+                                                  + list(sc.views[1:]))))
+            fd = (vals[0][1] - vals[1][1]) / (vals[0][0] - vals[1][0])
+            an = grads[name][pos]
+            scale = max(abs(an), np.abs(grads[name]).max() * 1e-2)
+            assert abs(fd - an) <= 2e-3 * scale, (name, pos, fd, an)
+            checked += 1
+    assert checked == 56
