@@ -431,24 +431,25 @@ def diff_bench(api, torch, steps=10, warmup=3):
                  for v in up["views"]]
         g = api.Gaussians.build(views, sc.C, sc.feat_dtype)
         Y = torch.from_numpy(sc.extra["target_map"]).cuda()
-        samples.append((g, Y, up))
+        samples.append((g, Y, up, views))
     sc0 = gen.scene_diff_sample(seed=300)
     cam, C = sc0.targets[0], sc0.C
     ctx = api.Context()
     P = N = 0
-    for g, Y, _ in samples:
+    for g, Y, _, _ in samples:
         ctx.render(g, cam, save=True)
         st = ctx.stats()
         P, N = max(P, st["n_pairs"]), max(N, st["n_gaussians"])
-    cap = max(g.capacity for g, _, _ in samples)
+    cap = max(g.capacity for g, _, _, _ in samples)
     ctx.reserve(cap, int(P * 1.25) + 65536, cam.width, cam.height, C)
     F = torch.empty((C, cam.height, cam.width), device="cuda")
     A = torch.empty((cam.height, cam.width), device="cuda")
     grads = [tuple(torch.empty(sh, device="cuda") for sh in ((cap, 2), (cap, 3), (cap,), (cap, C))) for _ in samples]
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in samples]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in samples]
+    g3 = [(torch.empty((cap, 3), device="cuda"), torch.empty((cap, 6), device="cuda")) for _ in samples]
 
-    def step(record):
-        for k, (g, Y, _) in enumerate(samples):
+    def step(record, sources=True):
+        for k, (g, Y, _, views) in enumerate(samples):
             if record:
                 ev[k][0].record()
             ctx.render(g, cam, save=True, async_=True, out_feat=F, out_alpha=A)
@@ -458,22 +459,24 @@ def diff_bench(api, torch, steps=10, warmup=3):
             ctx.backward(dF, out=grads[k])
             if record:
                 ev[k][2].record()
+            if sources:  # on to the 3D Gaussians and the source maps
+                ctx.backward_project(g, grads[k][0], grads[k][1], out=g3[k])
+                g.build_backward(views, g3[k][0], g3[k][1], grads[k][2], grads[k][3])
+            if record:
+                ev[k][3].record()
 
     for _ in range(warmup):
         step(False)
     torch.cuda.synchronize()
-    fwd = bwd = 0.0
-    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t0.record()
+    fwd = bwd = src = 0.0
     for _ in range(steps):
         step(True)
         torch.cuda.synchronize()
         fwd += sum(e[0].elapsed_time(e[1]) for e in ev)
         bwd += sum(e[1].elapsed_time(e[2]) for e in ev)
-    t1.record()
-    torch.cuda.synchronize()
+        src += sum(e[2].elapsed_time(e[3]) for e in ev)
     ctx.status()
-    per_fwd, per_bwd = fwd / (steps * 8), bwd / (steps * 8)
+    per_fwd, per_bwd, per_src = fwd / (steps * 8), bwd / (steps * 8), src / (steps * 8)
     # backward algorithmic bytes per sample (last sample's P, N): per pair id +
     # record + feature row; per pixel dF (C f32), T_final, last index; gradient
     # outputs N x (2 + 3 + 1 + C) f32
@@ -481,7 +484,8 @@ def diff_bench(api, torch, steps=10, warmup=3):
     peak, src = measured_peaks()
     return {"workload": "8 samples x 2 x 512^2 source views (~315K Gaussians each), 16-ch FP32 features, 512^2 "
                         "target; loss = MSE vs a seeded N(0,1) map",
-            "samples_per_s": 1e3 / (per_fwd + per_bwd), "forward_ms": per_fwd, "backward_ms": per_bwd,
+            "samples_per_s": 1e3 / (per_fwd + per_bwd + per_src), "forward_ms": per_fwd, "backward_ms": per_bwd,
+            "backward_to_source_maps_ms": per_src,
             "gaussians": N, "pairs": P,
             "backward_roofline": {"bound": "hbm", "achieved": bw_bytes / (per_bwd * 1e-3) / 1e9, "peak": peak,
                                   "unit": "GB/s", "frac": bw_bytes / (per_bwd * 1e-3) / 1e9 / peak,

@@ -274,12 +274,15 @@ class Context:
                *(_ptr(o) for o in outs), _stream(stream))
         return outs
 
-    def backward_project(self, g: Gaussians, d_mean2d, d_conic, stream=None):
+    def backward_project(self, g: Gaussians, d_mean2d, d_conic, stream=None, out=None):
         """dL/dmean3d (cap,3), dL/dcov3d (cap,6) from the 2D gradients of the last
-        render (tsplat_render with save=True) of `g`."""
+        render (tsplat_render with save=True) of `g`; `out` = preallocated pair."""
         dev = torch.device("cuda")
-        dm = torch.empty((g.capacity, 3), device=dev)
-        dc = torch.empty((g.capacity, 6), device=dev)
+        if out is not None:
+            dm, dc = out
+        else:
+            dm = torch.empty((g.capacity, 3), device=dev)
+            dc = torch.empty((g.capacity, 6), device=dev)
         L.call("tsplat_backward_project", self.handle, g.handle, _ptr(d_mean2d.contiguous()),
                _ptr(d_conic.contiguous()), _ptr(dm), _ptr(dc), _stream(stream))
         return dm, dc
