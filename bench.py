@@ -591,8 +591,11 @@ def run_ours(args):
     # whole path (A1..A7) against the same peak, per the algorithmic byte model
     path_bytes = (N * (40 + 36) + N * 8 + N * 12 + P * 12 + P * 24 + P * 8 + st["tiles_x"] * st["tiles_y"] * 8
                   + comp_bytes)
+    # lifting: the masks of all source pixels; depth, scale, quaternion, opacity
+    # and feature row of each foreground pixel (= Gaussian) read; the Gaussian
+    # written (40 B + its feature row)
     fin = up["views"][0]["feat"].element_size()  # bytes per source feature element
-    build_bytes = sum(v.depth.size * (4 + 1 + 12 + 16 + 4 + fin * sc.C) for v in sc.views) + N * (40 + sc.C * bf)
+    build_bytes = sum(v.depth.size for v in sc.views) + N * (4 + 12 + 16 + 4 + fin * sc.C) + N * (40 + sc.C * bf)
 
     # end to end through the public API with host buffers
     e2e = None
