@@ -182,7 +182,7 @@ tsplat_status tsplat_build_into(tsplat_gaussians *g, const tsplat_src_view *view
  * caller beforehand (tsplat_gaussians_create).
  * Limit: at most 64 Mi source pixels in total per call (e.g. 16 views of
  * 2048 x 2048); larger inputs return TSPLAT_ERR_CAPACITY before any work.
- * The per-block scratch of the compaction is one fixed 128 KiB device array
+ * The per-block scratch of the compaction is one fixed 512 KiB device array
  * that every GPU loading the library keeps until the process exits.  The
  * first call on a device resolves that array's device address (with that
  * device current); make that first call before any stream capture.  All

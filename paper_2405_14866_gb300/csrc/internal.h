@@ -41,7 +41,7 @@ struct BuildArgs {
     uint32_t *n_dev;    // N (output)
     int nblocks;
 };
-constexpr int BUILD_PIX_PER_BLOCK = 4096;
+constexpr int BUILD_PIX_PER_BLOCK = 1024;
 void launch_build(const BuildArgs &a, cudaStream_t s);
 
 // Convert/copy caller arrays into a Gaussian store.

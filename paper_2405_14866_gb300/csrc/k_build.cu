@@ -14,7 +14,7 @@ namespace tsp {
 namespace {
 
 constexpr int BT = 256;                             // threads per block
-constexpr int BI = BUILD_PIX_PER_BLOCK / BT;        // pixels per thread (16)
+constexpr int BI = BUILD_PIX_PER_BLOCK / BT;        // pixels per thread (4)
 constexpr uint32_t FULL = 0xffffffffu;
 
 __device__ __forceinline__ int view_of(const BuildArgs &a, int64_t g) {
@@ -63,7 +63,7 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     return m;
 }
 
-// Pixels of block b: [b * 4096, (b + 1) * 4096), visited in 16 rounds of 256
+// Pixels of block b: [b * 1024, (b + 1) * 1024), visited in 4 rounds of 256
 // consecutive pixels (thread t takes pixel round * 256 + t).
 __global__ __launch_bounds__(BT) void k_build_count(BuildArgs a) {
     __shared__ uint32_t sw[BT / 32];

@@ -16,7 +16,7 @@
 namespace {
 
 // Largest total source-pixel count one call may lift: 64 Mi pixels (e.g.
-// 16 views of 2048 x 2048).  Scratch: 2 words per 4096-pixel block = 128 KiB,
+// 16 views of 2048 x 2048).  Scratch: 2 words per 1024-pixel block = 512 KiB,
 // held by every GPU that loads the library until the process exits.
 constexpr int64_t NOALLOC_MAX_PIXELS = int64_t(64) << 20;
 constexpr int NOALLOC_MAX_BLOCKS = (int)(NOALLOC_MAX_PIXELS / tsp::BUILD_PIX_PER_BLOCK);
