@@ -112,6 +112,7 @@ struct tsplat_ctx {
     // tiles / pixels / view table
     DBuf ranges, tfinal, last, views;
     DBuf zkeys;  // point z-buffer scratch
+    DBuf torder; // composite tile order
     // small words: kminmax[2], n_vis, npass, p_dev, p_eff, status, n_dev, totals[4*256]
     DBuf small;
     uint32_t *host_small = nullptr;  // pinned mirror
@@ -347,7 +348,7 @@ tsplat_status tsplat_ctx_destroy(tsplat_ctx *c) {
     cudaDeviceSynchronize();
     DBuf *bufs[] = {&c->hdr, &c->rect, &c->ntiles, &c->dkey, &c->radius, &c->skeys0, &c->skeys1, &c->svals0,
                     &c->svals1, &c->hist_n, &c->emit_blk, &c->pk0, &c->pk1, &c->pv0, &c->pv1, &c->hist_p,
-                    &c->ranges, &c->tfinal, &c->last, &c->views, &c->zkeys, &c->small};
+                    &c->ranges, &c->tfinal, &c->last, &c->views, &c->zkeys, &c->torder, &c->small};
     for (DBuf *b : bufs) release(*b);
     for (auto &row : c->ev)
         for (cudaEvent_t e : row)
@@ -389,6 +390,7 @@ static tsplat_status ensure_p(tsplat_ctx *c, int64_t p, cudaStream_t s) {
 
 static tsplat_status ensure_pix(tsplat_ctx *c, int W, int H, int n_tiles, bool save, cudaStream_t s) {
     TRY(grow(c->ranges, (size_t)std::max(n_tiles, 1) * 8, s));
+    TRY(grow(c->torder, (size_t)std::max(n_tiles, 1) * 4, s));
     TRY(grow(c->views, sizeof(RenderView) * MAX_BATCH, s));
     if (save) {
         TRY(grow(c->tfinal, (size_t)W * H * 4, s));
@@ -521,6 +523,7 @@ static tsplat_status render_tail(tsplat_ctx *c, int64_t n_cap, const uint32_t *n
     const uint32_t *tiles_sorted = tpass == 0 ? ts.keys_in : ts.keys[(tpass - 1) & 1];
     const uint32_t *ids_sorted = tpass == 0 ? ts.vals_in : ts.vals[(tpass - 1) & 1];
     launch_ranges(tiles_sorted, sm + SM_PEFF, c->p_cap, c->ranges.as<uint2>(), n_tiles, s);
+    launch_tile_order(c->ranges.as<uint2>(), c->views.as<RenderView>(), vb.n_views, n_tiles, c->torder.as<uint32_t>(), s);
     TRY(check_launch("render: bins"));
     TRY(mark(c, prof, 5, s));
 
@@ -543,6 +546,7 @@ static tsplat_status render_tail(tsplat_ctx *c, int64_t n_cap, const uint32_t *n
     ca.status = sm + SM_STATUS;
     ca.tile_counter = sm + SM_TILECTR;
     ca.save = save ? 1 : 0;
+    ca.tile_order = c->torder.as<uint32_t>();
     launch_composite(ca, s);
     TRY(check_launch("render: composite"));
     TRY(mark(c, prof, 6, s));
@@ -921,6 +925,7 @@ tsplat_status ctx_reserve_batch(tsplat_ctx *c, int64_t instances, int64_t pairs,
     TRY(ensure_n(c, instances, nullptr));
     TRY(ensure_p(c, pairs, nullptr));
     TRY(grow(c->ranges, (size_t)std::max<int64_t>(tiles, 1) * 8, nullptr));
+    TRY(grow(c->torder, (size_t)std::max<int64_t>(tiles, 1) * 4, nullptr));
     TRY(grow(c->views, sizeof(RenderView) * MAX_BATCH, nullptr));
     TRY_CUDA(cudaStreamSynchronize(nullptr));
     return TSPLAT_OK;

@@ -181,6 +181,7 @@ struct CompositeArgs {
     uint32_t *status;      // TSPLAT_ERR_TIMEOUT if a bounded wait expired
     uint32_t *tile_counter;  // next tile to hand out (0 at launch)
     int save;                // record T_final and the last blended index (backward)
+    const uint32_t *tile_order;  // tile taken at each ticket (longest lists first), or NULL
 };
 void launch_composite(const CompositeArgs &a, cudaStream_t s);
 
@@ -272,6 +273,11 @@ void launch_build_backward(const LiftBwdArgs &a, cudaStream_t s);
 // depth / id = W*H outputs (id may be NULL).
 void launch_zbuffer(const float4 *xyzo, const uint32_t *n_dev, int64_t n_cap, const tsplat_camera &cam,
                     unsigned long long *keys, float *depth, int32_t *id, cudaStream_t s);
+
+// Composite tile order: n_slots tiles (the launch's tile count), longest
+// pair lists first; slots beyond the views' tiles last.
+void launch_tile_order(const uint2 *ranges, const RenderView *views, int n_views, int n_slots, uint32_t *order,
+                       cudaStream_t s);
 
 // small utilities
 void launch_fill_u32(uint32_t *p, uint32_t v, int64_t n, cudaStream_t s);

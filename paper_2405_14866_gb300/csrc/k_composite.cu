@@ -126,6 +126,7 @@ __device__ void producer(CompSmem<CP, F32F> &S, const CompositeArgs &a, int lane
         if (lane == 0) t = atomicAdd(a.tile_counter, 1u);
         t = __shfl_sync(FULL, t, 0);
         const bool last_tile = t >= n_tiles;
+        if (!last_tile && a.tile_order) t = a.tile_order[t];
         uint32_t first = 0;
         int n = 0;
         if (!last_tile) {

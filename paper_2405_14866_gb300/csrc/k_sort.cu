@@ -410,6 +410,41 @@ __global__ void k_ranges(const uint32_t *tiles, const uint32_t *p_dev, uint64_t 
     }
 }
 
+// Order in which the persistent composite takes the tiles: longest lists
+// first (largest-processing-time-first scheduling shortens the tail of the
+// grid).  One block buckets the tiles by 4 log2(pair count); tiles with no
+// pairs follow, then tile slots beyond the views' tile count (graph replays
+// size the launch for their largest batch).  The order within a bucket
+// depends on atomics, which changes nothing in the output: every tile is
+// composited independently.
+constexpr int TO_BUCKETS = 64;
+__global__ __launch_bounds__(1024) void k_tile_order(const uint2 *ranges, const RenderView *views, int n_views,
+                                                     uint32_t n_slots, uint32_t *order) {
+    __shared__ uint32_t cnt[TO_BUCKETS + 2], off[TO_BUCKETS + 2];
+    const RenderView &lv = views[n_views - 1];
+    const uint32_t n_tiles = min(n_slots, lv.tile_base + (uint32_t)(lv.tiles_x * lv.tiles_y));
+    for (int i = threadIdx.x; i < TO_BUCKETS + 2; i += blockDim.x) cnt[i] = 0;
+    __syncthreads();
+    auto bucket = [&](uint32_t t) -> int {
+        if (t >= n_tiles) return TO_BUCKETS + 1;  // not a tile of this batch
+        const uint32_t c = ranges[t].y - ranges[t].x;
+        if (c == 0) return TO_BUCKETS;
+        const int lg = (int)(4.0f * __log2f((float)c));
+        return TO_BUCKETS - 1 - min(TO_BUCKETS - 1, max(0, lg));  // descending count
+    };
+    for (uint32_t t = threadIdx.x; t < n_slots; t += blockDim.x) atomicAdd(&cnt[bucket(t)], 1u);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int b = 0; b < TO_BUCKETS + 2; ++b) {
+            off[b] = run;
+            run += cnt[b];
+        }
+    }
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < n_slots; t += blockDim.x) order[atomicAdd(&off[bucket(t)], 1u)] = t;
+}
+
 __global__ void k_scale_u32(const uint32_t *src, uint32_t k, uint32_t *dst) { *dst = *src * k; }
 
 __global__ void k_fill_u32(uint32_t *p, uint32_t v, uint64_t n) {
@@ -496,6 +531,13 @@ void launch_ranges(const uint32_t *tiles_sorted, const uint32_t *p_dev, int64_t 
     const int threads = 256;
     const int64_t blocks = std::min<int64_t>((p_cap + threads - 1) / threads, (int64_t)sm_count() * 16);
     k_ranges<<<(unsigned)blocks, threads, 0, s>>>(tiles_sorted, p_dev, (uint64_t)p_cap, ranges, (uint32_t)n_tiles);
+    note_launches(1);
+}
+
+void launch_tile_order(const uint2 *ranges, const RenderView *views, int n_views, int n_slots, uint32_t *order,
+                       cudaStream_t s) {
+    if (n_slots <= 0) return;
+    k_tile_order<<<1, 1024, 0, s>>>(ranges, views, n_views, (uint32_t)n_slots, order);
     note_launches(1);
 }
 
