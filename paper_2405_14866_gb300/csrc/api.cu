@@ -822,6 +822,7 @@ tsplat_status tsplat_backward(tsplat_ctx *c, const float *dL_dfeat, const float 
     b.d_opac = d_opac;
     b.d_feat = d_feat;
     b.unit_counter = small_ptr(c, SM_BWDCTR);
+    b.tile_order = c->torder.as<uint32_t>();
     TRY_CUDA(cudaMemsetAsync(b.unit_counter, 0, sizeof(uint32_t), s));
     launch_backward(b, s);
     return check_launch("backward");

@@ -188,7 +188,7 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
     if (lane == 0) unit = atomicAdd(a.unit_counter, 1u);
     unit = __shfl_sync(FULL, unit, 0);
     if (unit >= (uint32_t)n_units) break;
-    const int tile = (int)(unit >> 3), wb = (int)(unit & 7);
+    const int tile = a.tile_order ? (int)a.tile_order[unit >> 3] : (int)(unit >> 3), wb = (int)(unit & 7);
     const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
     const int bx0 = tx * TILE + (wb & 1) * 8, by0 = ty * TILE + (wb >> 1) * 4;
     const int px = bx0 + (lane & 7), py = by0 + (lane >> 3);
