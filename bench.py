@@ -367,7 +367,7 @@ def serving_bench(api, torch, sc, g, views, seconds=1.5):
     load = ServeLoad(api, torch, sc, [g, g2], views)
     common = dict(max_width=max(SERVE_SIZES), max_height=max(SERVE_SIZES), max_gaussians=g.capacity, C=sc.C,
                   feat_dtype=sc.feat_dtype)
-    servers = {"server": api.Server(max_views_per_batch=8, max_lanes=3, budget_bytes=24 << 30, max_inflight_views=12,
+    servers = {"server": api.Server(max_views_per_batch=8, max_lanes=3, budget_bytes=24 << 30, max_inflight_views=8,
                                     **common),
                "plain": api.Server(max_views_per_batch=1, max_lanes=1, budget_bytes=24 << 30, graphs=False, **common)}
     for srv in servers.values():
@@ -378,7 +378,7 @@ def serving_bench(api, torch, sc, g, views, seconds=1.5):
                        "Poisson 30 Hz per viewer; the 2.1M-Gaussian frame rebuilt at 30 Hz into two alternating "
                        "stores; latency = submission to completion seen by the server",
            "server": {"max_views_per_batch": 8, "lanes": servers["server"].stats()["lanes"], "graphs": True,
-                      "max_inflight_views": 12,
+                      "max_inflight_views": 8,
                       "lane_bytes": servers["server"].stats()["lane_bytes"]},
            "plain": {"max_views_per_batch": 1, "lanes": 1, "graphs": False,
                      "what": "one launch sequence per view, one at a time, same queue and frames"}}
