@@ -96,7 +96,7 @@ def look_at_c2w(center, target, up=(0.0, -1.0, 0.0)) -> np.ndarray:
     z = np.asarray(target, np.float64) - c
     z /= np.linalg.norm(z)
     upv = np.asarray(up, np.float64)
-    x = np.cross(upv, z)
+    x = np.cross(z, upv)           # right = forward x up (y down, z forward)
     x /= np.linalg.norm(x)
     y = np.cross(z, x)
     return np.stack([x, y, z], axis=1)
@@ -286,6 +286,89 @@ def eye_cameras(rng: np.random.Generator, res: int, n_viewers: int,
     return cams
 
 
+# --------------------------------------------------------------------------
+# the paper's display geometry (Sec. 3.1) and its three-view lifting rig
+# (Sec. 4.1: Gaussians from the depth maps of cam0, cam2 and cam3)
+# --------------------------------------------------------------------------
+
+DISPLAY_DISTANCE = 1.25     # nominal eye-to-display distance (m)
+DISPLAY_SCALE = 0.5         # scale of the rendered upper body
+PANEL_HALF_HEIGHT = 0.1681  # 27-inch 16:9 panel: 0.598 m x 0.336 m
+VIEWER_LATERAL = 0.4        # left-right range 0.8 m (about 40 deg of view)
+VIEWER_DEPTH = 0.15         # forward-backward range 0.3 m
+REMOTE_EYE_DEPTH = 1.2      # remote eye centre on the rig axis, 1.2 m out
+
+
+def display_transform(remote_eye_depth: float = REMOTE_EYE_DEPTH, scale: float = DISPLAY_SCALE):
+    """Similarity x_local = s * Rm @ x_remote + tm that places the remote
+    user in front of the local display (Sec. 3.1).
+
+    Both sites use the frame of their own display: display centre at the
+    origin, x right, y down, user on the +z side.  The remote scene is
+    turned 180 deg about the vertical axis through the midpoint
+    M = (0, 0, d/2) of the remote eye-to-display segment (d = depth of the
+    remote eye centre E = (0, 0, d)), which puts E on the display plane,
+    then scaled by s about that image of E (the display centre)."""
+    d = float(remote_eye_depth)
+    Rm = np.diag([-1.0, 1.0, -1.0])
+    M = np.array([0.0, 0.0, 0.5 * d])
+    e_img = Rm @ (np.array([0.0, 0.0, d]) - M) + M      # = 0: the display centre
+    tm = scale * (M - Rm @ M - e_img) + e_img
+    return float(scale), Rm, tm
+
+
+def display_eye_camera(eye_local, res: int, remote_eye_depth: float = REMOTE_EYE_DEPTH,
+                       scale: float = DISPLAY_SCALE) -> Camera:
+    """Camera in the remote capture frame that sees the remote Gaussians as
+    a local eye at `eye_local` (display frame) sees them on the display.
+
+    The local eye looks at the display centre; its image spans the panel
+    height at the nominal 1.25 m (f = res * 1.25 / (2 * half height)).  A
+    perspective image is unchanged when the scene and the camera centre are
+    scaled together about a point, so the eye camera is carried back through
+    the inverse similarity: centre s^-1 Rm^T (e - tm), rotation Rm^T R_eye,
+    same intrinsics."""
+    s, Rm, tm = display_transform(remote_eye_depth, scale)
+    e = np.asarray(eye_local, np.float64)
+    R_eye = look_at_c2w(e, (0.0, 0.0, 0.0))
+    centre = Rm.T @ (e - tm) / s
+    f = res * DISPLAY_DISTANCE / (2.0 * PANEL_HALF_HEIGHT)
+    return make_camera(f, res, res, centre, Rm.T @ R_eye)
+
+
+def display_eye_cameras(rng: np.random.Generator, res: int, n_viewers: int, ipd: float = 0.064,
+                        heads=None) -> List[Camera]:
+    """Left+right eye cameras of `n_viewers` local viewers, each head drawn
+    uniformly over the paper's viewing range (lateral +-0.4 m, depth
+    1.25 +- 0.15 m from the display, eyes level with the display centre,
+    6.4 cm apart), mapped into the remote capture frame.  `heads` (n, 3)
+    overrides the draw."""
+    if heads is None:
+        heads = np.stack([rng.uniform(-VIEWER_LATERAL, VIEWER_LATERAL, n_viewers), np.zeros(n_viewers),
+                          DISPLAY_DISTANCE + rng.uniform(-VIEWER_DEPTH, VIEWER_DEPTH, n_viewers)], 1)
+    cams = []
+    for h in np.asarray(heads, np.float64):
+        for side in (-0.5, 0.5):
+            cams.append(display_eye_camera(h + np.array([side * ipd, 0.0, 0.0]), res))
+    return cams
+
+
+def scene_paper_rig(seed: int = 3, res: int = 1024, C: int = 32, n_viewers: int = 1,
+                    target_res: Optional[int] = None) -> Scene:
+    """The paper's lifting setup: Gaussians from three of the four capture
+    views only -- the upper-left camera of the narrow pair (cam0) and both
+    cameras of the wide pair (cam2, cam3) -- with the precision scene's map
+    generators (50% ellipse, ~1.58M Gaussians at 1024^2, BF16 features);
+    targets are display-mapped eye pairs of `n_viewers` viewers."""
+    rng = np.random.default_rng(seed)
+    f = float(res)
+    four = _rig_four(res, f)
+    cams = [four[0], four[2], four[3]]
+    targets = display_eye_cameras(np.random.default_rng([seed, 1]), target_res or res, n_viewers)
+    return _scene_from_rig(f"rig3-3x{res}-c{C}-bf16", cams, rng, C, FEAT_BF16,
+                           (0.42, 0.379), 10.0, targets, seed)
+
+
 def scene_frame(frame_id: int, res: int = 1024, C: int = 32) -> Scene:
     """Serving frame: the four-view precision scene regenerated with
     seed = frame id."""
@@ -326,4 +409,5 @@ WORKLOADS = {
     "tiny": scene_tiny,
     "paper": scene_paper,
     "precision": scene_precision,
+    "rig3": scene_paper_rig,
 }
