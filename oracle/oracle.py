@@ -60,6 +60,8 @@ def lib():
             _lib.orc_tile_list_bruteforce.restype = ctypes.c_int64
             _lib.orc_pixel_alternatives.restype = ctypes.c_int
             _lib.orc_num_threads.restype = ctypes.c_int
+            _lib.orc_key_ln_f32.restype = ctypes.c_float
+            _lib.orc_key_ln_f32.argtypes = [ctypes.c_float]
     return _lib
 
 
@@ -169,6 +171,7 @@ class Projected:
     radius: np.ndarray   # (N,) float32
     mu: np.ndarray       # (N,2) float32
     conic: np.ndarray    # (N,3) float32
+    mask: Optional[np.ndarray] = None   # (N,) uint32 kept-tile masks (tight binning)
 
 
 def project_f32(g32: Gaussians, cam, par=None) -> Projected:
@@ -180,6 +183,32 @@ def project_f32(g32: Gaussians, cam, par=None) -> Projected:
                     np.empty(n, np.float32), np.empty((n, 2), np.float32), np.empty((n, 3), np.float32))
     lib().orc_project_f32(_i64(n), _p(mean), _p(cov), _p(cam_array(cam)), _p(par),
                           _p(out.rect), _p(out.ntiles), _p(out.dkey), _p(out.radius), _p(out.mu), _p(out.conic))
+    return out
+
+
+def key_ln(x: float) -> float:
+    """ln x (x >= 1) in key mode, as the tight binning evaluates it."""
+    return float(lib().orc_key_ln_f32(ctypes.c_float(x)))
+
+
+def tighten(proj: Projected, opac: np.ndarray, width: int, height: int, par=None) -> Projected:
+    """Tight binning: keep only the tiles of each rect (of at most 32 tiles)
+    whose pixel-centre rectangle reaches Q <= 2 ln(o / alpha_min) (with a
+    rounding margin).  Returns a copy whose ntiles count the kept tiles and
+    whose mask holds them; Gaussians left with no tile are culled."""
+    par = params_array() if par is None else par
+    n = proj.rect.shape[0]
+    out = Projected(proj.rect.copy(), proj.ntiles.copy(), proj.dkey.copy(), proj.radius.copy(), proj.mu.copy(),
+                    proj.conic.copy(), np.empty(n, np.uint32))
+    lib().orc_tight_tiles_f32(_i64(n), _p(out.rect), _p(out.mu), _p(out.conic),
+                              _p(np.ascontiguousarray(opac, np.float32)), _p(par), ctypes.c_int(width),
+                              ctypes.c_int(height), _p(out.mask), _p(out.ntiles))
+    gone = (proj.ntiles > 0) & (out.ntiles == 0)
+    out.rect[gone] = 0
+    out.dkey[gone] = 0xFFFFFFFF
+    out.radius[gone] = 0
+    out.mu[gone] = 0
+    out.conic[gone] = 0
     return out
 
 
@@ -257,6 +286,15 @@ def tile_grid(width: int, height: int):
     return (width + TILE - 1) // TILE, (height + TILE - 1) // TILE
 
 
+def _emit(proj: Projected, offsets, tx, keys, vals):
+    n = proj.rect.shape[0]
+    if proj.mask is None:
+        lib().orc_emit(_i64(n), _p(proj.rect), _p(offsets), _p(proj.dkey), ctypes.c_int(tx), _p(keys), _p(vals))
+    else:
+        lib().orc_emit_masked(_i64(n), _p(proj.rect), _p(proj.mask), _p(offsets), _p(proj.dkey), ctypes.c_int(tx),
+                              _p(keys), _p(vals))
+
+
 def bin_gaussians(proj: Projected, width: int, height: int) -> Bins:
     n = proj.rect.shape[0]
     tx, ty = tile_grid(width, height)
@@ -264,7 +302,7 @@ def bin_gaussians(proj: Projected, width: int, height: int) -> Bins:
     P = int(lib().orc_scan(_i64(n), _p(proj.ntiles), _p(offsets)))
     keys = np.empty(max(P, 1), np.uint64)
     vals = np.empty(max(P, 1), np.uint32)
-    lib().orc_emit(_i64(n), _p(proj.rect), _p(offsets), _p(proj.dkey), ctypes.c_int(tx), _p(keys), _p(vals))
+    _emit(proj, offsets, tx, keys, vals)
     lib().orc_sort_pairs(_i64(P), _p(keys), _p(vals))
     keys, vals = keys[:P], vals[:P]
     ranges = np.empty((tx * ty, 2), np.uint32)
@@ -280,7 +318,7 @@ def emit_unsorted(proj: Projected, width: int, height: int):
     P = int(lib().orc_scan(_i64(n), _p(proj.ntiles), _p(offsets)))
     keys = np.empty(max(P, 1), np.uint64)
     vals = np.empty(max(P, 1), np.uint32)
-    lib().orc_emit(_i64(n), _p(proj.rect), _p(offsets), _p(proj.dkey), ctypes.c_int(tx), _p(keys), _p(vals))
+    _emit(proj, offsets, tx, keys, vals)
     return keys[:P], vals[:P]
 
 
@@ -385,7 +423,7 @@ class Render:
 
 
 def render(g32: Gaussians, cam, par=None, margins=None, tiles=None, feat64=None,
-           values: str = "key") -> Render:
+           values: str = "key", tight: bool = False) -> Render:
     """Key-mode binning of FP32 Gaussians, then FP64 compositing.
 
     values="key": the compositing consumes the projected record (mu, conic)
@@ -394,9 +432,12 @@ def render(g32: Gaussians, cam, par=None, margins=None, tiles=None, feat64=None,
     values="f64": mu and conic are re-derived in FP64 from the same
     Gaussians (end-to-end comparison, includes FP32 rounding of mu).
     `feat64` overrides the features that are composited (e.g. the original
-    FP32 features when the stored ones were rounded to BF16)."""
+    FP32 features when the stored ones were rounded to BF16).  `tight`
+    bins with the tight-binning variant (see `tighten`)."""
     par = params_array() if par is None else par
     proj = project_f32(g32, cam, par)
+    if tight:
+        proj = tighten(proj, g32.opac, cam.width, cam.height, par)
     bins = bin_gaussians(proj, cam.width, cam.height)
     if values == "key":
         mu64, conic64 = proj.mu.astype(np.float64), proj.conic.astype(np.float64)

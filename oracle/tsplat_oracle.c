@@ -581,6 +581,126 @@ void orc_emit(int64_t n, const int32_t *rect, const int64_t *offsets, const uint
     }
 }
 
+/* ------------------------------------------------------------------------
+ * Tight binning (an optional variant of the binning above; the paper's
+ * rasterizer keeps the whole rect).  A Gaussian can only be blended at a
+ * pixel where alpha = o exp(-Q/2) >= alpha_min, Q = d^T conic d, i.e. where
+ * Q <= kappa = 2 ln(o / alpha_min).  A tile of the rect is kept when the
+ * smallest Q over the rectangle spanned by the tile's pixel centres (clipped
+ * to the image) is at most kappa (1 + 2^-10) + 2^-8 -- a margin far above
+ * the rounding of any single-precision evaluation of alpha, so that a
+ * dropped tile holds no pixel the full rect would have blended.  Rects of
+ * more than 32 tiles are kept whole.  Everything here is key mode (strict
+ * single precision, in the order written).
+ * ------------------------------------------------------------------------ */
+
+/* ln x for finite x >= 1 in key mode, from the mathematics: x = 2^e m with
+ * m in [sqrt(1/2), sqrt(2)), ln x = e ln 2 + 2 atanh(t), t = (m - 1)/(m + 1),
+ * and atanh(t) = t + t^3/3 + t^5/5 + t^7/7 + t^9/9 + ... (|t| < 0.172, so the
+ * terms left out are below 1e-9). */
+float orc_key_ln_f32(float x)
+{
+    uint32_t u;
+    memcpy(&u, &x, 4);
+    int e = (int)((u >> 23) & 0xffu) - 127;
+    uint32_t mb = (u & 0x7fffffu) | 0x3f800000u;
+    float m;
+    memcpy(&m, &mb, 4);
+    if (m > 1.41421354f) {
+        m = m * 0.5f;
+        e = e + 1;
+    }
+    const float t = (m - 1.0f) / (m + 1.0f);
+    const float t2 = t * t;
+    float s = 0.111111111f;
+    s = s * t2 + 0.142857143f;
+    s = s * t2 + 0.2f;
+    s = s * t2 + 0.333333333f;
+    s = s * t2 + 1.0f;
+    return (float)e * 0.693147182f + 2.0f * (t * s);
+}
+
+/* Q = a dx^2 + 2 b dx dy + c dy^2 evaluated as dx (a dx + 2b dy) + (c dy) dy */
+static float tight_q(float a, float b2, float c, float dx, float dy)
+{
+    return dx * (a * dx + b2 * dy) + (c * dy) * dy;
+}
+
+static float clampf_(float v, float lo, float hi) { return fminf(hi, fmaxf(lo, v)); }
+
+/* Smallest Q over the rectangle [dx0, dx1] x [dy0, dy1] of offsets from the
+ * mean: 0 when the mean lies inside; else the least of the four edge minima
+ * (on each edge Q is a parabola, minimised at the clamped vertex). */
+static float tight_qmin(float a, float b, float c, float dx0, float dx1, float dy0, float dy1)
+{
+    if (dx0 <= 0.0f && dx1 >= 0.0f && dy0 <= 0.0f && dy1 >= 0.0f) return 0.0f;
+    const float b2 = 2.0f * b, ra = b / a, rc = b / c;
+    float q = INFINITY, d;
+    d = clampf_(-(ra * dy0), dx0, dx1); q = fminf(q, tight_q(a, b2, c, d, dy0));
+    d = clampf_(-(ra * dy1), dx0, dx1); q = fminf(q, tight_q(a, b2, c, d, dy1));
+    d = clampf_(-(rc * dx0), dy0, dy1); q = fminf(q, tight_q(a, b2, c, dx0, d));
+    d = clampf_(-(rc * dx1), dy0, dy1); q = fminf(q, tight_q(a, b2, c, dx1, d));
+    return q;
+}
+
+/* For each Gaussian with ntiles > 0 and a rect of at most 32 tiles: bit
+ * (ty - y0) * (x1 - x0) + (tx - x0) of mask[i] is set for a kept tile, and
+ * ntiles[i] becomes the number kept (0 culls).  mask[i] = 0xFFFFFFFF for
+ * rects kept whole, 0 for culled Gaussians.  opac: the stored opacities;
+ * par: params (alpha_min = par[2]); W, H: target size. */
+void orc_tight_tiles_f32(int64_t n, const int32_t *rect, const float *mu, const float *conic, const float *opac,
+                         const float *par, int W, int H, uint32_t *mask, int32_t *ntiles)
+{
+    const float amin = par[2];
+    for (int64_t i = 0; i < n; ++i) {
+        mask[i] = 0u;
+        if (ntiles[i] <= 0) continue;
+        const int x0 = rect[4 * i], y0 = rect[4 * i + 1], x1 = rect[4 * i + 2], y1 = rect[4 * i + 3];
+        const int w = x1 - x0, area = w * (y1 - y0);
+        if (area > 32) { mask[i] = 0xFFFFFFFFu; continue; }
+        const float ratio = opac[i] / amin;
+        uint32_t m = 0u;
+        if (ratio >= 1.0f) {
+            const float kappa = 2.0f * orc_key_ln_f32(ratio);
+            const float thr = kappa * 1.0009765625f + 0.00390625f;
+            const float mx = mu[2 * i], my = mu[2 * i + 1];
+            const float a = conic[3 * i], b = conic[3 * i + 1], c = conic[3 * i + 2];
+            for (int ty = y0; ty < y1; ++ty)
+                for (int tx = x0; tx < x1; ++tx) {
+                    const float px0 = (float)(TILE * tx), py0 = (float)(TILE * ty);
+                    const float px1 = (float)(TILE * tx + TILE - 1 < W - 1 ? TILE * tx + TILE - 1 : W - 1);
+                    const float py1 = (float)(TILE * ty + TILE - 1 < H - 1 ? TILE * ty + TILE - 1 : H - 1);
+                    const float qm = tight_qmin(a, b, c, px0 - mx, px1 - mx, py0 - my, py1 - my);
+                    if (qm <= thr) m |= 1u << ((ty - y0) * w + (tx - x0));
+                }
+        }
+        mask[i] = m;
+        int cnt = 0;
+        for (int k = 0; k < 32; ++k) cnt += (int)((m >> k) & 1u);
+        ntiles[i] = cnt;
+    }
+}
+
+/* Emission with the masks of orc_tight_tiles_f32: the kept tiles of each
+ * rect in row-major order (whole rects where mask = 0xFFFFFFFF). */
+void orc_emit_masked(int64_t n, const int32_t *rect, const uint32_t *mask, const int64_t *offsets,
+                     const uint32_t *dkey, int tiles_x, uint64_t *keys, uint32_t *vals)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t k = offsets[i];
+        const int x0 = rect[4 * i], y0 = rect[4 * i + 1], x1 = rect[4 * i + 2], y1 = rect[4 * i + 3];
+        const int w = x1 - x0;
+        for (int ty = y0; ty < y1; ++ty)
+            for (int tx = x0; tx < x1; ++tx) {
+                const int bit = (ty - y0) * w + (tx - x0);
+                if (mask[i] != 0xFFFFFFFFu && (bit >= 32 || !((mask[i] >> bit) & 1u))) continue;
+                keys[k] = ((uint64_t)(uint32_t)(ty * tiles_x + tx) << 32) | dkey[i];
+                vals[k] = (uint32_t)i;
+                ++k;
+            }
+    }
+}
+
 /* Stable bottom-up merge sort of (key, val) on the key alone. */
 void orc_sort_pairs(int64_t P, uint64_t *keys, uint32_t *vals)
 {

@@ -753,3 +753,110 @@ def test_chained_adjoints_match_central_differences_of_source_maps():
             assert abs(fd - an) <= 2e-3 * scale, (name, pos, fd, an)
             checked += 1
     assert checked == 56
+
+
+# ---------------------------------------------------------------------------
+# tight binning (a variant of the binning; not in the paper's rasterizer)
+# ---------------------------------------------------------------------------
+
+def test_key_ln_matches_math_log():
+    xs = np.concatenate([np.geomspace(1.0, 1e4, 2000), [1.0, 2.0, 1.41421354, 1.4142137, 255.0, 0.95 * 255.0]])
+    xs = xs.astype(np.float32)
+    err = max(abs(O.key_ln(float(x)) - math.log(float(x))) for x in xs)
+    assert err <= 1.5e-6
+    assert O.key_ln(1.0) == 0.0 and O.key_ln(2.0) == np.float32(math.log(2.0))
+
+
+def _tight_scene():
+    """Anisotropic random Gaussians (some below alpha_min in opacity, some
+    large) in a ragged 150 x 100 target."""
+    gs = gen.random_gaussians(31, 4000, 2, center=(0, 0, 1.2), spread=0.45, sigma_range=(0.001, 0.03))
+    rng = np.random.default_rng(32)
+    op = gs.opac.copy()
+    op[rng.choice(len(op), 200, replace=False)] = rng.uniform(0.0005, 0.0039, 200).astype(np.float32)
+    g32 = O.Gaussians(gs.mean, gs.cov, op, gs.feat)
+    cam = _cam(f=120.0, W=150, H=100)
+    return g32, cam
+
+
+def _pairs(proj, W, H):
+    b = O.bin_gaussians(proj, W, H)
+    return b, set(zip((b.keys >> 32).astype(np.int64).tolist(), b.ids.astype(np.int64).tolist()))
+
+
+def test_tight_binning_drops_only_tiles_without_a_blendable_pixel():
+    """Brute force over every pixel of every dropped (Gaussian, tile) pair:
+    alpha = o exp(-Q/2) < alpha_min there (FP64), so the full rect would
+    not have blended it anywhere in that tile."""
+    g32, cam = _tight_scene()
+    W, H = cam.width, cam.height
+    pr = O.project_f32(g32, cam, PAR)
+    pt = O.tighten(pr, g32.opac, W, H, PAR)
+    b0, full = _pairs(pr, W, H)
+    b1, tight = _pairs(pt, W, H)
+    assert tight <= full and len(tight) < 0.9 * len(full)
+    amin = float(PAR[2])
+    tx = (W + 15) // 16
+    for t, i in full - tight:
+        x0, y0 = 16 * (t % tx), 16 * (t // tx)
+        xs = np.arange(x0, min(x0 + 16, W), dtype=np.float64)
+        ys = np.arange(y0, min(y0 + 16, H), dtype=np.float64)
+        dx = xs[None, :] - float(pr.mu[i, 0])
+        dy = ys[:, None] - float(pr.mu[i, 1])
+        a, b, c = (float(v) for v in pr.conic[i])
+        Q = a * dx * dx + 2 * b * dx * dy + c * dy * dy
+        alpha = float(g32.opac[i]) * np.exp(-0.5 * Q)
+        assert alpha.max() < amin, (t, i)
+    # Gaussians whose opacity is below alpha_min have no tile at all
+    low = np.where(g32.opac < amin)[0]
+    assert np.all(pt.ntiles[low] == 0) and np.any(pr.ntiles[low] > 0)
+
+
+def test_tight_binning_keeps_tiles_the_ellipse_reaches():
+    """The kept tiles are not over-conservative: for each kept pair, dense
+    sampling of the tile's pixel-centre rectangle (FP64) finds a point with
+    Q within 2% of 2 ln(o / alpha_min) (the margin is 0.1% + 2^-8)."""
+    g32, cam = _tight_scene()
+    W, H = cam.width, cam.height
+    pr = O.project_f32(g32, cam, PAR)
+    pt = O.tighten(pr, g32.opac, W, H, PAR)
+    b1, tight = _pairs(pt, W, H)
+    amin = float(PAR[2])
+    tx = (W + 15) // 16
+    g = np.linspace(0.0, 1.0, 121)
+    checked = 0
+    for t, i in sorted(tight):
+        area = (pr.rect[i, 2] - pr.rect[i, 0]) * (pr.rect[i, 3] - pr.rect[i, 1])
+        if area > 32:
+            continue
+        x0, y0 = 16 * (t % tx), 16 * (t // tx)
+        x1, y1 = min(x0 + 15, W - 1), min(y0 + 15, H - 1)
+        dx = (x0 + g * (x1 - x0))[None, :] - float(pr.mu[i, 0])
+        dy = (y0 + g * (y1 - y0))[:, None] - float(pr.mu[i, 1])
+        a, b, c = (float(v) for v in pr.conic[i])
+        Q = a * dx * dx + 2 * b * dx * dy + c * dy * dy
+        kappa = 2 * math.log(float(g32.opac[i]) / amin)
+        assert Q.min() <= kappa * 1.02 + 0.05, (t, i, Q.min(), kappa)
+        checked += 1
+    assert checked > 1000
+
+
+def test_tight_binning_renders_the_same_maps():
+    """Dropping tiles that hold no blendable pixel changes no decision: the
+    FP64 composite with tight bins equals the full-rect one bit for bit,
+    and each pixel's last blended Gaussian is the same one."""
+    for g32, cam in [_tight_scene(), (O.lift_scene(gen.scene_paper(seed=5, res=96, C=3), "f32"),
+                                      gen.make_camera(110.0, 120, 90, (0.02, 0, 0), gen.rot_y(3.0)))]:
+        r0 = O.render(g32, cam, PAR)
+        r1 = O.render(g32, cam, PAR, tight=True)
+        assert r1.bins.P < r0.bins.P
+        assert np.array_equal(r0.comp.F, r1.comp.F) and np.array_equal(r0.comp.T, r1.comp.T)
+        assert np.array_equal(r0.comp.flags, r1.comp.flags)
+        yy, xx = np.mgrid[0:cam.height, 0:cam.width]
+        t = (yy // 16) * r0.bins.tiles_x + xx // 16
+        gid = []
+        for rr in (r0, r1):
+            pos = rr.bins.ranges[t, 0].astype(np.int64) + rr.comp.last.astype(np.int64) - 1
+            ids = rr.bins.ids.astype(np.int64)[np.clip(pos, 0, max(rr.bins.P - 1, 0))]
+            gid.append(np.where(rr.comp.last > 0, ids, -1))
+        assert np.array_equal(gid[0], gid[1]) and (gid[0] >= 0).mean() > 0.3
