@@ -81,7 +81,18 @@ enum {
     TSPLAT_RENDER_SAVE = 1u << 1,
     /* Record CUDA events between the stages of this render on its stream
      * (read back with tsplat_ctx_timings). */
-    TSPLAT_RENDER_PROFILE = 1u << 2
+    TSPLAT_RENDER_PROFILE = 1u << 2,
+    /* Tight binning (a variant; the cited rasterizer keeps the whole rect).
+     * A tile of a Gaussian's rect (rects of at most 32 tiles; larger ones
+     * stay whole) is kept only when the smallest Q = d^T conic d over the
+     * rectangle of the tile's pixel centres, clipped to the image, is at
+     * most 2 ln(o / alpha_min) (1 + 2^-10) + 2^-8: dropped tiles hold no
+     * pixel with alpha >= alpha_min, so the maps equal the full-rect ones up
+     * to the order of FP32 accumulation, while the pairs to sort and
+     * composite shrink.  Gaussians left with no tile (e.g. o < alpha_min)
+     * are culled.  All of it in single precision, one rounding per
+     * operation, so the tile lists are reproducible bit for bit. */
+    TSPLAT_RENDER_TIGHT = 1u << 3
 };
 
 /* Rasterizer constants (the 3DGS rasterizer's; all parameters). */

@@ -50,10 +50,12 @@ def ccamera(cam) -> L.CCamera:
 
 
 def cparams(lowpass=0.3, alpha_max=0.99, alpha_min=1.0 / 255.0, t_min=1e-4, frustum_clamp=1.3,
-            save=False, async_=False, profile=False) -> L.CParams:
+            save=False, async_=False, profile=False, tight=False) -> L.CParams:
+    """tsplat_render_params; `tight` selects tight binning (TSPLAT_RENDER_TIGHT)."""
     p = L.CParams()
     p.lowpass, p.alpha_max, p.alpha_min, p.t_min, p.frustum_clamp = lowpass, alpha_max, alpha_min, t_min, frustum_clamp
-    p.flags = (L.RENDER_SAVE if save else 0) | (L.RENDER_ASYNC if async_ else 0) | (L.RENDER_PROFILE if profile else 0)
+    p.flags = ((L.RENDER_SAVE if save else 0) | (L.RENDER_ASYNC if async_ else 0) | (L.RENDER_PROFILE if profile else 0)
+               | (L.RENDER_TIGHT if tight else 0))
     return p
 
 

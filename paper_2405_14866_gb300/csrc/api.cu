@@ -106,7 +106,7 @@ struct tsplat_gaussians {
 
 struct tsplat_ctx {
     // N-sized
-    DBuf hdr, rect, ntiles, dkey, radius, skeys0, skeys1, svals0, svals1, hist_n, emit_blk;
+    DBuf hdr, rect, ntiles, tmask, dkey, radius, skeys0, skeys1, svals0, svals1, hist_n, emit_blk;
     // P-sized
     DBuf pk0, pk1, pv0, pv1, hist_p;
     // tiles / pixels / view table
@@ -346,7 +346,7 @@ tsplat_status tsplat_ctx_create(tsplat_ctx **out) {
 tsplat_status tsplat_ctx_destroy(tsplat_ctx *c) {
     if (!c) return TSPLAT_OK;
     cudaDeviceSynchronize();
-    DBuf *bufs[] = {&c->hdr, &c->rect, &c->ntiles, &c->dkey, &c->radius, &c->skeys0, &c->skeys1, &c->svals0,
+    DBuf *bufs[] = {&c->hdr, &c->rect, &c->ntiles, &c->tmask, &c->dkey, &c->radius, &c->skeys0, &c->skeys1, &c->svals0,
                     &c->svals1, &c->hist_n, &c->emit_blk, &c->pk0, &c->pk1, &c->pv0, &c->pv1, &c->hist_p,
                     &c->ranges, &c->tfinal, &c->last, &c->views, &c->zkeys, &c->torder, &c->small};
     for (DBuf *b : bufs) release(*b);
@@ -364,6 +364,7 @@ static tsplat_status ensure_n(tsplat_ctx *c, int64_t n, cudaStream_t s) {
     TRY(grow(c->hdr, N * sizeof(Header), s));
     TRY(grow(c->rect, N * 8, s));
     TRY(grow(c->ntiles, N * 4, s));
+    TRY(grow(c->tmask, N * 4, s));
     TRY(grow(c->dkey, N * 4, s));
     TRY(grow(c->radius, N * 4, s));
     TRY(grow(c->skeys0, N * 4, s));
@@ -475,6 +476,7 @@ static tsplat_status render_tail(tsplat_ctx *c, int64_t n_cap, const uint32_t *n
     em.n_cap = inst_cap;
     em.ntiles = c->ntiles.as<uint32_t>();
     em.rect = c->rect.as<uint2>();
+    em.tmask = (par.flags & TSPLAT_RENDER_TIGHT) ? c->tmask.as<uint32_t>() : nullptr;
     em.views = c->views.as<RenderView>();
     em.n_stride = n_dev;
     em.blk_sum = c->emit_blk.as<uint32_t>();
@@ -595,6 +597,7 @@ static ProjectOut project_out(tsplat_ctx *c) {
     o.hdr = c->hdr.as<Header>();
     o.rect = c->rect.as<uint2>();
     o.ntiles = c->ntiles.as<uint32_t>();
+    o.tmask = c->tmask.as<uint32_t>();
     o.dkey = c->dkey.as<uint32_t>();
     o.radius = c->radius.as<float>();
     o.kminmax = small_ptr(c, SM_KMIN);

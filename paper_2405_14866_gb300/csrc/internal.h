@@ -84,7 +84,10 @@ struct ProjectOut {
     float *radius;      // [N]
     uint32_t *kminmax;  // [2] min / max depth key of rendered Gaussians (pre-set to ~0u / 0)
     uint32_t *n_vis;    // [1] rendered Gaussians (pre-set to 0)
+    uint32_t *tmask;    // [N] kept-tile masks (written with TSPLAT_RENDER_TIGHT)
 };
+// Rects of at most this many tiles are tested tile by tile in tight binning.
+constexpr int TIGHT_MAX_TILES = 32;
 // Instances: view v's copy of Gaussian g is instance v * N + g, N = *n_dev
 // (n_cap >= N bounds the grid).  Also writes the view table to views_dev.
 void launch_project(const float4 *xyzo, const float4 *cova, const float2 *covb,
@@ -148,6 +151,7 @@ struct EmitArgs {
     int64_t n_cap;
     const uint32_t *ntiles;
     const uint2 *rect;
+    const uint32_t *tmask;     // kept-tile masks, or nullptr (whole rects)
     const RenderView *views;   // instance i belongs to view i / N
     const uint32_t *n_stride;  // N (device)
     uint32_t *blk_sum;         // [nblocks]

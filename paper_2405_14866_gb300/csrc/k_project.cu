@@ -99,6 +99,93 @@ __device__ __forceinline__ int tile_rect(float mx, float my, float r, int tiles_
     return (x1 - x0) * (y1 - y0);
 }
 
+// ---- tight binning (TSPLAT_RENDER_TIGHT) --------------------------------
+// Single precision, one rounding per operation, in a fixed order, so that
+// an independent implementation of the same steps keeps the same tiles.
+
+// ln x for finite x >= 1: x = 2^e m with m in [sqrt(1/2), sqrt(2)),
+// ln x = e ln 2 + 2 atanh(t), t = (m - 1)/(m + 1), with atanh summed as its
+// odd power series up to t^9 (|t| < 0.172: the rest is below 1e-9).
+__device__ __forceinline__ float key_ln(float x) {
+    const uint32_t u = __float_as_uint(x);
+    int e = (int)((u >> 23) & 0xffu) - 127;
+    float m = __uint_as_float((u & 0x7fffffu) | 0x3f800000u);
+    if (m > 1.41421354f) {
+        m = fmul(m, 0.5f);
+        e += 1;
+    }
+    const float t = fdiv(fsub(m, 1.0f), fadd(m, 1.0f));
+    const float t2 = fmul(t, t);
+    float sr = 0.111111111f;
+    sr = fadd(fmul(sr, t2), 0.142857143f);
+    sr = fadd(fmul(sr, t2), 0.2f);
+    sr = fadd(fmul(sr, t2), 0.333333333f);
+    sr = fadd(fmul(sr, t2), 1.0f);
+    return fadd(fmul(__int2float_rn(e), 0.693147182f), fmul(2.0f, fmul(t, sr)));
+}
+
+// Q = a dx^2 + 2b dx dy + c dy^2 as dx (a dx + 2b dy) + (c dy) dy
+__device__ __forceinline__ float tight_q(float a, float b2, float c, float dx, float dy) {
+    return fadd(fmul(dx, fadd(fmul(a, dx), fmul(b2, dy))), fmul(fmul(c, dy), dy));
+}
+
+// Smallest Q over [dx0, dx1] x [dy0, dy1] when the mean lies outside it:
+// the least of the four edge minima (each edge: the parabola's clamped
+// vertex).  (With the mean inside, the smallest Q is 0.)
+__device__ __forceinline__ float tight_qmin_outside(float a, float b2, float c, float ra, float rc, float dx0,
+                                                    float dx1, float dy0, float dy1) {
+    float q = INFINITY;
+    q = fminf(q, tight_q(a, b2, c, fminf(dx1, fmaxf(dx0, -fmul(ra, dy0))), dy0));
+    q = fminf(q, tight_q(a, b2, c, fminf(dx1, fmaxf(dx0, -fmul(ra, dy1))), dy1));
+    q = fminf(q, tight_q(a, b2, c, dx0, fminf(dy1, fmaxf(dy0, -fmul(rc, dx0)))));
+    q = fminf(q, tight_q(a, b2, c, dx1, fminf(dy1, fmaxf(dy0, -fmul(rc, dx1)))));
+    return q;
+}
+
+// Kept tiles of the rect [x0, x1) x [y0, y1) (at most 32 tiles): bit
+// (ty - y0) * (x1 - x0) + (tx - x0) is set when the tile's pixel-centre
+// rectangle (clipped to the W x H image) reaches Q <= 2 ln(o / alpha_min)
+// (1 + 2^-10) + 2^-8.  Conic (a, b, c) of the inverse 2D covariance.
+__device__ uint32_t tight_mask(float mx, float my, float a, float b, float c, float o, float alpha_min, int x0,
+                               int y0, int x1, int y1, int W, int H) {
+    const float ratio = fdiv(o, alpha_min);
+    if (!(ratio >= 1.0f)) return 0u;
+    const int w = x1 - x0;
+    if (w == 1 && y1 - y0 == 1) {  // one tile holding the mean: kept (Q = 0 < threshold)
+        const float dx0 = fsub((float)(16 * x0), mx), dx1 = fsub((float)min(16 * x0 + 15, W - 1), mx);
+        const float dy0 = fsub((float)(16 * y0), my), dy1 = fsub((float)min(16 * y0 + 15, H - 1), my);
+        if (dx0 <= 0.0f && dx1 >= 0.0f && dy0 <= 0.0f && dy1 >= 0.0f) return 1u;
+    }
+    const float kappa = fmul(2.0f, key_ln(ratio));
+    const float thr = fadd(fmul(kappa, 1.0009765625f), 0.00390625f);
+    const float b2 = fmul(2.0f, b), ra = fdiv(b, a), rc = fdiv(b, c);
+    uint32_t m = 0u;
+    for (int ty = y0; ty < y1; ++ty) {
+        const float dy0 = fsub((float)(16 * ty), my), dy1 = fsub((float)min(16 * ty + 15, H - 1), my);
+        for (int tx = x0; tx < x1; ++tx) {
+            const float dx0 = fsub((float)(16 * tx), mx), dx1 = fsub((float)min(16 * tx + 15, W - 1), mx);
+            if ((dx0 <= 0.0f && dx1 >= 0.0f && dy0 <= 0.0f && dy1 >= 0.0f) ||
+                tight_qmin_outside(a, b2, c, ra, rc, dx0, dx1, dy0, dy1) <= thr)
+                m |= 1u << ((ty - y0) * w + (tx - x0));
+        }
+    }
+    return m;
+}
+
+// Applies tight binning to a visible Gaussian's tile count: writes its mask
+// and returns the tiles kept (0 culls).  Whole rects above 32 tiles.
+__device__ __forceinline__ int tighten(const ProjectOut &o, uint64_t i, int nt, float mx, float my, float a,
+                                       float b, float c, float op, float alpha_min, int x0, int y0, int x1, int y1,
+                                       int W, int H) {
+    if (nt > TIGHT_MAX_TILES) {
+        o.tmask[i] = 0xffffffffu;
+        return nt;
+    }
+    const uint32_t m = tight_mask(mx, my, a, b, c, op, alpha_min, x0, y0, x1, y1, W, H);
+    o.tmask[i] = m;
+    return __popc(m);
+}
+
 // Copy the view table to device memory for the kernels after this one.
 __device__ __forceinline__ void publish_views(const ViewBatch &vb, RenderView *views_dev) {
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x < (unsigned)vb.n_views) views_dev[threadIdx.x] = vb.v[threadIdx.x];
@@ -106,7 +193,7 @@ __device__ __forceinline__ void publish_views(const ViewBatch &vb, RenderView *v
 
 // grid (gx, n_views): view blockIdx.y; blocks stride over the Gaussians gi
 // (gx is at most a few waves, whatever the capacity); instance i = view * N + gi.
-__global__ __launch_bounds__(256) void k_project(const float4 *__restrict__ xyzo,
+__global__ __launch_bounds__(256, 4) void k_project(const float4 *__restrict__ xyzo,
                                                  const float4 *__restrict__ cova,
                                                  const float2 *__restrict__ covb,
                                                  const uint32_t *n_dev,
@@ -171,11 +258,14 @@ __global__ __launch_bounds__(256) void k_project(const float4 *__restrict__ xyzo
             const float mx = fadd(fdiv(fmul(cam.fx, px), pz), cam.cx);
             const float my = fadd(fdiv(fmul(cam.fy, py), pz), cam.cy);
             int x0, y0, x1, y1;
-            const int nt = tile_rect(mx, my, r, tiles_x, tiles_y, x0, y0, x1, y1);
+            int nt = tile_rect(mx, my, r, tiles_x, tiles_y, x0, y0, x1, y1);
+            const float ca_ = fdiv(c, det), cb_ = -fdiv(b, det), cc_ = fdiv(a, det);
+            if (nt > 0 && (par.flags & TSPLAT_RENDER_TIGHT))
+                nt = tighten(o, i, nt, mx, my, ca_, cb_, cc_, g.w, par.alpha_min, x0, y0, x1, y1, cam.width,
+                             cam.height);
             if (nt <= 0) {
                 vis = false;
             } else {
-                const float ca_ = fdiv(c, det), cb_ = -fdiv(b, det), cc_ = fdiv(a, det);
                 float ex, ey;
                 cull_extents(ca_, cb_, cc_, g.w, par.alpha_min, ex, ey);
                 o.hdr[i].h0 = make_float4(mx, my, -0.5f * ca_, -cb_);
@@ -222,11 +312,14 @@ __global__ __launch_bounds__(256) void k_prepare_2d(uint64_t n, const float *__r
         const float mx = mean2d[2 * i], my = mean2d[2 * i + 1];
         const float r = (float)ri;
         int x0, y0, x1, y1;
-        const int nt = tile_rect(mx, my, r, tiles_x, tiles_y, x0, y0, x1, y1);
+        int nt = tile_rect(mx, my, r, tiles_x, tiles_y, x0, y0, x1, y1);
+        const float a = conic[3 * i], b = conic[3 * i + 1], c = conic[3 * i + 2];
+        if (nt > 0 && (par.flags & TSPLAT_RENDER_TIGHT))
+            nt = tighten(o, i, nt, mx, my, a, b, c, opac[i], par.alpha_min, x0, y0, x1, y1, vb.v[0].cam.width,
+                         vb.v[0].cam.height);
         if (nt <= 0) {
             vis = false;
         } else {
-            const float a = conic[3 * i], b = conic[3 * i + 1], c = conic[3 * i + 2];
             float ex, ey;
             cull_extents(a, b, c, opac[i], par.alpha_min, ex, ey);
             o.hdr[i].h0 = make_float4(mx, my, -0.5f * a, -b);

@@ -352,13 +352,14 @@ __global__ __launch_bounds__(EM_THREADS) void k_emit_write(EmitArgs a) {
     const uint64_t base = (uint64_t)b * EM_TILE;
     for (int r = 0; r < EM_ITEMS; ++r) {
         const uint64_t k = base + (uint64_t)r * EM_THREADS + threadIdx.x;
-        uint32_t id = 0, cnt = 0, vbase = 0;
+        uint32_t id = 0, cnt = 0, vbase = 0, msk = 0xffffffffu;
         int x0 = 0, y0 = 0, x1 = 0, y1 = 0, vtx = 0;
         if (k < n) {
             id = sorted_val(a.order, np, k);
             cnt = a.ntiles[id];
             if (cnt) {
                 unpack_rect(a.rect[id], x0, y0, x1, y1);
+                if (a.tmask) msk = a.tmask[id];
                 const RenderView &vw = a.views[id / ns];
                 vbase = vw.tile_base;
                 vtx = vw.tiles_x;
@@ -385,8 +386,14 @@ __global__ __launch_bounds__(EM_THREADS) void k_emit_write(EmitArgs a) {
             const uint32_t oid = __shfl_sync(FULL, id, o);
             const uint32_t ovb = __shfl_sync(FULL, vbase, o);
             const int otx = __shfl_sync(FULL, vtx, o);
+            const uint32_t omsk = __shfl_sync(FULL, msk, o);
             if (e < wtot) {
-                const int loc = (int)(e - so);
+                int loc = (int)(e - so);
+                if (omsk != 0xffffffffu) {  // tight binning: the loc-th kept tile of the rect
+                    uint32_t mm = omsk;
+                    for (int j = 0; j < loc; ++j) mm &= mm - 1u;
+                    loc = __ffs(mm) - 1;
+                }
                 const int ty = oy0 + loc / ow, tx = ox0 + loc % ow;
                 a.pair_tile[wfirst + e] = ovb + (uint32_t)(ty * otx + tx);
                 a.pair_id[wfirst + e] = oid;
