@@ -516,6 +516,92 @@ def diff_bench(api, torch, steps=10, warmup=3):
 
 
 # ---------------------------------------------------------------------------
+# end to end: host buffers in, host buffers out
+# ---------------------------------------------------------------------------
+
+def e2e_run(api, torch, sc, g, ctx, cam, F, A, steps, world, compact):
+    """End to end through the public API with host buffers: every step
+    copies the source views from pinned host memory, lifts them, renders,
+    and copies F and A back.  Steps are pipelined over three streams with
+    double-buffered device inputs and outputs: the copies of one step overlap
+    the lifting and rendering of another.  compact: the maps carry only the
+    foreground pixels' rows (TSPLAT_SRC_COMPACT), as a producer that knows
+    the mask writes them."""
+    up = api.upload_scene(sc, feat_dtype=sc.feat_dtype, compact=compact)
+    pin = [{k: t.cpu().pin_memory() for k, t in v.items() if k != "cam"} for v in up["views"]]
+    dev_sets = [[{k: torch.empty_like(t) for k, t in v.items() if k != "cam"} for v in up["views"]] for _ in range(2)]
+    view_sets = [[api.source_view(d["depth"], d["mask"], d["scale"], d["quat"], d["opacity"], d["feat"], v["cam"],
+                                  compact=compact)
+                  for d, v in zip(ds, up["views"])] for ds in dev_sets]
+    del up
+    outs = [(torch.empty_like(F), torch.empty_like(A)) for _ in range(2)]
+    Fh = [torch.empty(F.shape, dtype=F.dtype, pin_memory=True) for _ in range(2)]
+    Ah = [torch.empty(A.shape, dtype=A.dtype, pin_memory=True) for _ in range(2)]
+    h2d = sum(t.numel() * t.element_size() for v in pin for t in v.values())
+    d2h = F.numel() * 4 + A.numel() * 4
+    cs, ks, ds = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    ev_in = [torch.cuda.Event() for _ in range(2)]
+    ev_free = [torch.cuda.Event() for _ in range(2)]
+    ev_out = [torch.cuda.Event() for _ in range(2)]
+    ev_read = [torch.cuda.Event() for _ in range(2)]
+    for e in ev_free + ev_read:
+        e.record(ks)
+
+    def e2e_step(k):
+        b = k & 1
+        with torch.cuda.stream(cs):
+            cs.wait_event(ev_free[b])
+            for d, p in zip(dev_sets[b], pin):
+                for key, t in p.items():
+                    d[key].copy_(t, non_blocking=True)
+            ev_in[b].record(cs)
+        ks.wait_event(ev_in[b])
+        g.build_into(view_sets[b], stream=ks)
+        ev_free[b].record(ks)
+        ks.wait_event(ev_read[b])  # the outputs of step k - 2 have been copied out
+        ctx.render(g, cam, async_=True, out_feat=outs[b][0], out_alpha=outs[b][1], stream=ks)
+        ev_out[b].record(ks)
+        with torch.cuda.stream(ds):
+            ds.wait_event(ev_out[b])
+            Fh[b].copy_(outs[b][0], non_blocking=True)
+            Ah[b].copy_(outs[b][1], non_blocking=True)
+            ev_read[b].record(ds)
+
+    for k in range(2):
+        e2e_step(k)
+    torch.cuda.synchronize()
+    x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    x0.record(cs)
+    ks.wait_event(x0)
+    ds.wait_event(x0)
+    for k in range(steps):
+        e2e_step(k)
+    cs.wait_stream(ks)
+    cs.wait_stream(ds)
+    x1.record(cs)
+    torch.cuda.synchronize()
+    ctx.status()
+    e2e_ms = x0.elapsed_time(x1) / steps
+    # the copy engine's rate on one large pinned buffer, for context
+    big = torch.empty(256 << 20, dtype=torch.uint8, pin_memory=True)
+    bigd = torch.empty_like(big, device="cuda")
+    bigd.copy_(big, non_blocking=True)
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0.record()
+    for _ in range(4):
+        bigd.copy_(big, non_blocking=True)
+    c1.record()
+    torch.cuda.synchronize()
+    maps = "foreground rows only (TSPLAT_SRC_COMPACT) + full masks" if compact else "full H x W maps"
+    return {"value": world * 1e3 / e2e_ms, "unit": "views/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms,
+            "pipeline": "host-to-device, compute and device-to-host streams; double-buffered inputs and outputs",
+            "inputs": f"{len(sc.views)} source views, {maps}: depth, scale, quaternion, opacity f32, mask u8, "
+                      f"features {'BF16' if sc.feat_dtype == api.BF16 else 'FP32'}",
+            "h2d_gbs_one_buffer": 4 * big.numel() / (c0.elapsed_time(c1) * 1e-3) / 1e9}
+
+
+# ---------------------------------------------------------------------------
 # the paper's own setup: three lifted views, display-mapped eye views
 # ---------------------------------------------------------------------------
 
@@ -680,6 +766,20 @@ def run_ours(args):
     torch.cuda.synchronize()
     build_ms = b0.elapsed_time(b1) / args.steps
     ctx.status()
+    # the same lifting from compact maps (foreground rows only), for context
+    upc = api.upload_scene(sc, feat_dtype=sc.feat_dtype, compact=True)
+    cviews = [api.source_view(v["depth"], v["mask"], v["scale"], v["quat"], v["opacity"], v["feat"], v["cam"],
+                              compact=True) for v in upc["views"]]
+    for _ in range(3):
+        g.build_into(cviews)
+    b0.record()
+    for _ in range(args.steps):
+        g.build_into(cviews)
+    b1.record()
+    torch.cuda.synchronize()
+    build_compact_ms = b0.elapsed_time(b1) / args.steps
+    g.build_into(views)
+    del cviews, upc
 
     # roofline of the dominant kernel (compositing): algorithmic bytes per
     # launch = P (4 B id + 24 B record + C*b_f features) + W*H*(4C + 4) outputs
@@ -701,80 +801,10 @@ def run_ours(args):
     build_bytes = sum(v.depth.size for v in sc.views) + N * (4 + 12 + 16 + 4 + fin * sc.C) + N * (40 + sc.C * bf)
 
     # end to end through the public API with host buffers
-    e2e = None
+    e2e = e2e_full = None
     if not args.no_e2e:
-        # End to end through the public API with host buffers: every step
-        # copies the four source views from pinned host memory, lifts them,
-        # renders, and copies F and A back.  Steps are pipelined over two
-        # streams with double-buffered device inputs and outputs: the copies
-        # of one step overlap the lifting and rendering of the previous one.
-        pin = [{k: t.cpu().pin_memory() for k, t in v.items() if k != "cam"} for v in up["views"]]
-        dev_sets = [[{k: torch.empty_like(t) for k, t in v.items() if k != "cam"} for v in up["views"]] for _ in range(2)]
-        view_sets = [[api.source_view(d["depth"], d["mask"], d["scale"], d["quat"], d["opacity"], d["feat"], v["cam"])
-                      for d, v in zip(ds, up["views"])] for ds in dev_sets]
-        outs = [(torch.empty_like(F), torch.empty_like(A)) for _ in range(2)]
-        Fh = [torch.empty(F.shape, dtype=F.dtype, pin_memory=True) for _ in range(2)]
-        Ah = [torch.empty(A.shape, dtype=A.dtype, pin_memory=True) for _ in range(2)]
-        h2d = sum(t.numel() * t.element_size() for v in pin for t in v.values())
-        d2h = F.numel() * 4 + A.numel() * 4
-        cs, ks, ds = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
-        ev_in = [torch.cuda.Event() for _ in range(2)]
-        ev_free = [torch.cuda.Event() for _ in range(2)]
-        ev_out = [torch.cuda.Event() for _ in range(2)]
-        ev_read = [torch.cuda.Event() for _ in range(2)]
-        for e in ev_free + ev_read:
-            e.record(ks)
-
-        def e2e_step(k):
-            b = k & 1
-            with torch.cuda.stream(cs):
-                cs.wait_event(ev_free[b])
-                for d, p in zip(dev_sets[b], pin):
-                    for key, t in p.items():
-                        d[key].copy_(t, non_blocking=True)
-                ev_in[b].record(cs)
-            ks.wait_event(ev_in[b])
-            g.build_into(view_sets[b], stream=ks)
-            ev_free[b].record(ks)
-            ks.wait_event(ev_read[b])  # the outputs of step k - 2 have been copied out
-            ctx.render(g, cam, async_=True, out_feat=outs[b][0], out_alpha=outs[b][1], stream=ks)
-            ev_out[b].record(ks)
-            with torch.cuda.stream(ds):
-                ds.wait_event(ev_out[b])
-                Fh[b].copy_(outs[b][0], non_blocking=True)
-                Ah[b].copy_(outs[b][1], non_blocking=True)
-                ev_read[b].record(ds)
-
-        for k in range(2):
-            e2e_step(k)
-        torch.cuda.synchronize()
-        x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        x0.record(cs)
-        ks.wait_event(x0)
-        ds.wait_event(x0)
-        for k in range(args.e2e_steps):
-            e2e_step(k)
-        cs.wait_stream(ks)
-        cs.wait_stream(ds)
-        x1.record(cs)
-        torch.cuda.synchronize()
-        ctx.status()
-        e2e_ms = x0.elapsed_time(x1) / args.e2e_steps
-        # the copy engine's rate on one large pinned buffer, for context
-        big = torch.empty(256 << 20, dtype=torch.uint8, pin_memory=True)
-        bigd = torch.empty_like(big, device="cuda")
-        bigd.copy_(big, non_blocking=True)
-        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        c0.record()
-        for _ in range(4):
-            bigd.copy_(big, non_blocking=True)
-        c1.record()
-        torch.cuda.synchronize()
-        e2e = {"value": world * 1e3 / e2e_ms, "unit": "views/s", "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms,
-               "pipeline": "host-to-device, compute and device-to-host streams; double-buffered inputs and outputs",
-               "inputs": "four 1024^2 source views: depth, mask, scale, quaternion, opacity f32/u8, features BF16",
-               "h2d_gbs_one_buffer": 4 * big.numel() / (c0.elapsed_time(c1) * 1e-3) / 1e9}
+        e2e = e2e_run(api, torch, sc, g, ctx, cam, F, A, args.e2e_steps, world, compact=True)
+        e2e_full = e2e_run(api, torch, sc, g, ctx, cam, F, A, args.e2e_steps, world, compact=False)
 
     # tight binning (TSPLAT_RENDER_TIGHT): same maps, fewer pairs; its
     # composite roofline stays quoted against the full-rect bytes
@@ -852,8 +882,10 @@ def run_ours(args):
                 "render_only": {"views_per_s": 1e3 / render_ms, "ms": render_ms,
                                 "frac_of_peak": path_bytes / (render_ms * 1e-3) / 1e9 / peak},
                 "build_ms": build_ms, "build_gbs": build_bytes / (build_ms * 1e-3) / 1e9,
+                "build_compact_maps_ms": build_compact_ms,
                 "gaussians_per_s": value * N,
-                "stages_ms": stages, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "stages_ms": stages, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "e2e_full_maps": e2e_full,
+                "clocks": clocks,
                 "tight_binning": tight,
                 "serving": serving, "differentiation": diff, "zbuffer": zbuffer, "paper_rig": rig,
                 "gpu_launches": int(launches)}

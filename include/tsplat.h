@@ -108,6 +108,17 @@ typedef struct {
 /* Fill `p` with the defaults listed above (flags = 0). */
 void tsplat_render_params_default(tsplat_render_params *p);
 
+/* flags of tsplat_src_view */
+enum {
+    /* depth, scale, quat, opacity and feat hold only the foreground pixels
+     * (mask nonzero), in row-major pixel order: n_fg rows instead of H*W.
+     * The mask is required.  Background pixels carry nothing the lifting
+     * reads, so this halves the bytes to move for a half-foreground view.
+     * Not accepted by tsplat_build_backward (whose outputs are full maps) or
+     * tsplat_build_into_noalloc (TSPLAT_ERR_UNSUPPORTED there). */
+    TSPLAT_SRC_COMPACT = 1
+};
+
 /* One source view (Sec. 4.2: depth map plus the encoder's per-pixel maps).
  * All map pointers are device pointers, row-major H x W (x channels):
  *   depth    H*W   f32  camera-space z in metres
@@ -116,7 +127,8 @@ void tsplat_render_params_default(tsplat_render_params *p);
  *   quat     H*W*4 f32  (w,x,y,z) rotation of the axes in the source camera
  *                       frame; NULL = identity (the paper's choice)
  *   opacity  H*W   f32  (M_alpha)
- *   feat     H*W*C      latent features (M_f), type feat_dtype */
+ *   feat     H*W*C      latent features (M_f), type feat_dtype
+ * (with TSPLAT_SRC_COMPACT: n_fg rows of each map but the mask). */
 typedef struct {
     const float *depth;
     const uint8_t *mask;
@@ -125,7 +137,7 @@ typedef struct {
     const float *opacity;
     const void *feat;
     int32_t feat_dtype;
-    int32_t reserved;
+    int32_t flags;        /* TSPLAT_SRC_* (0: full maps) */
     tsplat_camera cam;
 } tsplat_src_view;
 

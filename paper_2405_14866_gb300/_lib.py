@@ -36,7 +36,7 @@ class CParams(Structure):
 
 class CSrcView(Structure):
     _fields_ = [("depth", c_void_p), ("mask", c_void_p), ("scale", c_void_p), ("quat", c_void_p),
-                ("opacity", c_void_p), ("feat", c_void_p), ("feat_dtype", c_int32), ("reserved", c_int32),
+                ("opacity", c_void_p), ("feat", c_void_p), ("feat_dtype", c_int32), ("flags", c_int32),
                 ("cam", CCamera)]
 
 

@@ -77,36 +77,58 @@ def launch_count() -> int:
     return int(L.lib().tsplat_launch_count())
 
 
-def source_view(depth, mask, scale, quat, opacity, feat, cam, feat_dtype=None) -> L.CSrcView:
+SRC_COMPACT = 1  # TSPLAT_SRC_COMPACT
+
+
+def source_view(depth, mask, scale, quat, opacity, feat, cam, feat_dtype=None, compact=False,
+                check=True) -> L.CSrcView:
     """tsplat_src_view from CUDA tensors (H,W), (H,W) u8 or None, (H,W,3),
     (H,W,4) or None, (H,W), (H,W,C) f32 or bf16 (feat_dtype defaults to the
-    feature tensor's type).  The tensors must stay alive until the build has
-    run."""
+    feature tensor's type).  compact=True: every map but the mask holds the
+    foreground pixels only, in row-major order ((n_fg,), (n_fg,3), ...).
+    The tensors must stay alive until the build has run.  check=False skips
+    the shape checks (for tests of the library's own argument checks)."""
+    H, W = int(cam.height), int(cam.width)
+    if not check:
+        pass
+    elif mask is not None and tuple(mask.shape) != (H, W):
+        raise ValueError(f"tsplat: mask shape {tuple(mask.shape)} != camera size ({H}, {W})")
+    rows = H * W if not compact else None   # compact: the foreground count (checked by the shapes' agreement)
+    n = depth.numel()
+    if check and ((rows is not None and n != rows) or scale.numel() != 3 * n or opacity.numel() != n or
+                  feat.numel() % max(n, 1) != 0 or (quat is not None and quat.numel() != 4 * n)):
+        raise ValueError("tsplat: source maps do not match the camera size (or each other)")
     v = L.CSrcView()
     v.depth, v.mask, v.scale, v.quat = _ptr(depth), _ptr(mask), _ptr(scale), _ptr(quat)
     v.opacity, v.feat = _ptr(opacity), _ptr(feat)
     if feat_dtype is None:
         feat_dtype = BF16 if feat.dtype == torch.bfloat16 else F32
     v.feat_dtype = feat_dtype
+    v.flags = SRC_COMPACT if compact else 0
     v.cam = ccamera(cam)
     return v
 
 
-def upload_scene(scene, device="cuda", feat_dtype=F32) -> Dict:
+def upload_scene(scene, device="cuda", feat_dtype=F32, compact=False) -> Dict:
     """Copy a gen.Scene's per-view maps to the device (feature maps as FP32,
-    or rounded to BF16 on the host with feat_dtype=BF16)."""
+    or rounded to BF16 on the host with feat_dtype=BF16).  compact=True
+    keeps only the foreground pixels' rows of every map but the mask (pass
+    compact=True to source_view with these)."""
     views = []
     fdt = torch.bfloat16 if feat_dtype == BF16 else torch.float32
     for v in scene.views:
+        fg = np.asarray(v.mask) != 0
+        pick = (lambda a: a[fg]) if compact else (lambda a: a)
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(pick(np.asarray(a))))
         views.append(dict(
-            depth=torch.from_numpy(np.ascontiguousarray(v.depth)).to(device),
+            depth=t(v.depth).to(device),
             mask=torch.from_numpy(np.ascontiguousarray(v.mask)).to(device),
-            scale=torch.from_numpy(np.ascontiguousarray(v.scale)).to(device),
-            quat=torch.from_numpy(np.ascontiguousarray(v.quat)).to(device),
-            opacity=torch.from_numpy(np.ascontiguousarray(v.opacity)).to(device),
-            feat=torch.from_numpy(np.ascontiguousarray(v.feat)).to(fdt).to(device),
+            scale=t(v.scale).to(device),
+            quat=t(v.quat).to(device),
+            opacity=t(v.opacity).to(device),
+            feat=t(v.feat).to(fdt).to(device),
             cam=v.cam))
-    return dict(views=views, C=scene.C, feat_dtype=scene.feat_dtype)
+    return dict(views=views, C=scene.C, feat_dtype=scene.feat_dtype, compact=compact)
 
 
 class Gaussians:

@@ -275,9 +275,12 @@ static tsplat_status build_args(tsplat_gaussians *g, const tsplat_src_view *view
         if (sv.quat && ((uintptr_t)sv.quat & 15)) return fail(TSPLAT_ERR_INVALID_ARG, "view %d: quat not 16-byte aligned", v);
         if ((g->C % 4) == 0 && ((uintptr_t)sv.feat & 15)) return fail(TSPLAT_ERR_INVALID_ARG, "view %d: feat not 16-byte aligned", v);
         if (sv.feat_dtype != TSPLAT_F32 && sv.feat_dtype != TSPLAT_BF16) return fail(TSPLAT_ERR_INVALID_ARG, "view %d: feat_dtype", v);
+        if (sv.flags & ~(int32_t)TSPLAT_SRC_COMPACT) return fail(TSPLAT_ERR_INVALID_ARG, "view %d: unknown flags 0x%x", v, sv.flags);
+        if ((sv.flags & TSPLAT_SRC_COMPACT) && !sv.mask) return fail(TSPLAT_ERR_INVALID_ARG, "view %d: TSPLAT_SRC_COMPACT needs a mask", v);
         ViewDesc &d = a.views[v];
         d.depth = sv.depth; d.mask = sv.mask; d.scale = sv.scale; d.quat = sv.quat; d.opacity = sv.opacity;
-        d.feat = sv.feat; d.feat_dtype = sv.feat_dtype; d.H = H; d.W = W; d.pix_off = total; d.cam = sv.cam;
+        d.feat = sv.feat; d.feat_dtype = sv.feat_dtype; d.compact = (sv.flags & TSPLAT_SRC_COMPACT) != 0;
+        d.H = H; d.W = W; d.cam = sv.cam;
         total += (int64_t)H * W;
     }
     if (total > g->cap) return fail(TSPLAT_ERR_CAPACITY, "build: %lld pixels exceed capacity %lld", (long long)total, (long long)g->cap);
@@ -289,7 +292,7 @@ static tsplat_status build_args(tsplat_gaussians *g, const tsplat_src_view *view
     a.cova = g->cova.as<float4>();
     a.covb = g->covb.as<float2>();
     a.feat = g->feat.p;
-    a.nblocks = (int)((total + BUILD_PIX_PER_BLOCK - 1) / BUILD_PIX_PER_BLOCK);
+    a.nblocks = (int)layout_build_blocks(a);
     TRY(grow(g->blk, (size_t)a.nblocks * 8, s));
     a.blk_cnt = g->blk.as<uint32_t>();
     a.blk_off = a.blk_cnt + a.nblocks;
@@ -723,6 +726,9 @@ tsplat_status tsplat_build_backward(tsplat_gaussians *g, const tsplat_src_view *
     LiftBwdArgs a;
     memset(&a, 0, sizeof(a));
     TRY(build_args(g, views, n_views, a.b, s));
+    for (int v = 0; v < n_views; ++v)
+        if (a.b.views[v].compact)
+            return fail(TSPLAT_ERR_UNSUPPORTED, "build_backward: view %d has compact maps (the gradients are full maps)", v);
     for (int v = 0; v < n_views; ++v) {
         const tsplat_src_grads &gr = grads[v];
         if (!gr.depth || !gr.scale || !gr.opacity || !gr.feat)

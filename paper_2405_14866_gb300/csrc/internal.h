@@ -21,8 +21,9 @@ struct ViewDesc {
     const float *opacity;
     const void *feat;
     int feat_dtype;
+    int compact;      // TSPLAT_SRC_COMPACT: maps hold the foreground pixels only
     int H, W;
-    int64_t pix_off;  // first global pixel index of this view
+    int64_t blk0;     // first lifting block of this view
     tsplat_camera cam;
 };
 
@@ -42,6 +43,16 @@ struct BuildArgs {
     int nblocks;
 };
 constexpr int BUILD_PIX_PER_BLOCK = 1024;
+// Lifting blocks are laid out view by view (no block spans two views):
+// sets each view's first block and returns the block count.
+inline int64_t layout_build_blocks(BuildArgs &a) {
+    int64_t nb = 0;
+    for (int v = 0; v < a.n_views; ++v) {
+        a.views[v].blk0 = nb;
+        nb += ((int64_t)a.views[v].H * a.views[v].W + BUILD_PIX_PER_BLOCK - 1) / BUILD_PIX_PER_BLOCK;
+    }
+    return nb;
+}
 void launch_build(const BuildArgs &a, cudaStream_t s);
 
 // Convert/copy caller arrays into a Gaussian store.

@@ -17,17 +17,19 @@ constexpr int BT = 256;                             // threads per block
 constexpr int BI = BUILD_PIX_PER_BLOCK / BT;        // pixels per thread (4)
 constexpr uint32_t FULL = 0xffffffffu;
 
-__device__ __forceinline__ int view_of(const BuildArgs &a, int64_t g) {
+// Blocks are laid out view by view: view v owns blocks [blk0, blk0 +
+// ceil(H W / 1024)), and block b of it covers the view's pixels
+// [(b - blk0) * 1024, (b - blk0 + 1) * 1024).
+__device__ __forceinline__ int view_of_block(const BuildArgs &a, int64_t b) {
     int v = 0;
     for (int k = 1; k < a.n_views; ++k)
-        if (g >= a.views[k].pix_off) v = k;
+        if (b >= a.views[k].blk0) v = k;
     return v;
 }
 
-__device__ __forceinline__ bool is_fg(const BuildArgs &a, int64_t g) {
-    if (g >= a.total_pix) return false;
-    const ViewDesc &vd = a.views[view_of(a, g)];
-    return vd.mask == nullptr || vd.mask[g - vd.pix_off] != 0;
+__device__ __forceinline__ bool is_fg(const ViewDesc &vd, int64_t p) {
+    if (p >= (int64_t)vd.H * vd.W) return false;
+    return vd.mask == nullptr || vd.mask[p] != 0;
 }
 
 template <int NW>
@@ -63,13 +65,14 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     return m;
 }
 
-// Pixels of block b: [b * 1024, (b + 1) * 1024), visited in 4 rounds of 256
-// consecutive pixels (thread t takes pixel round * 256 + t).
+// Pixels of a block are visited in 4 rounds of 256 consecutive pixels
+// (thread t takes pixel round * 256 + t).
 __global__ __launch_bounds__(BT) void k_build_count(BuildArgs a) {
     __shared__ uint32_t sw[BT / 32];
-    const int64_t base = (int64_t)blockIdx.x * BUILD_PIX_PER_BLOCK + threadIdx.x;
+    const ViewDesc &vd = a.views[view_of_block(a, blockIdx.x)];
+    const int64_t base = ((int64_t)blockIdx.x - vd.blk0) * BUILD_PIX_PER_BLOCK + threadIdx.x;
     uint32_t c = 0;
-    for (int r = 0; r < BI; ++r) c += is_fg(a, base + (int64_t)r * BT) ? 1u : 0u;
+    for (int r = 0; r < BI; ++r) c += is_fg(vd, base + (int64_t)r * BT) ? 1u : 0u;
     uint32_t tot;
     block_excl_scan<BT / 32>(c, sw, tot);
     if (threadIdx.x == 0) a.blk_cnt[blockIdx.x] = tot;
@@ -114,12 +117,13 @@ __device__ __forceinline__ void copy_feat(const void *src, int src_dtype, int64_
     }
 }
 
-// Lift pixel p (row v, column u) of view vd into Gaussian `id`.
-__device__ __forceinline__ void lift_one(const BuildArgs &a, const ViewDesc &vd, int64_t p, int64_t id) {
+// Lift pixel p (row v, column u) of view vd into Gaussian `id`; its maps
+// are read at index k (k = p, or the pixel's foreground rank for compact maps).
+__device__ __forceinline__ void lift_one(const BuildArgs &a, const ViewDesc &vd, int64_t p, int64_t k, int64_t id) {
     const int u = (int)(p % vd.W), v = (int)(p / vd.W);
     const tsplat_camera &cam = vd.cam;
     const float *R = cam.R;
-    const float z = vd.depth[p];
+    const float z = vd.depth[k];
     const float rx = fdiv(fsub((float)u, cam.cx), cam.fx);
     const float ry = fdiv(fsub((float)v, cam.cy), cam.fy);
     const float d0 = fsub(fmul(rx, z), cam.t[0]);
@@ -131,7 +135,7 @@ __device__ __forceinline__ void lift_one(const BuildArgs &a, const ViewDesc &vd,
 
     float w = 1.0f, x = 0.0f, y = 0.0f, zq = 0.0f;
     if (vd.quat) {
-        const float4 q = reinterpret_cast<const float4 *>(vd.quat)[p];
+        const float4 q = reinterpret_cast<const float4 *>(vd.quat)[k];
         w = q.x; x = q.y; y = q.z; zq = q.w;
     }
     const float nn = fadd(fadd(fadd(fmul(w, w), fmul(x, x)), fmul(y, y)), fmul(zq, zq));
@@ -147,7 +151,7 @@ __device__ __forceinline__ void lift_one(const BuildArgs &a, const ViewDesc &vd,
     Rq[2][0] = fmul(2.0f, fsub(fmul(x, zq), fmul(w, y)));
     Rq[2][1] = fmul(2.0f, fadd(fmul(y, zq), fmul(w, x)));
     Rq[2][2] = fsub(1.0f, fmul(2.0f, fadd(fmul(x, x), fmul(y, y))));
-    const float s[3] = {vd.scale[3 * p], vd.scale[3 * p + 1], vd.scale[3 * p + 2]};
+    const float s[3] = {vd.scale[3 * k], vd.scale[3 * k + 1], vd.scale[3 * k + 2]};
     float M[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
@@ -159,23 +163,22 @@ __device__ __forceinline__ void lift_one(const BuildArgs &a, const ViewDesc &vd,
     auto cv = [&](int i, int j) {
         return fadd(fadd(fmul(M[i][0], M[j][0]), fmul(M[i][1], M[j][1])), fmul(M[i][2], M[j][2]));
     };
-    a.xyzo[id] = make_float4(m[0], m[1], m[2], vd.opacity[p]);
+    a.xyzo[id] = make_float4(m[0], m[1], m[2], vd.opacity[k]);
     a.cova[id] = make_float4(cv(0, 0), cv(0, 1), cv(0, 2), cv(1, 1));
     a.covb[id] = make_float2(cv(1, 2), cv(2, 2));
 }
 
-// Copy `rows` feature rows (Gaussian ids first .. first + rows - 1, source
-// pixels s_src[]) cooperatively: consecutive threads take consecutive 4-wide
-// chunks, so both the reads and the writes are coalesced.
-__device__ __forceinline__ void copy_rows(const BuildArgs &a, const int64_t *s_src, int rows, int64_t first) {
+// Copy `rows` feature rows (Gaussian ids first .. first + rows - 1, rows
+// s_src[] of view vd's feature map) cooperatively: consecutive threads take
+// consecutive 4-wide chunks, so both the reads and the writes are coalesced.
+__device__ __forceinline__ void copy_rows(const BuildArgs &a, const ViewDesc &vd, const int64_t *s_src, int rows,
+                                          int64_t first) {
     const int C = a.C;
     const bool vec = (C & 3) == 0;
     const int cpr = vec ? C / 4 : C;  // chunks per row
     for (int ch = threadIdx.x; ch < rows * cpr; ch += BT) {
         const int row = ch / cpr, part = ch - row * cpr;
-        const int64_t g = s_src[row];
-        const ViewDesc &vd = a.views[view_of(a, g)];
-        const int64_t p = g - vd.pix_off, id = first + row;
+        const int64_t p = s_src[row], id = first + row;
         if (vec) {
             const int c0 = part * 4;
             float v[4];
@@ -209,11 +212,14 @@ __global__ __launch_bounds__(BT) void k_build_lift(BuildArgs a) {
     __shared__ uint32_t s_wn[BT / 32];
     __shared__ int64_t s_src[BT];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t base = (int64_t)blockIdx.x * BUILD_PIX_PER_BLOCK;
+    const ViewDesc &vd = a.views[view_of_block(a, blockIdx.x)];
+    const int64_t base = ((int64_t)blockIdx.x - vd.blk0) * BUILD_PIX_PER_BLOCK;
     int64_t running = a.blk_off[blockIdx.x];
+    // compact maps: a foreground pixel's row is its Gaussian id minus the view's first id
+    const int64_t goff = vd.compact ? (int64_t)a.blk_off[vd.blk0] : 0;
     for (int r = 0; r < BI; ++r) {
-        const int64_t g = base + (int64_t)r * BT + threadIdx.x;
-        const bool fg = is_fg(a, g);
+        const int64_t g = base + (int64_t)r * BT + threadIdx.x;  // pixel of the view
+        const bool fg = is_fg(vd, g);
         const uint32_t bal = __ballot_sync(FULL, fg);
         if (lane == 0) s_wn[warp] = __popc(bal);
         __syncthreads();
@@ -226,12 +232,13 @@ __global__ __launch_bounds__(BT) void k_build_lift(BuildArgs a) {
         }
         const uint32_t local = woff + __popc(bal & lanemask_lt());
         if (fg) {
-            const ViewDesc &vd = a.views[view_of(a, g)];
-            lift_one(a, vd, g - vd.pix_off, running + local);
-            s_src[local] = g;
+            const int64_t id = running + local;
+            const int64_t k = vd.compact ? id - goff : g;
+            lift_one(a, vd, g, k, id);
+            s_src[local] = k;
         }
         __syncthreads();
-        copy_rows(a, s_src, (int)tot, running);
+        copy_rows(a, vd, s_src, (int)tot, running);
         running += tot;
         __syncthreads();
     }
@@ -249,12 +256,15 @@ __global__ __launch_bounds__(BT) void k_build_backward(LiftBwdArgs a) {
     __shared__ uint32_t s_wn[BT / 32];
     const BuildArgs &b = a.b;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t base = (int64_t)blockIdx.x * BUILD_PIX_PER_BLOCK;
+    const int vi = view_of_block(b, blockIdx.x);
+    const ViewDesc &vd = b.views[vi];
+    const SrcGrads &out = a.g[vi];
+    const int64_t base = ((int64_t)blockIdx.x - vd.blk0) * BUILD_PIX_PER_BLOCK;
     const int C = b.C;
     int64_t running = b.blk_off[blockIdx.x];
     for (int r = 0; r < BI; ++r) {
-        const int64_t g = base + (int64_t)r * BT + threadIdx.x;
-        const bool fg = is_fg(b, g);
+        const int64_t p = base + (int64_t)r * BT + threadIdx.x;  // pixel of the view
+        const bool fg = is_fg(vd, p);
         const uint32_t bal = __ballot_sync(FULL, fg);
         if (lane == 0) s_wn[warp] = __popc(bal);
         __syncthreads();
@@ -265,11 +275,7 @@ __global__ __launch_bounds__(BT) void k_build_backward(LiftBwdArgs a) {
             woff += w < warp ? c : 0u;
             tot += c;
         }
-        if (g < b.total_pix) {
-            const int vi = view_of(b, g);
-            const ViewDesc &vd = b.views[vi];
-            const SrcGrads &out = a.g[vi];
-            const int64_t p = g - vd.pix_off;
+        if (p < (int64_t)vd.H * vd.W) {
             if (!fg) {
                 out.depth[p] = 0.0f;
                 out.opacity[p] = 0.0f;

@@ -72,9 +72,10 @@ extern "C" tsplat_status tsplat_build_into_noalloc(tsplat_gaussians *g, const ts
         if (!sv.depth || !sv.scale || !sv.opacity || !sv.feat) return record_error(TSPLAT_ERR_INVALID_ARG, "build_into_noalloc: NULL map");
         if (sv.quat && ((uintptr_t)sv.quat & 15)) return record_error(TSPLAT_ERR_INVALID_ARG, "build_into_noalloc: quat not 16-byte aligned");
         if (sv.feat_dtype != TSPLAT_F32 && sv.feat_dtype != TSPLAT_BF16) return record_error(TSPLAT_ERR_INVALID_ARG, "build_into_noalloc: feat_dtype");
+        if (sv.flags != 0) return record_error(TSPLAT_ERR_UNSUPPORTED, "build_into_noalloc: source view flags are not supported here");
         ViewDesc &d = a.views[v];
         d.depth = sv.depth; d.mask = sv.mask; d.scale = sv.scale; d.quat = sv.quat; d.opacity = sv.opacity;
-        d.feat = sv.feat; d.feat_dtype = sv.feat_dtype; d.H = H; d.W = W; d.pix_off = total; d.cam = sv.cam;
+        d.feat = sv.feat; d.feat_dtype = sv.feat_dtype; d.H = H; d.W = W; d.cam = sv.cam;
         total += (int64_t)H * W;
     }
     if (total > NOALLOC_MAX_PIXELS) {
@@ -100,7 +101,9 @@ extern "C" tsplat_status tsplat_build_into_noalloc(tsplat_gaussians *g, const ts
     a.cova = st.cova;
     a.covb = st.covb;
     a.feat = st.feat;
-    a.nblocks = (int)((total + BUILD_PIX_PER_BLOCK - 1) / BUILD_PIX_PER_BLOCK);
+    const int64_t nblocks = layout_build_blocks(a);
+    if (nblocks > NOALLOC_MAX_BLOCKS) return record_error(TSPLAT_ERR_CAPACITY, "build_into_noalloc: too many lifting blocks for the fixed scratch");
+    a.nblocks = (int)nblocks;
     // every entry of the scratch that the kernels read is written earlier in the same call
     a.blk_cnt = scratch;
     a.blk_off = scratch + NOALLOC_MAX_BLOCKS;
