@@ -1,0 +1,105 @@
+"""Edge cases of the render path on the GPU against the oracle.
+
+- Every Gaussian at exactly the same depth: the depth sort has no digit to
+  sort on, so the (tile, depth, id) order is the emission order by id, and
+  the tile sort's stability alone keeps it; and two interleaved depths
+  (heavy ties in one digit pass).  Pairs and ranges bit-exact.
+- Zero covariances (the footprint is the low-pass filter alone).
+- Non-finite depths and scales: culled by the projection as in the oracle.
+- Limits: channel counts outside [1, 64], batches beyond 8 views.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2405_14866_gb300 import _lib as L
+from paper_2405_14866_gb300 import api, gen
+from tests import parity as P
+
+pytestmark = pytest.mark.gpu
+PAR = O.params_array()
+
+
+def _check_bins_and_maps(g32, cam, tol=P.TOL_F32):
+    g = P.gpu_gaussians(g32)
+    ctx = api.Context()
+    F, A = ctx.render(g, cam)
+    torch.cuda.synchronize()
+    pr = O.project_f32(g32, cam, PAR)
+    bins = O.bin_gaussians(pr, cam.width, cam.height)
+    assert ctx.stats()["n_pairs"] == bins.P
+    assert np.array_equal(ctx.export("pairs").cpu().numpy().view(np.uint32), bins.ids)
+    assert np.array_equal(ctx.export("ranges").cpu().numpy().view(np.uint32), bins.ranges)
+    orc = O.render(g32, cam, PAR)
+    P.compare_render(F, A, orc, g32, cam, PAR, tol)
+    return bins
+
+
+@pytest.mark.parametrize("n_depths", [1, 2])
+def test_equal_depths_keep_id_order(n_depths):
+    rng = np.random.default_rng(61)
+    n = 20000 + 123                      # several sort tiles and a ragged tail
+    z = np.where(np.arange(n) % n_depths == 0, 1.5, 1.25).astype(np.float32)
+    mean = np.stack([rng.uniform(-0.6, 0.6, n) * z, rng.uniform(-0.6, 0.6, n) * z, z], 1).astype(np.float32)
+    s = rng.uniform(0.001, 0.006, n).astype(np.float32)
+    cov = np.zeros((n, 6), np.float32)
+    cov[:, 0] = cov[:, 3] = cov[:, 5] = s * s
+    cov[::7] = 0.0                       # zero covariance: the low-pass footprint alone
+    opac = rng.uniform(0.3, 0.95, n).astype(np.float32)
+    feat = rng.standard_normal((n, 4)).astype(np.float32)
+    cam = gen.make_camera(200.0, 256, 240, (0, 0, 0), np.eye(3))
+    bins = _check_bins_and_maps(O.Gaussians(mean, cov, opac, feat), cam)
+    # within each tile the ids ascend per depth run
+    ids, keys = bins.ids.astype(np.int64), bins.keys
+    same = keys[1:] == keys[:-1]
+    assert np.all(ids[1:][same] > ids[:-1][same]) and same.sum() > n
+
+
+def test_nonfinite_maps_are_culled():
+    sc = gen.scene_tiny(seed=62)
+    v = sc.views[0]
+    rng = np.random.default_rng(63)
+    H, W = v.depth.shape
+    idx = rng.choice(H * W, 300, replace=False)
+    d = v.depth.reshape(-1).copy()
+    d[idx[:100]] = np.nan
+    d[idx[100:150]] = np.inf
+    sc_ = v.scale.reshape(-1, 3).copy()
+    sc_[idx[150:250], 1] = np.nan
+    sc_[idx[250:], 0] = np.inf
+    v.depth = d.reshape(H, W)
+    v.scale = sc_.reshape(H, W, 3)
+    g, keep = P.gpu_build(sc)
+    g32 = O.lift_scene(sc, "f32")
+    cam = sc.targets[0]
+    ctx = api.Context()
+    F, A = ctx.render(g, cam)
+    torch.cuda.synchronize()
+    pr = O.project_f32(g32, cam, PAR)
+    bins = O.bin_gaussians(pr, cam.width, cam.height)
+    assert ctx.stats()["n_pairs"] == bins.P
+    assert ctx.stats()["n_visible"] == int((pr.ntiles > 0).sum()) <= H * W - 300
+    assert np.array_equal(ctx.export("pairs").cpu().numpy().view(np.uint32), bins.ids)
+    assert torch.isfinite(F).all() and torch.isfinite(A).all()
+    orc = O.render(g32, cam, PAR)
+    P.compare_render(F, A, orc, g32, cam, PAR, P.TOL_F32)
+
+
+def test_limits_are_rejected():
+    for C in (0, 65):
+        with pytest.raises(L.TsplatError) as e:
+            api.Gaussians.create(16, C)
+        assert e.value.status == 1
+    gs = gen.random_gaussians(64, 500, 4, center=(0, 0, 1.5), spread=0.3)
+    g = P.gpu_gaussians(O.Gaussians(gs.mean, gs.cov, gs.opac, gs.feat))
+    cams = [gen.make_camera(60.0, 48 + 8 * k, 40, (0.01 * k, 0, 0), np.eye(3)) for k in range(9)]
+    Fs, As = api.Context().render_batch(g, cams[:8])       # the largest batch
+    torch.cuda.synchronize()
+    for cam, F in zip(cams[:8], Fs):
+        F1, _ = api.Context().render(g, cam)
+        torch.cuda.synchronize()
+        assert torch.equal(F, F1)
+    with pytest.raises(L.TsplatError) as e:
+        api.Context().render_batch(g, cams)
+    assert e.value.status == 1
