@@ -81,13 +81,6 @@ void release(DBuf &b) {
 
 size_t feat_size(int dtype) { return dtype == TSPLAT_BF16 ? 2 : 4; }
 
-int tile_digits(int n_tiles) {  // radix passes over tile ids 0..n_tiles-1
-    if (n_tiles <= 1) return 0;
-    int bits = 0;
-    while ((1u << bits) < (uint32_t)n_tiles) ++bits;
-    return (bits + 7) / 8;
-}
-
 }  // namespace
 
 namespace tsp {
@@ -106,9 +99,9 @@ struct tsplat_gaussians {
 
 struct tsplat_ctx {
     // N-sized
-    DBuf hdr, rect, ntiles, tmask, dkey, radius, skeys0, skeys1, svals0, svals1, hist_n, emit_blk;
+    DBuf hdr, rect, ntiles, tmask, dkey, radius;
     // P-sized
-    DBuf pk0, pk1, pv0, pv1, hist_p;
+    DBuf pk0, pk1, pv0, pv1, tcnt;
     // tiles / pixels / view table
     DBuf ranges, tfinal, last, views;
     DBuf zkeys;  // point z-buffer scratch
@@ -138,8 +131,8 @@ struct tsplat_ctx {
 };
 
 namespace {
-enum { SM_KMIN = 0, SM_KMAX = 1, SM_NVIS = 2, SM_NPASS = 3, SM_P = 4, SM_PEFF = 5, SM_STATUS = 6, SM_TILECTR = 7,
-       SM_N = 8, SM_NINST = 9, SM_SORTCTR = 10 /* 4 words */, SM_BWDCTR = 14, SM_TOTALS = 16, SM_WORDS = 16 + 4 * 256 };
+enum { SM_KMIN = 0, SM_KMAX = 1, SM_NVIS = 2, SM_P = 4, SM_PEFF = 5, SM_STATUS = 6, SM_TILECTR = 7,
+       SM_N = 8, SM_NINST = 9, SM_BINCTR = 10, SM_BWDCTR = 14, SM_WORDS = 16 };
 uint32_t *small_ptr(tsplat_ctx *c, int w) { return c->small.as<uint32_t>() + w; }
 }  // namespace
 
@@ -338,6 +331,7 @@ tsplat_status tsplat_ctx_create(tsplat_ctx **out) {
     if (st == TSPLAT_OK && cudaMallocHost(&c->host_small, SM_WORDS * 4) != cudaSuccess) st = fail(TSPLAT_ERR_OOM, "pinned allocation failed");
     if (st == TSPLAT_OK && (cudaMemset(c->small.p, 0, SM_WORDS * 4) != cudaSuccess)) st = fail(TSPLAT_ERR_CUDA, "memset");
     if (st == TSPLAT_OK && cudaStreamSynchronize(nullptr) != cudaSuccess) st = fail(TSPLAT_ERR_CUDA, "sync");
+    if (st == TSPLAT_OK) bin_sort_setup();
     if (st != TSPLAT_OK) {
         tsplat_ctx_destroy(c);
         return st;
@@ -349,8 +343,8 @@ tsplat_status tsplat_ctx_create(tsplat_ctx **out) {
 tsplat_status tsplat_ctx_destroy(tsplat_ctx *c) {
     if (!c) return TSPLAT_OK;
     cudaDeviceSynchronize();
-    DBuf *bufs[] = {&c->hdr, &c->rect, &c->ntiles, &c->tmask, &c->dkey, &c->radius, &c->skeys0, &c->skeys1, &c->svals0,
-                    &c->svals1, &c->hist_n, &c->emit_blk, &c->pk0, &c->pk1, &c->pv0, &c->pv1, &c->hist_p,
+    DBuf *bufs[] = {&c->hdr, &c->rect, &c->ntiles, &c->tmask, &c->dkey, &c->radius, &c->pk0, &c->pk1, &c->pv0,
+                    &c->pv1, &c->tcnt,
                     &c->ranges, &c->tfinal, &c->last, &c->views, &c->zkeys, &c->torder, &c->small};
     for (DBuf *b : bufs) release(*b);
     for (auto &row : c->ev)
@@ -363,39 +357,45 @@ tsplat_status tsplat_ctx_destroy(tsplat_ctx *c) {
 
 static tsplat_status ensure_n(tsplat_ctx *c, int64_t n, cudaStream_t s) {
     const size_t N = (size_t)std::max<int64_t>(n, 1);
-    const size_t nb = (N + RS_TILE - 1) / RS_TILE;
     TRY(grow(c->hdr, N * sizeof(Header), s));
     TRY(grow(c->rect, N * 8, s));
     TRY(grow(c->ntiles, N * 4, s));
     TRY(grow(c->tmask, N * 4, s));
     TRY(grow(c->dkey, N * 4, s));
     TRY(grow(c->radius, N * 4, s));
-    TRY(grow(c->skeys0, N * 4, s));
-    TRY(grow(c->skeys1, N * 4, s));
-    TRY(grow(c->svals0, N * 4, s));
-    TRY(grow(c->svals1, N * 4, s));
-    TRY(grow(c->hist_n, nb * 256 * 4 * RS_MAX_PASSES, s));
-    TRY(grow(c->emit_blk, nb * 4, s));
     return TSPLAT_OK;
 }
 
 static tsplat_status ensure_p(tsplat_ctx *c, int64_t p, cudaStream_t s) {
     if (p <= c->p_cap && c->pk0.p) return TSPLAT_OK;
-    const int64_t cap = std::max<int64_t>(p + p / 8, 4096);
-    const size_t nb = (size_t)((cap + RS_TILE - 1) / RS_TILE);
+    const int64_t cap = std::min<int64_t>(std::max<int64_t>(p + p / 8, 4096), 0xfffffffell);
+    if (p > cap) return fail(TSPLAT_ERR_CAPACITY, "render: %lld pairs exceed the 32-bit pair index", (long long)p);
     TRY(grow(c->pk0, (size_t)cap * 4, s));
     TRY(grow(c->pk1, (size_t)cap * 4, s));
     TRY(grow(c->pv0, (size_t)cap * 4, s));
     TRY(grow(c->pv1, (size_t)cap * 4, s));
-    TRY(grow(c->hist_p, nb * 256 * 4 * RS_MAX_PASSES, s));
     c->p_cap = cap;
     return TSPLAT_OK;
 }
 
-static tsplat_status ensure_pix(tsplat_ctx *c, int W, int H, int n_tiles, bool save, cudaStream_t s) {
-    TRY(grow(c->ranges, (size_t)std::max(n_tiles, 1) * 8, s));
-    TRY(grow(c->torder, (size_t)std::max(n_tiles, 1) * 4, s));
+// Per-tile buffers of a render over n_tiles tile slots (all views of a batch).
+static tsplat_status ensure_tiles(tsplat_ctx *c, int64_t n_tiles, cudaStream_t s) {
+    const size_t T = (size_t)std::max<int64_t>(n_tiles, 1);
+    TRY(grow(c->ranges, T * 8, s));
+    TRY(grow(c->torder, T * 4, s));
+    TRY(grow(c->tcnt, T * 8, s));  // counts, then fill cursors
     TRY(grow(c->views, sizeof(RenderView) * MAX_BATCH, s));
+    return TSPLAT_OK;
+}
+
+static bool tiles_fit(const tsplat_ctx *c, int64_t n_tiles) {
+    const size_t T = (size_t)std::max<int64_t>(n_tiles, 1);
+    return c->ranges.bytes >= T * 8 && c->torder.bytes >= T * 4 && c->tcnt.bytes >= T * 8 &&
+           c->views.bytes >= sizeof(RenderView) * MAX_BATCH;
+}
+
+static tsplat_status ensure_pix(tsplat_ctx *c, int W, int H, int n_tiles, bool save, cudaStream_t s) {
+    TRY(ensure_tiles(c, n_tiles, s));
     if (save) {
         TRY(grow(c->tfinal, (size_t)W * H * 4, s));
         TRY(grow(c->last, (size_t)W * H * 4, s));
@@ -439,6 +439,7 @@ static tsplat_status render_tail(tsplat_ctx *c, int64_t n_cap, const uint32_t *n
     const bool save = (par.flags & TSPLAT_RENDER_SAVE) != 0;
     const bool prof = (par.flags & TSPLAT_RENDER_PROFILE) != 0;
     uint32_t *sm = c->small.as<uint32_t>();
+    if (!tiles_fit(c, n_tiles)) return fail(TSPLAT_ERR_CAPACITY, "render: the context holds fewer than %d tile slots", n_tiles);
     const int64_t inst_cap = n_cap * vb.n_views;
     const uint32_t *n_inst = n_dev;
     if (vb.n_views > 1) {
@@ -447,46 +448,30 @@ static tsplat_status render_tail(tsplat_ctx *c, int64_t n_cap, const uint32_t *n
     }
     TRY(mark(c, prof, 1, s));
 
-    // depth order of the Gaussians (radix passes only over the differing bytes)
-    launch_depth_npass(sm + SM_KMIN, sm + SM_NPASS, s);
-    RadixSort ds;
-    memset(&ds, 0, sizeof(ds));
-    ds.keys_in = c->dkey.as<uint32_t>();
-    ds.vals_in = nullptr;
-    ds.keys[0] = c->skeys0.as<uint32_t>();
-    ds.keys[1] = c->skeys1.as<uint32_t>();
-    ds.vals[0] = c->svals0.as<uint32_t>();
-    ds.vals[1] = c->svals1.as<uint32_t>();
-    ds.n_dev = n_inst;
-    ds.npass_dev = sm + SM_NPASS;
-    ds.kmin = sm + SM_KMIN;
-    ds.status = c->hist_n.as<uint32_t>();
-    ds.tile_ctr = sm + SM_SORTCTR;
-    ds.err = sm + SM_STATUS;
-    ds.totals = sm + SM_TOTALS;
-    ds.nblocks = (int)((std::max<int64_t>(inst_cap, 1) + RS_TILE - 1) / RS_TILE);
-    launch_radix_sort(ds, 4, s);
+    // (tile, depth, id) order of the pairs through per-tile buckets
+    BinArgs bn;
+    memset(&bn, 0, sizeof(bn));
+    bn.n_inst = n_inst;
+    bn.n_stride = n_dev;
+    bn.inst_cap = inst_cap;
+    bn.ntiles = c->ntiles.as<uint32_t>();
+    bn.rect = c->rect.as<uint2>();
+    bn.tmask = (par.flags & TSPLAT_RENDER_TIGHT) ? c->tmask.as<uint32_t>() : nullptr;
+    bn.dkey = c->dkey.as<uint32_t>();
+    bn.views = c->views.as<RenderView>();
+    bn.n_views = vb.n_views;
+    bn.n_slots = (uint32_t)n_tiles;
+    bn.tile_cnt = c->tcnt.as<uint32_t>();
+    bn.cursor = bn.tile_cnt + std::max(n_tiles, 1);
+    bn.ranges = c->ranges.as<uint2>();
+    bn.p_dev = sm + SM_P;
+    bn.p_eff = sm + SM_PEFF;
+    bn.tile_order = c->torder.as<uint32_t>();
+    bn.tile_ctr = sm + SM_BINCTR;
+    bn.status = sm + SM_STATUS;
+    launch_bin_count(bn, s);
+    TRY(check_launch("render: count"));
     TRY(mark(c, prof, 2, s));
-
-    // scan of tiles per Gaussian in depth order and pair emission
-    EmitArgs em;
-    memset(&em, 0, sizeof(em));
-    em.order.vals_in = nullptr;
-    em.order.vals[0] = ds.vals[0];
-    em.order.vals[1] = ds.vals[1];
-    em.order.npass_dev = sm + SM_NPASS;
-    em.n_dev = n_inst;
-    em.n_cap = inst_cap;
-    em.ntiles = c->ntiles.as<uint32_t>();
-    em.rect = c->rect.as<uint2>();
-    em.tmask = (par.flags & TSPLAT_RENDER_TIGHT) ? c->tmask.as<uint32_t>() : nullptr;
-    em.views = c->views.as<RenderView>();
-    em.n_stride = n_dev;
-    em.blk_sum = c->emit_blk.as<uint32_t>();
-    em.p_dev = sm + SM_P;
-    em.status = sm + SM_STATUS;
-    launch_emit_count(em, s);
-    TRY(check_launch("render: sort/count"));
 
     if (!async_mode) {
         TRY_CUDA(cudaMemcpyAsync(c->host_small + SM_P, sm + SM_P, 4, cudaMemcpyDeviceToHost, s));
@@ -495,42 +480,20 @@ static tsplat_status render_tail(tsplat_ctx *c, int64_t n_cap, const uint32_t *n
     } else if (!c->pk0.p) {
         return fail(TSPLAT_ERR_CAPACITY, "render: TSPLAT_RENDER_ASYNC needs tsplat_ctx_reserve first");
     }
-    em.pair_tile = c->pk1.as<uint32_t>();
-    em.pair_id = c->pv1.as<uint32_t>();
-    em.p_cap = c->p_cap;
-    launch_emit_write(em, s);
+    bn.p_cap = c->p_cap;
+    bn.bk_key = c->pk0.as<uint32_t>();
+    bn.bk_id = c->pv0.as<uint32_t>();
+    bn.tmp_key = c->pk1.as<uint32_t>();
+    bn.tmp_id = c->pv1.as<uint32_t>();
+    bn.ids_out = c->pv1.as<uint32_t>();  // the scratch of a bucket ends before its output is written
+    launch_bin_fill(bn, s);
     TRY(mark(c, prof, 3, s));
-
-    // stable sort of the pairs on the tile digits; the emit buffer is the
-    // odd ping-pong buffer, so two passes end where they started
-    const int tpass = tile_digits(n_tiles);
-    RadixSort ts;
-    memset(&ts, 0, sizeof(ts));
-    ts.keys_in = c->pk1.as<uint32_t>();
-    ts.vals_in = c->pv1.as<uint32_t>();
-    ts.keys[0] = c->pk0.as<uint32_t>();
-    ts.keys[1] = c->pk1.as<uint32_t>();
-    ts.vals[0] = c->pv0.as<uint32_t>();
-    ts.vals[1] = c->pv1.as<uint32_t>();
-    ts.n_dev = sm + SM_PEFF;
-    ts.npass_dev = nullptr;
-    ts.npass_host = tpass;
-    ts.kmin = nullptr;
-    ts.status = c->hist_p.as<uint32_t>();
-    ts.tile_ctr = sm + SM_SORTCTR;
-    ts.err = sm + SM_STATUS;
-    ts.totals = sm + SM_TOTALS;
-    ts.nblocks = (int)((c->p_cap + RS_TILE - 1) / RS_TILE);
-    // effective pair count: P, or 0 when the pairs did not fit
-    launch_pairs_effective(sm + SM_P, (uint32_t)std::min<int64_t>(c->p_cap, 0xffffffffll), sm + SM_PEFF, s);
-    if (tpass > 0) launch_radix_sort(ts, tpass, s);
-    TRY(mark(c, prof, 4, s));
-    const uint32_t *tiles_sorted = tpass == 0 ? ts.keys_in : ts.keys[(tpass - 1) & 1];
-    const uint32_t *ids_sorted = tpass == 0 ? ts.vals_in : ts.vals[(tpass - 1) & 1];
-    launch_ranges(tiles_sorted, sm + SM_PEFF, c->p_cap, c->ranges.as<uint2>(), n_tiles, s);
     launch_tile_order(c->ranges.as<uint2>(), c->views.as<RenderView>(), vb.n_views, n_tiles, c->torder.as<uint32_t>(), s);
+    TRY(mark(c, prof, 4, s));
+    launch_bin_sort(bn, s);
     TRY(check_launch("render: bins"));
     TRY(mark(c, prof, 5, s));
+    const uint32_t *ids_sorted = bn.ids_out;
 
     CompositeArgs ca;
     memset(&ca, 0, sizeof(ca));
@@ -611,7 +574,7 @@ static ProjectOut project_out(tsplat_ctx *c) {
 static void init_small(tsplat_ctx *c, cudaStream_t s) {
     uint32_t *sm = c->small.as<uint32_t>();
     launch_fill_u32(sm + SM_KMIN, CULLED_KEY, 1, s);
-    cudaMemsetAsync(sm + SM_KMAX, 0, sizeof(uint32_t) * 7, s);  // kmax, n_vis, npass, P, P_eff, status, tile counter
+    cudaMemsetAsync(sm + SM_KMAX, 0, sizeof(uint32_t) * 7, s);  // kmax, n_vis, (unused), P, P_eff, status, tile counter
 }
 
 tsplat_status tsplat_render(const tsplat_gaussians *g, const tsplat_camera *cam, const tsplat_render_params *params,
@@ -624,7 +587,7 @@ tsplat_status tsplat_render(const tsplat_gaussians *g, const tsplat_camera *cam,
     const bool async_mode = (params->flags & TSPLAT_RENDER_ASYNC) != 0;
     if (async_mode) {
         if (ctx->hdr.bytes < (size_t)std::max<int64_t>(g->cap, 1) * sizeof(Header) ||
-            ctx->ranges.bytes < (size_t)tiles_x * tiles_y * 8 ||
+            !tiles_fit(ctx, (int64_t)tiles_x * tiles_y) ||
             ((params->flags & TSPLAT_RENDER_SAVE) && ctx->tfinal.bytes < (size_t)W * H * 4))
             return fail(TSPLAT_ERR_CAPACITY, "render: TSPLAT_RENDER_ASYNC needs tsplat_ctx_reserve for these sizes");
     } else {
@@ -685,7 +648,7 @@ tsplat_status render_batch_impl(const tsplat_gaussians *g, const tsplat_camera *
     cudaStream_t s = S(stream);
     const int64_t inst = std::max<int64_t>(g->cap, 1) * n_views;
     if (params->flags & TSPLAT_RENDER_ASYNC) {
-        if (ctx->hdr.bytes < (size_t)inst * sizeof(Header) || ctx->ranges.bytes < (size_t)tiles * 8)
+        if (ctx->hdr.bytes < (size_t)inst * sizeof(Header) || !tiles_fit(ctx, tiles))
             return fail(TSPLAT_ERR_CAPACITY, "render_batch: TSPLAT_RENDER_ASYNC needs tsplat_ctx_reserve for these sizes");
     } else {
         TRY(ensure_n(ctx, inst, s));
@@ -774,7 +737,7 @@ tsplat_status tsplat_rasterize(int64_t n, const float *mean2d, const float *coni
     const int tiles_x = (width + TILE - 1) / TILE, tiles_y = (height + TILE - 1) / TILE;
     const bool async_mode = (params->flags & TSPLAT_RENDER_ASYNC) != 0;
     if (async_mode) {
-        if (ctx->hdr.bytes < (size_t)std::max<int64_t>(n, 1) * sizeof(Header) || ctx->ranges.bytes < (size_t)tiles_x * tiles_y * 8)
+        if (ctx->hdr.bytes < (size_t)std::max<int64_t>(n, 1) * sizeof(Header) || !tiles_fit(ctx, (int64_t)tiles_x * tiles_y))
             return fail(TSPLAT_ERR_CAPACITY, "rasterize: TSPLAT_RENDER_ASYNC needs tsplat_ctx_reserve for these sizes");
     } else {
         TRY(ensure_n(ctx, n, s));
@@ -872,7 +835,7 @@ tsplat_status tsplat_ctx_status(tsplat_ctx *c) {
 tsplat_status tsplat_ctx_stats_get(tsplat_ctx *c, tsplat_ctx_stats *out) {
     if (!c || !out) return fail(TSPLAT_ERR_INVALID_ARG, "ctx_stats: NULL argument");
     TRY_CUDA(cudaStreamSynchronize(c->stream));
-    uint32_t w[SM_TOTALS];
+    uint32_t w[SM_WORDS];
     TRY_CUDA(cudaMemcpy(w, c->small.p, sizeof(w), cudaMemcpyDeviceToHost));
     uint32_t n = 0;
     if (c->n_dev) TRY_CUDA(cudaMemcpy(&n, c->n_dev, 4, cudaMemcpyDeviceToHost));
@@ -934,9 +897,7 @@ namespace tsp {
 tsplat_status ctx_reserve_batch(tsplat_ctx *c, int64_t instances, int64_t pairs, int64_t tiles) {
     TRY(ensure_n(c, instances, nullptr));
     TRY(ensure_p(c, pairs, nullptr));
-    TRY(grow(c->ranges, (size_t)std::max<int64_t>(tiles, 1) * 8, nullptr));
-    TRY(grow(c->torder, (size_t)std::max<int64_t>(tiles, 1) * 4, nullptr));
-    TRY(grow(c->views, sizeof(RenderView) * MAX_BATCH, nullptr));
+    TRY(ensure_tiles(c, tiles, nullptr));
     TRY_CUDA(cudaStreamSynchronize(nullptr));
     return TSPLAT_OK;
 }

@@ -110,74 +110,43 @@ void launch_prepare_2d(int64_t n, const float *mean2d, const float *conic, const
                        const float *depth, const int32_t *radius, const tsplat_render_params &par,
                        const ViewBatch &vb, RenderView *views_dev, const ProjectOut &o, cudaStream_t s);
 
-// ------------------------------------------------------ A3..A6 sort / bins
-constexpr int RS_THREADS = 256;
-constexpr int RS_ITEMS = 16;
-constexpr int RS_TILE = RS_THREADS * RS_ITEMS;  // keys per radix block
-
-// Stable LSD radix sort of (u32 key, u32 value) pairs, 8-bit digits.
-// Pass p reads pass p-1's output (pass 0 reads keys_in / vals_in, vals_in
-// NULL meaning 0..n-1, and maps key k to k - *kmin, CULLED_KEY to 0, when
-// kmin is given) and writes keys[p & 1] / vals[p & 1].  The number of
-// passes is *npass_dev when given, else npass_host; passes beyond it do
-// nothing, so the result lives in buffer (npass-1) & 1, or is the input
-// when npass is 0.  One histogram launch counts the digits of every pass;
-// then each pass is one launch in which blocks take key tiles in order from
-// a counter and obtain each digit's global offset by looking back over the
-// earlier tiles' published counts (bounded waits; a wait that expires sets
-// TSPLAT_ERR_TIMEOUT in *err).  Launch cost does not depend on n_cap.
-constexpr int RS_MAX_PASSES = 4;
-struct RadixSort {
-    const uint32_t *keys_in;
-    const uint32_t *vals_in;
-    uint32_t *keys[2];
-    uint32_t *vals[2];
-    const uint32_t *n_dev;
-    const uint32_t *npass_dev;
-    int npass_host;
-    const uint32_t *kmin;
-    uint32_t *status;    // [RS_MAX_PASSES][nblocks][256] look-back words
-    uint32_t *totals;    // [RS_MAX_PASSES][256], zeroed by the launcher
-    uint32_t *tile_ctr;  // [RS_MAX_PASSES] tile tickets, zeroed by the histogram launch
-    uint32_t *err;       // status word
-    int nblocks;         // ceil(n_cap / RS_TILE)
+// ------------------------------------------------------ A3..A6 bins
+// The (Gaussian, tile) pairs of a render in (tile, depth key, instance id)
+// order, and each tile's [first, last) range, through tile buckets (see
+// k_bin.cu).  Instances: view v's copy of Gaussian g is instance v N + g.
+struct BinArgs {
+    const uint32_t *n_inst;      // instances (device)
+    const uint32_t *n_stride;    // N (device)
+    int64_t inst_cap;            // bound of the instance count (grid sizing)
+    const uint32_t *ntiles;      // [inst] kept tiles per instance (0: culled)
+    const uint2 *rect;           // [inst] packed tile rects
+    const uint32_t *tmask;       // [inst] tight-binning masks, or nullptr
+    const uint32_t *dkey;        // [inst] depth keys
+    const RenderView *views;     // device view table
+    int n_views;
+    uint32_t n_slots;            // tile slots of the launch (>= the views' tiles)
+    uint32_t *tile_cnt;          // [n_slots] per-tile pair counts
+    uint32_t *cursor;            // [n_slots] fill cursors
+    uint2 *ranges;               // [n_slots] output
+    uint32_t *p_dev;             // P (written by the scan)
+    uint32_t *p_eff;             // P, or 0 when the pairs do not fit (written by the fill)
+    int64_t p_cap;               // pair buffer capacity
+    uint32_t *bk_key, *bk_id;    // [p_cap] buckets: depth keys, instance ids
+    uint32_t *tmp_key, *tmp_id;  // [p_cap] scratch of buckets too large for shared memory
+    uint32_t *ids_out;           // [p_cap] instance ids in (tile, depth, id) order
+    const uint32_t *tile_order;  // [n_slots]
+    uint32_t *tile_ctr;          // persistent-sort tile counter
+    uint32_t *status;            // TSPLAT_ERR_CAPACITY when P > p_cap
 };
-void launch_radix_sort(const RadixSort &rs, int max_passes, cudaStream_t s);
-void launch_depth_npass(const uint32_t *kminmax, uint32_t *npass, cudaStream_t s);
-
-// Where a sort left its values: buffer (npass - 1) & 1, or the input.
-struct SortedVals {
-    const uint32_t *vals_in;  // NULL = identity
-    const uint32_t *vals[2];
-    const uint32_t *npass_dev;
-    int npass_host;
-};
-
-// A3/A4: exclusive scan of n_tiles in depth order and emission of
-// (tile, Gaussian id) pairs.  Two launches: reduce (+ total P), then
-// scan + emit.  P_cap bounds the emission; overflow sets TSPLAT_ERR_CAPACITY.
-struct EmitArgs {
-    SortedVals order;          // depth order (values = Gaussian ids)
-    const uint32_t *n_dev;
-    int64_t n_cap;
-    const uint32_t *ntiles;
-    const uint2 *rect;
-    const uint32_t *tmask;     // kept-tile masks, or nullptr (whole rects)
-    const RenderView *views;   // instance i belongs to view i / N
-    const uint32_t *n_stride;  // N (device)
-    uint32_t *blk_sum;         // [nblocks]
-    uint32_t *p_dev;           // total pairs (output)
-    uint32_t *pair_tile;       // [P_cap]
-    uint32_t *pair_id;         // [P_cap]
-    int64_t p_cap;
-    uint32_t *status;
-};
-void launch_emit_count(const EmitArgs &a, cudaStream_t s);
-void launch_emit_write(const EmitArgs &a, cudaStream_t s);
-
-// A6: per-tile [first, last) of the tile-sorted pairs (ranges zeroed first).
-void launch_ranges(const uint32_t *tiles_sorted, const uint32_t *p_dev, int64_t p_cap, uint2 *ranges,
-                   int n_tiles, cudaStream_t s);
+// Per-tile counts, then ranges, cursors and P (two launches).
+void launch_bin_count(const BinArgs &a, cudaStream_t s);
+// Buckets filled with (depth key, id); P > p_cap: nothing written, empty ranges.
+void launch_bin_fill(const BinArgs &a, cudaStream_t s);
+// Each bucket sorted by (depth key, id) into ids_out (tiles in tile_order).
+void launch_bin_sort(const BinArgs &a, cudaStream_t s);
+// One-time kernel attributes of the bucket sort (called outside any stream
+// capture, when a context is created); returns its grid.
+int bin_sort_setup();
 
 // ------------------------------------------------------------ A7 composite
 struct CompositeArgs {
@@ -298,8 +267,6 @@ void launch_tile_order(const uint2 *ranges, const RenderView *views, int n_views
 // small utilities
 void launch_fill_u32(uint32_t *p, uint32_t v, int64_t n, cudaStream_t s);
 void launch_scale_u32(const uint32_t *src, uint32_t k, uint32_t *dst, cudaStream_t s);  // *dst = *src * k
-// *dst = *src if it fits in cap, else 0 (an overflowing render emits no pairs)
-void launch_pairs_effective(const uint32_t *src, uint32_t cap, uint32_t *dst, cudaStream_t s);
 void launch_zero_f32_n(float *p, const uint32_t *n_dev, int mult, int64_t n_cap, cudaStream_t s);  // p[0 .. n*mult)
 void launch_export_rect(const uint2 *rect, const uint32_t *n_dev, int64_t n_cap, int32_t *dst, cudaStream_t s);
 void launch_export_header(const Header *hdr, const uint32_t *n_dev, int64_t n_cap, int what, void *dst,

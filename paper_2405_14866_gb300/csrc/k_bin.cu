@@ -1,0 +1,602 @@
+// A3..A6: the (Gaussian, tile) pairs of a render ordered by (tile, depth,
+// id) -- the order the cited 3DGS rasterizer (Tele-Aloha Sec. 4.2) gets from
+// one stable sort of the 64-bit keys tile << 32 | bits(depth) over pairs
+// emitted in Gaussian-id order -- and each tile's [first, last) range.
+//
+// Built from tile buckets instead of device-wide sorts:
+//   1. k_bin_walk<false>  every instance, in id order, walks its kept tiles;
+//                         lanes of a warp that meet the same tile add their
+//                         count with one atomic (match_any);
+//   2. k_bin_scan         one block: exclusive scan of the tile counts: each
+//                         tile's range and fill cursor, and the total P;
+//   3. k_bin_walk<true>   the same walk; each (warp, tile) group reserves a run
+//                         of its tile's bucket with one atomic and writes
+//                         (depth key, instance id) into it;
+//   4. k_tile_order       tiles longest list first;
+//   5. k_bin_sort         persistent blocks take tiles in that order and sort
+//                         each bucket by (depth key, id): an LSD radix sort
+//                         with 8-bit digits over the bits in which the tile's
+//                         depth keys differ, then runs of equal depth keys
+//                         put in id order (runs longer than 32: id digits,
+//                         then depth digits again); in shared memory, or for
+//                         buckets larger than it, by the same passes over
+//                         global memory.
+// A bucket's order after step 3 depends on the atomics; after step 5 it does
+// not: (depth key, id) is unique within a tile.
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace tsp {
+
+namespace {
+
+constexpr uint32_t FULL = 0xffffffffu;
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Exclusive scan across a block of NW warps; `sw` holds NW words.
+template <int NW, typename T>
+__device__ __forceinline__ T block_excl_scan(T v, T *sw, T &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const T y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sw[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        T w = lane < NW ? sw[lane] : T(0);
+#pragma unroll
+        for (int o = 1; o < NW; o <<= 1) {
+            const T y = __shfl_up_sync(FULL, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < NW) sw[lane] = w;
+    }
+    __syncthreads();
+    total = sw[NW - 1];
+    const T pre = warp ? sw[warp - 1] : T(0);
+    __syncthreads();
+    return pre + x - v;
+}
+
+// The kept tiles of one instance, in row-major order of its rect: the whole
+// rect, or the set bits of its tight-binning mask.
+struct TileWalk {
+    uint32_t row0;  // global id of tile (0, y0) of the rect's view
+    int tiles_x, x0, w;
+    uint32_t rest;  // masked: kept tiles not visited yet (bit = index in the rect)
+    uint32_t inv_w; // masked: ceil(2^16 / w); loc * inv_w >> 16 = loc / w for loc < 32
+    int lx, ly;     // whole rect: the next tile
+    bool masked;
+    __device__ __forceinline__ uint32_t next() {
+        int x, y;
+        if (masked) {
+            const int loc = __ffs(rest) - 1;
+            rest &= rest - 1u;
+            y = (int)(((uint32_t)loc * inv_w) >> 16);
+            x = loc - y * w;
+        } else {
+            x = lx;
+            y = ly;
+            if (++lx == w) {
+                lx = 0;
+                ++ly;
+            }
+        }
+        return row0 + (uint32_t)(y * tiles_x + x0 + x);
+    }
+};
+
+// Steps 1 and 3.  Warps stride over 32-instance chunks in id order; the loop
+// over a chunk's tiles runs to the chunk's largest count, lanes past their
+// own count sitting out.
+template <bool FILL>
+__global__ __launch_bounds__(256) void k_bin_walk(BinArgs a) {
+    const uint32_t n = *a.n_inst;
+    if (FILL && blockIdx.x == 0 && threadIdx.x == 0) *a.p_eff = *a.p_dev <= a.p_cap ? *a.p_dev : 0u;
+    if (FILL && *a.p_dev > a.p_cap) {
+        // the pairs do not fit: nothing is written and every tile is empty
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_status(a.status, TSPLAT_ERR_CAPACITY);
+        for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < a.n_slots; t += gridDim.x * blockDim.x)
+            a.ranges[t] = make_uint2(0u, 0u);
+        return;
+    }
+    const uint32_t ns = *a.n_stride;
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = lanemask_lt();
+    const uint64_t wstride = (uint64_t)gridDim.x * (blockDim.x >> 5) * 32;
+    for (uint64_t c0 = ((uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; c0 < n; c0 += wstride) {
+        const uint64_t i = c0 + lane;
+        uint32_t cnt = 0, key = 0;
+        TileWalk tw;
+        tw.row0 = 0; tw.tiles_x = 1; tw.x0 = 0; tw.w = 1; tw.rest = 0; tw.inv_w = 0; tw.lx = 0; tw.ly = 0;
+        tw.masked = false;
+        if (i < n) {
+            cnt = a.ntiles[i];
+            if (cnt) {
+                int x0, y0, x1, y1;
+                unpack_rect(a.rect[i], x0, y0, x1, y1);
+                const RenderView &vw = a.views[a.n_views > 1 ? (uint32_t)(i / ns) : 0u];
+                tw.tiles_x = vw.tiles_x;
+                tw.x0 = x0;
+                tw.w = x1 - x0;
+                tw.row0 = vw.tile_base + (uint32_t)(y0 * vw.tiles_x);
+                const uint32_t m = a.tmask ? a.tmask[i] : FULL;
+                tw.masked = m != FULL;  // then the rect has at most 32 tiles
+                tw.rest = m;
+                tw.inv_w = (65535u + (uint32_t)tw.w) / (uint32_t)tw.w;
+                if (FILL) key = a.dkey[i];
+            }
+        }
+        const uint32_t maxc = __reduce_max_sync(FULL, cnt);
+        for (uint32_t k = 0; k < maxc; ++k) {
+            const bool act = k < cnt;
+            const uint32_t am = __ballot_sync(FULL, act);
+            if (act) {
+                const uint32_t t = tw.next();
+                const uint32_t peers = __match_any_sync(am, t);
+                const int leader = __ffs(peers) - 1;
+                if (!FILL) {
+                    if (lane == leader) atomicAdd(&a.tile_cnt[t], (uint32_t)__popc(peers));
+                } else {
+                    uint32_t b = 0;
+                    if (lane == leader) b = atomicAdd(&a.cursor[t], (uint32_t)__popc(peers));
+                    b = __shfl_sync(peers, b, leader);
+                    const uint32_t slot = b + (uint32_t)__popc(peers & lt);
+                    a.bk_key[slot] = key;
+                    a.bk_id[slot] = (uint32_t)i;
+                }
+            }
+        }
+    }
+}
+
+// Step 2 (one block of 1024): ranges ([0, 0) for an empty tile), fill
+// cursors and P.  Tile slots past the views' tiles (a graph replayed with
+// smaller views) are empty.  P saturates at 2^32 - 1, which no pair buffer
+// holds.
+__global__ __launch_bounds__(1024) void k_bin_scan(BinArgs a) {
+    __shared__ unsigned long long sw[32];
+    const RenderView &lv = a.views[a.n_views - 1];
+    const uint32_t T = min(a.n_slots, lv.tile_base + (uint32_t)(lv.tiles_x * lv.tiles_y));
+    const uint32_t per = (a.n_slots + 1023u) / 1024u;
+    const uint32_t t0 = min(threadIdx.x * per, a.n_slots), t1 = min(t0 + per, a.n_slots);
+    unsigned long long local = 0;
+    for (uint32_t t = t0; t < t1; ++t) local += t < T ? a.tile_cnt[t] : 0u;
+    unsigned long long tot;
+    unsigned long long run = block_excl_scan<32>(local, sw, tot);
+    for (uint32_t t = t0; t < t1; ++t) {
+        const uint32_t c = t < T ? a.tile_cnt[t] : 0u;
+        const uint32_t f = (uint32_t)min(run, 0xffffffffull);
+        a.ranges[t] = c ? make_uint2(f, (uint32_t)min(run + c, 0xffffffffull)) : make_uint2(0u, 0u);  // empty: [0, 0)
+        a.cursor[t] = f;
+        run += c;
+    }
+    if (threadIdx.x == 0) *a.p_dev = (uint32_t)min(tot, 0xffffffffull);
+}
+
+// ---------------------------------------------------------------- step 5
+constexpr int BS_THREADS = 256;                  // >= 256: thread d < 256 owns digit d in the scans
+constexpr int BS_WARPS = BS_THREADS / 32;
+constexpr int BS_MAX = 6144;                    // bucket size sorted in shared memory
+constexpr int BS_ROUNDS = BS_MAX / BS_THREADS;   // rounds of 32 per warp for a full chunk
+constexpr int BS_RUN_MAX = 32;                  // longest run of equal depth keys fixed in place
+
+struct BinSortSmem {
+    uint32_t k[2][BS_MAX];
+    uint32_t v[2][BS_MAX];
+    uint32_t wcnt[BS_WARPS][256];  // per warp and digit: counts, then offsets within the digit
+    uint32_t dbase[256];           // first position of each digit
+    uint32_t run[256];             // global path: next position of each digit
+    uint32_t sw[BS_WARPS];
+    uint32_t red[4];
+    uint32_t tile, flag;
+};
+
+__device__ __forceinline__ uint32_t digit_of(uint32_t x, uint32_t sub, int shift) { return ((x - sub) >> shift) & 255u; }
+
+// Elements per warp for a chunk of m: the chunk is split evenly, in
+// multiples of 32 (a warp's round), warp w owning [w pw, (w + 1) pw).
+__device__ __forceinline__ int per_warp(int m) { return ((m + BS_THREADS - 1) / BS_THREADS) * 32; }
+
+// Stable ranking of the chunk (ks, vs)[0, m) on one 8-bit digit (of v - sub
+// when by_val, else of k - sub): warp w owns elements [w pw, (w + 1) pw),
+// 32 per round in order (R >= pw / 32 rounds unrolled); on return
+// S.wcnt[w][d] is warp w's first position within digit d, and thread d
+// holds digit d's count in `count`.
+template <int R>
+__device__ __forceinline__ void rank_chunk(BinSortSmem &S, const uint32_t *ks, const uint32_t *vs, int m,
+                                           bool by_val, uint32_t sub, int shift, uint32_t (&dig)[R],
+                                           uint32_t (&rank)[R], uint32_t &count) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t lt = lanemask_lt();
+    for (int i = tid; i < BS_WARPS * 256; i += BS_THREADS) (&S.wcnt[0][0])[i] = 0u;
+    __syncthreads();
+    const int pw = per_warp(m), wb = warp * pw;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int j = wb + r * 32 + lane;
+        const bool valid = r * 32 < pw && j < m;
+        uint32_t d = 0;
+        if (valid) d = digit_of(by_val ? vs[j] : ks[j], sub, shift);
+        uint32_t peers = __ballot_sync(FULL, valid);
+        uint32_t rk = 0;
+        if (peers) {  // warp-uniform
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                const uint32_t bal = __ballot_sync(FULL, (d >> b) & 1u);
+                peers &= ((d >> b) & 1u) ? bal : ~bal;
+            }
+            uint32_t before = 0;
+            if (valid) before = S.wcnt[warp][d];
+            __syncwarp();
+            if (valid && (peers & lt) == 0) S.wcnt[warp][d] = before + (uint32_t)__popc(peers);
+            __syncwarp();
+            rk = before + (uint32_t)__popc(peers & lt);
+        }
+        dig[r] = d;
+        rank[r] = rk;
+    }
+    __syncthreads();
+    count = 0;
+    if (tid < 256) {  // thread d: digit d
+#pragma unroll
+        for (int w = 0; w < BS_WARPS; ++w) {
+            const uint32_t c = S.wcnt[w][tid];
+            S.wcnt[w][tid] = count;
+            count += c;
+        }
+    }
+}
+
+// One stable pass over the chunk in shared memory: (k, v)[src] -> [src ^ 1].
+template <int R>
+__device__ __forceinline__ void smem_pass(BinSortSmem &S, int src, int m, bool by_val, uint32_t sub, int shift) {
+    uint32_t dig[R], rank[R], count;
+    rank_chunk<R>(S, S.k[src], S.v[src], m, by_val, sub, shift, dig, rank, count);
+    uint32_t tot;
+    const uint32_t base = block_excl_scan<BS_WARPS>(count, S.sw, tot);
+    if (threadIdx.x < 256) S.dbase[threadIdx.x] = base;
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, pw = per_warp(m), wb = warp * pw;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int j = wb + r * 32 + lane;
+        if (r * 32 < pw && j < m) {
+            const uint32_t pos = S.dbase[dig[r]] + S.wcnt[warp][dig[r]] + rank[r];
+            S.k[src ^ 1][pos] = S.k[src][j];
+            S.v[src ^ 1][pos] = S.v[src][j];
+        }
+    }
+    __syncthreads();
+}
+
+// The pass with the fewest unrolled rounds that cover m.
+__device__ __forceinline__ void smem_pass_any(BinSortSmem &S, int src, int m, bool by_val, uint32_t sub, int shift) {
+    const int rounds = per_warp(m) / 32;
+    if (rounds <= 1) smem_pass<1>(S, src, m, by_val, sub, shift);
+    else if (rounds <= 2) smem_pass<2>(S, src, m, by_val, sub, shift);
+    else if (rounds <= 4) smem_pass<4>(S, src, m, by_val, sub, shift);
+    else if (rounds <= 8) smem_pass<8>(S, src, m, by_val, sub, shift);
+    else smem_pass<BS_ROUNDS>(S, src, m, by_val, sub, shift);
+}
+
+// One stable pass over a bucket in global memory, chunk by chunk:
+// (ka, va)[0, n) -> (kb, vb)[0, n).
+__device__ void global_pass(BinSortSmem &S, const uint32_t *ka, const uint32_t *va, uint32_t *kb, uint32_t *vb,
+                            uint32_t n, bool by_val, uint32_t sub, int shift) {
+    const int tid = threadIdx.x;
+    if (tid < 256) S.dbase[tid] = 0u;
+    __syncthreads();
+    for (uint32_t j = tid; j < n; j += BS_THREADS) atomicAdd(&S.dbase[digit_of(by_val ? va[j] : ka[j], sub, shift)], 1u);
+    __syncthreads();
+    {
+        const uint32_t c = tid < 256 ? S.dbase[tid] : 0u;
+        uint32_t tot;
+        const uint32_t e = block_excl_scan<BS_WARPS>(c, S.sw, tot);
+        if (tid < 256) S.run[tid] = e;
+    }
+    __syncthreads();
+    const int warp = tid >> 5, lane = tid & 31;
+    for (uint32_t c0 = 0; c0 < n; c0 += BS_MAX) {
+        const int m = (int)min((uint32_t)BS_MAX, n - c0);
+        for (int j = tid; j < m; j += BS_THREADS) {
+            S.k[0][j] = ka[c0 + j];
+            S.v[0][j] = va[c0 + j];
+        }
+        __syncthreads();
+        uint32_t dig[BS_ROUNDS], rank[BS_ROUNDS], count;
+        rank_chunk<BS_ROUNDS>(S, S.k[0], S.v[0], m, by_val, sub, shift, dig, rank, count);
+        __syncthreads();
+        const int pw = per_warp(m), wb = warp * pw;
+#pragma unroll
+        for (int r = 0; r < BS_ROUNDS; ++r) {
+            const int j = wb + r * 32 + lane;
+            if (r * 32 < pw && j < m) {
+                const uint32_t pos = S.run[dig[r]] + S.wcnt[warp][dig[r]] + rank[r];
+                kb[pos] = S.k[0][j];
+                vb[pos] = S.v[0][j];
+            }
+        }
+        __syncthreads();
+        if (tid < 256) S.run[tid] += count;
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ int sig_bits(uint32_t lo, uint32_t hi) { return hi > lo ? 32 - __clz(hi - lo) : 0; }
+
+// Block-wide min and max of two words (results in S.red: kmin, kmax, vmin, vmax).
+__device__ __forceinline__ void block_minmax(BinSortSmem &S, uint32_t kmn, uint32_t kmx, uint32_t vmn, uint32_t vmx) {
+    kmn = __reduce_min_sync(FULL, kmn);
+    kmx = __reduce_max_sync(FULL, kmx);
+    vmn = __reduce_min_sync(FULL, vmn);
+    vmx = __reduce_max_sync(FULL, vmx);
+    if (threadIdx.x == 0) {
+        S.red[0] = FULL;
+        S.red[1] = 0u;
+        S.red[2] = FULL;
+        S.red[3] = 0u;
+    }
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&S.red[0], kmn);
+        atomicMax(&S.red[1], kmx);
+        atomicMin(&S.red[2], vmn);
+        atomicMax(&S.red[3], vmx);
+    }
+    __syncthreads();
+}
+
+// Puts the ids of each run of equal keys of (k, v)[0, n) (sorted by key)
+// in ascending order, in place, when the run holds at most 32 entries (one
+// thread per run); returns true (block-uniform) when a longer run exists,
+// leaving the array sorted by key only.
+__device__ bool fix_ties(BinSortSmem &S, const uint32_t *k, uint32_t *v, uint32_t n) {
+    const int tid = threadIdx.x;
+    if (tid == 0) S.flag = 0u;
+    __syncthreads();
+    for (uint32_t j = tid; j + 1 < n; j += BS_THREADS) {
+        const uint32_t kj = k[j];
+        if ((j == 0 || k[j - 1] != kj) && k[j + 1] == kj) {
+            uint32_t e = j + 1;
+            while (e < n && k[e] == kj && e - j <= (uint32_t)BS_RUN_MAX) ++e;
+            if (e - j > (uint32_t)BS_RUN_MAX) {
+                atomicOr(&S.flag, 1u);
+            } else {
+                for (uint32_t x = j + 1; x < e; ++x) {  // insertion sort of the run's ids
+                    const uint32_t vx = v[x];
+                    uint32_t y = x;
+                    while (y > j && v[y - 1] > vx) {
+                        v[y] = v[y - 1];
+                        --y;
+                    }
+                    v[y] = vx;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const bool longrun = S.flag != 0u;
+    __syncthreads();
+    return longrun;
+}
+
+__global__ __launch_bounds__(BS_THREADS, 2) void k_bin_sort(BinArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    BinSortSmem &S = *reinterpret_cast<BinSortSmem *>(smem_raw);
+    const int tid = threadIdx.x;
+    if (*a.p_dev > a.p_cap) return;  // nothing was filled (the ranges are empty)
+    for (;;) {
+        if (tid == 0) S.tile = atomicAdd(a.tile_ctr, 1u);
+        __syncthreads();
+        const uint32_t q = S.tile;
+        __syncthreads();
+        if (q >= a.n_slots) break;
+        const uint2 rg = a.ranges[a.tile_order[q]];
+        const uint32_t first = rg.x, n = rg.y - rg.x;
+        if (n == 0) continue;
+        const uint32_t *bk = a.bk_key + first, *bi = a.bk_id + first;
+        uint32_t *out = a.ids_out + first;
+        if (n == 1) {
+            if (tid == 0) out[0] = bi[0];
+            continue;
+        }
+        uint32_t kmn = FULL, kmx = 0u, vmn = FULL, vmx = 0u;
+        if (n <= (uint32_t)BS_MAX) {
+            for (uint32_t j = tid; j < n; j += BS_THREADS) {
+                const uint32_t k = bk[j], v = bi[j];
+                S.k[0][j] = k;
+                S.v[0][j] = v;
+                kmn = min(kmn, k); kmx = max(kmx, k); vmn = min(vmn, v); vmx = max(vmx, v);
+            }
+            block_minmax(S, kmn, kmx, vmn, vmx);
+            const uint32_t kmin = S.red[0], vmin = S.red[2];
+            const int kb = sig_bits(kmin, S.red[1]), vb = sig_bits(vmin, S.red[3]);
+            const int m = (int)n;
+            int src = 0;
+            for (int sh = 0; sh < kb; sh += 8) {
+                smem_pass_any(S, src, m, false, kmin, sh);
+                src ^= 1;
+            }
+            // runs of equal depth keys: ids in order (short runs in place)
+            if (fix_ties(S, S.k[src], S.v[src], n)) {  // a long run: the full (depth key, id) order
+                for (int sh = 0; sh < vb; sh += 8) {
+                    smem_pass_any(S, src, m, true, vmin, sh);
+                    src ^= 1;
+                }
+                for (int sh = 0; sh < kb; sh += 8) {
+                    smem_pass_any(S, src, m, false, kmin, sh);
+                    src ^= 1;
+                }
+            }
+            for (int j = tid; j < m; j += BS_THREADS) out[j] = S.v[src][j];
+            __syncthreads();
+        } else {
+            // beyond shared memory: the same passes over global memory, chunk by chunk
+            for (uint32_t j = tid; j < n; j += BS_THREADS) {
+                const uint32_t k = bk[j], v = bi[j];
+                kmn = min(kmn, k); kmx = max(kmx, k); vmn = min(vmn, v); vmx = max(vmx, v);
+            }
+            block_minmax(S, kmn, kmx, vmn, vmx);
+            const uint32_t kmin = S.red[0], vmin = S.red[2];
+            const int kb = sig_bits(kmin, S.red[1]), vb = sig_bits(vmin, S.red[3]);
+            uint32_t *k0 = a.bk_key + first, *k1 = a.tmp_key + first;
+            uint32_t *v0 = a.bk_id + first, *v1 = a.tmp_id + first;
+            for (int sh = 0; sh < kb; sh += 8) {
+                global_pass(S, k0, v0, k1, v1, n, false, kmin, sh);
+                uint32_t *t = k0; k0 = k1; k1 = t;
+                t = v0; v0 = v1; v1 = t;
+            }
+            if (fix_ties(S, k0, v0, n)) {  // a long run of equal depth keys: id digits first, then depth
+                for (int sh = 0; sh < vb; sh += 8) {
+                    global_pass(S, k0, v0, k1, v1, n, true, vmin, sh);
+                    uint32_t *t = k0; k0 = k1; k1 = t;
+                    t = v0; v0 = v1; v1 = t;
+                }
+                for (int sh = 0; sh < kb; sh += 8) {
+                    global_pass(S, k0, v0, k1, v1, n, false, kmin, sh);
+                    uint32_t *t = k0; k0 = k1; k1 = t;
+                    t = v0; v0 = v1; v1 = t;
+                }
+            }
+            // the result is in (k0, v0); the output region may be v0 itself
+            for (uint32_t j = tid; j < n; j += BS_THREADS) out[j] = v0[j];
+            __syncthreads();
+        }
+    }
+}
+
+// Order in which the persistent kernels take the tiles: longest lists first
+// (largest-processing-time-first scheduling shortens the tail of the grid).
+// One block buckets the tiles by 4 log2(pair count); tiles with no pairs
+// follow, then tile slots beyond the views' tile count (graph replays size
+// the launch for their largest batch).  The order within a bucket depends
+// on atomics, which changes no output: every tile is processed independently.
+constexpr int TO_BUCKETS = 64;
+__global__ __launch_bounds__(1024) void k_tile_order(const uint2 *ranges, const RenderView *views, int n_views,
+                                                     uint32_t n_slots, uint32_t *order) {
+    __shared__ uint32_t cnt[TO_BUCKETS + 2], off[TO_BUCKETS + 2];
+    const RenderView &lv = views[n_views - 1];
+    const uint32_t n_tiles = min(n_slots, lv.tile_base + (uint32_t)(lv.tiles_x * lv.tiles_y));
+    for (int i = threadIdx.x; i < TO_BUCKETS + 2; i += blockDim.x) cnt[i] = 0;
+    __syncthreads();
+    auto bucket = [&](uint32_t t) -> int {
+        if (t >= n_tiles) return TO_BUCKETS + 1;  // not a tile of this batch
+        const uint32_t c = ranges[t].y - ranges[t].x;
+        if (c == 0) return TO_BUCKETS;
+        const int lg = (int)(4.0f * __log2f((float)c));
+        return TO_BUCKETS - 1 - min(TO_BUCKETS - 1, max(0, lg));  // descending count
+    };
+    for (uint32_t t = threadIdx.x; t < n_slots; t += blockDim.x) atomicAdd(&cnt[bucket(t)], 1u);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int b = 0; b < TO_BUCKETS + 2; ++b) {
+            off[b] = run;
+            run += cnt[b];
+        }
+    }
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < n_slots; t += blockDim.x) order[atomicAdd(&off[bucket(t)], 1u)] = t;
+}
+
+__global__ void k_fill_u32(uint32_t *p, uint32_t v, uint64_t n) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+__global__ void k_scale_u32(const uint32_t *src, uint32_t k, uint32_t *dst) { *dst = *src * k; }
+
+__global__ void k_zero_f32_n(float *p, const uint32_t *n_dev, int mult) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < (uint64_t)*n_dev * mult) p[i] = 0.0f;
+}
+
+int sm_count() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        sms = std::max(sms, 1);
+    }
+    return sms;
+}
+
+// Grid of the instance walks: at most a few waves, whatever the capacity is
+// (warps stride over the instance count on the device).
+int walk_blocks(int64_t inst_cap) {
+    const int64_t want = (std::max<int64_t>(inst_cap, 1) + 255) / 256;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sm_count() * 8));
+}
+
+}  // namespace
+
+void launch_bin_count(const BinArgs &a, cudaStream_t s) {
+    cudaMemsetAsync(a.tile_cnt, 0, sizeof(uint32_t) * std::max<uint32_t>(a.n_slots, 1), s);
+    k_bin_walk<false><<<walk_blocks(a.inst_cap), 256, 0, s>>>(a);
+    k_bin_scan<<<1, 1024, 0, s>>>(a);
+    note_launches(2);
+}
+
+void launch_bin_fill(const BinArgs &a, cudaStream_t s) {
+    k_bin_walk<true><<<walk_blocks(a.inst_cap), 256, 0, s>>>(a);
+    note_launches(1);
+}
+
+static int g_sort_grid = 0;
+
+int bin_sort_setup() {
+    if (!g_sort_grid) {
+        const size_t smem = sizeof(BinSortSmem);
+        cudaFuncSetAttribute(k_bin_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bin_sort, BS_THREADS, smem);
+        g_sort_grid = sm_count() * std::max(1, per_sm);
+    }
+    return g_sort_grid;
+}
+
+void launch_bin_sort(const BinArgs &a, cudaStream_t s) {
+    const int grid = bin_sort_setup();
+    cudaMemsetAsync(a.tile_ctr, 0, sizeof(uint32_t), s);
+    k_bin_sort<<<std::min(grid, (int)std::max<uint32_t>(a.n_slots, 1)), BS_THREADS, sizeof(BinSortSmem), s>>>(a);
+    note_launches(1);
+}
+
+void launch_tile_order(const uint2 *ranges, const RenderView *views, int n_views, int n_slots, uint32_t *order,
+                       cudaStream_t s) {
+    if (n_slots <= 0) return;
+    k_tile_order<<<1, 1024, 0, s>>>(ranges, views, n_views, (uint32_t)n_slots, order);
+    note_launches(1);
+}
+
+void launch_fill_u32(uint32_t *p, uint32_t v, int64_t n, cudaStream_t s) {
+    if (n <= 0) return;
+    k_fill_u32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, v, (uint64_t)n);
+    note_launches(1);
+}
+
+void launch_scale_u32(const uint32_t *src, uint32_t k, uint32_t *dst, cudaStream_t s) {
+    k_scale_u32<<<1, 1, 0, s>>>(src, k, dst);
+    note_launches(1);
+}
+
+void launch_zero_f32_n(float *p, const uint32_t *n_dev, int mult, int64_t n_cap, cudaStream_t s) {
+    if (n_cap <= 0) return;
+    const int64_t n = n_cap * mult;
+    k_zero_f32_n<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, n_dev, mult);
+    note_launches(1);
+}
+
+}  // namespace tsp

@@ -404,13 +404,14 @@ tsplat_status tsplat_server_create(const tsplat_server_config *cfg, tsplat_serve
         delete S;
         return record_error(TSPLAT_ERR_CUDA, "server_create: event creation failed");
     }
-    // bytes of one lane: per instance 32 (record) + 8 (rect) + 16 (counts, keys) + 16 (sort buffers),
-    // per pair 16 (two key/value buffers), plus the view table and ranges
+    // bytes of one lane: per instance 32 (record) + 8 (rect) + 16 (tile count, mask, depth key, radius),
+    // per pair 16 (bucket keys and ids, scratch, sorted ids) with the 1/8 headroom of the pair buffers,
+    // per tile 20 (range, order, count and cursor), plus the view table
     const int64_t K = cfg->max_views_per_batch;
     const int64_t inst = K * cfg->max_gaussians;
     const int64_t tiles = K * (int64_t)((cfg->max_width + TILE - 1) / TILE) * ((cfg->max_height + TILE - 1) / TILE);
     const int64_t pairs = K * est_pairs(*S, cfg->max_gaussians, cfg->max_width, cfg->max_height);
-    const int64_t lane_bytes = inst * 72 + pairs * 18 + tiles * 8 + (int64_t)(1 << 20);
+    const int64_t lane_bytes = inst * 56 + pairs * 18 + tiles * 20 + (int64_t)(1 << 20);
     const int64_t n_lanes = std::min<int64_t>(cfg->max_lanes, cfg->budget_bytes / std::max<int64_t>(lane_bytes, 1));
     S->lane_bytes = lane_bytes;
     if (n_lanes < 1) {
