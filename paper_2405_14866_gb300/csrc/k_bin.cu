@@ -185,15 +185,14 @@ __global__ __launch_bounds__(1024) void k_bin_scan(BinArgs a) {
 }
 
 // ---------------------------------------------------------------- step 5
-constexpr int BS_THREADS = 256;                  // >= 256: thread d < 256 owns digit d in the scans
+constexpr int BS_THREADS = 256;                  // = the 256 digits: thread d owns digit d in the scans
 constexpr int BS_WARPS = BS_THREADS / 32;
-constexpr int BS_MAX = 6144;                    // bucket size sorted in shared memory
+constexpr int BS_MAX = 6144;                     // bucket size sorted in shared memory
 constexpr int BS_ROUNDS = BS_MAX / BS_THREADS;   // rounds of 32 per warp for a full chunk
-constexpr int BS_RUN_MAX = 32;                  // longest run of equal depth keys fixed in place
+constexpr int BS_RUN_MAX = 32;                   // longest run of equal depth keys fixed in place
 
 struct BinSortSmem {
-    uint32_t k[2][BS_MAX];
-    uint32_t v[2][BS_MAX];
+    uint2 kv[2][BS_MAX];           // (depth key - the tile's smallest, instance id)
     uint32_t wcnt[BS_WARPS][256];  // per warp and digit: counts, then offsets within the digit
     uint32_t dbase[256];           // first position of each digit
     uint32_t run[256];             // global path: next position of each digit
@@ -202,21 +201,22 @@ struct BinSortSmem {
     uint32_t tile, flag;
 };
 
-__device__ __forceinline__ uint32_t digit_of(uint32_t x, uint32_t sub, int shift) { return ((x - sub) >> shift) & 255u; }
+// Digit `shift` of an entry: of its remapped depth key, or of its id - vmin.
+__device__ __forceinline__ uint32_t digit_of(uint2 e, bool by_id, uint32_t vmin, int shift) {
+    return ((by_id ? e.y - vmin : e.x) >> shift) & 255u;
+}
 
 // Elements per warp for a chunk of m: the chunk is split evenly, in
 // multiples of 32 (a warp's round), warp w owning [w pw, (w + 1) pw).
 __device__ __forceinline__ int per_warp(int m) { return ((m + BS_THREADS - 1) / BS_THREADS) * 32; }
 
-// Stable ranking of the chunk (ks, vs)[0, m) on one 8-bit digit (of v - sub
-// when by_val, else of k - sub): warp w owns elements [w pw, (w + 1) pw),
-// 32 per round in order (R >= pw / 32 rounds unrolled); on return
-// S.wcnt[w][d] is warp w's first position within digit d, and thread d
-// holds digit d's count in `count`.
+// Stable ranking of the chunk kv[0, m) on one 8-bit digit: warp w owns
+// elements [w pw, (w + 1) pw), 32 per round in order (R >= pw / 32 rounds
+// unrolled); on return S.wcnt[w][d] is warp w's first position within digit
+// d, and thread d holds digit d's count in `count`.
 template <int R>
-__device__ __forceinline__ void rank_chunk(BinSortSmem &S, const uint32_t *ks, const uint32_t *vs, int m,
-                                           bool by_val, uint32_t sub, int shift, uint32_t (&dig)[R],
-                                           uint32_t (&rank)[R], uint32_t &count) {
+__device__ __forceinline__ void rank_chunk(BinSortSmem &S, const uint2 *kv, int m, bool by_id, uint32_t vmin,
+                                           int shift, uint32_t (&dig)[R], uint32_t (&rank)[R], uint32_t &count) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t lt = lanemask_lt();
     for (int i = tid; i < BS_WARPS * 256; i += BS_THREADS) (&S.wcnt[0][0])[i] = 0u;
@@ -227,7 +227,7 @@ __device__ __forceinline__ void rank_chunk(BinSortSmem &S, const uint32_t *ks, c
         const int j = wb + r * 32 + lane;
         const bool valid = r * 32 < pw && j < m;
         uint32_t d = 0;
-        if (valid) d = digit_of(by_val ? vs[j] : ks[j], sub, shift);
+        if (valid) d = digit_of(kv[j], by_id, vmin, shift);
         uint32_t peers = __ballot_sync(FULL, valid);
         uint32_t rk = 0;
         if (peers) {  // warp-uniform
@@ -248,74 +248,67 @@ __device__ __forceinline__ void rank_chunk(BinSortSmem &S, const uint32_t *ks, c
     }
     __syncthreads();
     count = 0;
-    if (tid < 256) {  // thread d: digit d
 #pragma unroll
-        for (int w = 0; w < BS_WARPS; ++w) {
-            const uint32_t c = S.wcnt[w][tid];
-            S.wcnt[w][tid] = count;
-            count += c;
-        }
+    for (int w = 0; w < BS_WARPS; ++w) {
+        const uint32_t c = S.wcnt[w][tid];
+        S.wcnt[w][tid] = count;
+        count += c;
     }
 }
 
-// One stable pass over the chunk in shared memory: (k, v)[src] -> [src ^ 1].
+// One stable pass over the chunk in shared memory: kv[src] -> kv[src ^ 1].
 template <int R>
-__device__ __forceinline__ void smem_pass(BinSortSmem &S, int src, int m, bool by_val, uint32_t sub, int shift) {
+__device__ __forceinline__ void smem_pass(BinSortSmem &S, int src, int m, bool by_id, uint32_t vmin, int shift) {
     uint32_t dig[R], rank[R], count;
-    rank_chunk<R>(S, S.k[src], S.v[src], m, by_val, sub, shift, dig, rank, count);
+    rank_chunk<R>(S, S.kv[src], m, by_id, vmin, shift, dig, rank, count);
     uint32_t tot;
     const uint32_t base = block_excl_scan<BS_WARPS>(count, S.sw, tot);
-    if (threadIdx.x < 256) S.dbase[threadIdx.x] = base;
+    S.dbase[threadIdx.x] = base;
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, pw = per_warp(m), wb = warp * pw;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int j = wb + r * 32 + lane;
-        if (r * 32 < pw && j < m) {
-            const uint32_t pos = S.dbase[dig[r]] + S.wcnt[warp][dig[r]] + rank[r];
-            S.k[src ^ 1][pos] = S.k[src][j];
-            S.v[src ^ 1][pos] = S.v[src][j];
-        }
+        if (r * 32 < pw && j < m) S.kv[src ^ 1][S.dbase[dig[r]] + S.wcnt[warp][dig[r]] + rank[r]] = S.kv[src][j];
     }
     __syncthreads();
 }
 
 // The pass with the fewest unrolled rounds that cover m.
-__device__ __forceinline__ void smem_pass_any(BinSortSmem &S, int src, int m, bool by_val, uint32_t sub, int shift) {
+__device__ __forceinline__ void smem_pass_any(BinSortSmem &S, int src, int m, bool by_id, uint32_t vmin, int shift) {
     const int rounds = per_warp(m) / 32;
-    if (rounds <= 1) smem_pass<1>(S, src, m, by_val, sub, shift);
-    else if (rounds <= 2) smem_pass<2>(S, src, m, by_val, sub, shift);
-    else if (rounds <= 4) smem_pass<4>(S, src, m, by_val, sub, shift);
-    else if (rounds <= 8) smem_pass<8>(S, src, m, by_val, sub, shift);
-    else smem_pass<BS_ROUNDS>(S, src, m, by_val, sub, shift);
+    if (rounds <= 1) smem_pass<1>(S, src, m, by_id, vmin, shift);
+    else if (rounds <= 2) smem_pass<2>(S, src, m, by_id, vmin, shift);
+    else if (rounds <= 4) smem_pass<4>(S, src, m, by_id, vmin, shift);
+    else if (rounds <= 8) smem_pass<8>(S, src, m, by_id, vmin, shift);
+    else if (rounds <= 12) smem_pass<12>(S, src, m, by_id, vmin, shift);
+    else smem_pass<BS_ROUNDS>(S, src, m, by_id, vmin, shift);
 }
 
 // One stable pass over a bucket in global memory, chunk by chunk:
-// (ka, va)[0, n) -> (kb, vb)[0, n).
+// (ka, va)[0, n) -> (kb, vb)[0, n); keys are remapped by kmin while in
+// shared memory.
 __device__ void global_pass(BinSortSmem &S, const uint32_t *ka, const uint32_t *va, uint32_t *kb, uint32_t *vb,
-                            uint32_t n, bool by_val, uint32_t sub, int shift) {
+                            uint32_t n, bool by_id, uint32_t kmin, uint32_t vmin, int shift) {
     const int tid = threadIdx.x;
-    if (tid < 256) S.dbase[tid] = 0u;
+    S.dbase[tid] = 0u;
     __syncthreads();
-    for (uint32_t j = tid; j < n; j += BS_THREADS) atomicAdd(&S.dbase[digit_of(by_val ? va[j] : ka[j], sub, shift)], 1u);
+    for (uint32_t j = tid; j < n; j += BS_THREADS)
+        atomicAdd(&S.dbase[digit_of(make_uint2(ka[j] - kmin, va[j]), by_id, vmin, shift)], 1u);
     __syncthreads();
     {
-        const uint32_t c = tid < 256 ? S.dbase[tid] : 0u;
         uint32_t tot;
-        const uint32_t e = block_excl_scan<BS_WARPS>(c, S.sw, tot);
-        if (tid < 256) S.run[tid] = e;
+        const uint32_t e = block_excl_scan<BS_WARPS>(S.dbase[tid], S.sw, tot);
+        S.run[tid] = e;
     }
     __syncthreads();
     const int warp = tid >> 5, lane = tid & 31;
     for (uint32_t c0 = 0; c0 < n; c0 += BS_MAX) {
         const int m = (int)min((uint32_t)BS_MAX, n - c0);
-        for (int j = tid; j < m; j += BS_THREADS) {
-            S.k[0][j] = ka[c0 + j];
-            S.v[0][j] = va[c0 + j];
-        }
+        for (int j = tid; j < m; j += BS_THREADS) S.kv[0][j] = make_uint2(ka[c0 + j] - kmin, va[c0 + j]);
         __syncthreads();
         uint32_t dig[BS_ROUNDS], rank[BS_ROUNDS], count;
-        rank_chunk<BS_ROUNDS>(S, S.k[0], S.v[0], m, by_val, sub, shift, dig, rank, count);
+        rank_chunk<BS_ROUNDS>(S, S.kv[0], m, by_id, vmin, shift, dig, rank, count);
         __syncthreads();
         const int pw = per_warp(m), wb = warp * pw;
 #pragma unroll
@@ -323,12 +316,13 @@ __device__ void global_pass(BinSortSmem &S, const uint32_t *ka, const uint32_t *
             const int j = wb + r * 32 + lane;
             if (r * 32 < pw && j < m) {
                 const uint32_t pos = S.run[dig[r]] + S.wcnt[warp][dig[r]] + rank[r];
-                kb[pos] = S.k[0][j];
-                vb[pos] = S.v[0][j];
+                const uint2 e = S.kv[0][j];
+                kb[pos] = e.x + kmin;
+                vb[pos] = e.y;
             }
         }
         __syncthreads();
-        if (tid < 256) S.run[tid] += count;
+        S.run[tid] += count;
         __syncthreads();
     }
 }
@@ -357,30 +351,46 @@ __device__ __forceinline__ void block_minmax(BinSortSmem &S, uint32_t kmn, uint3
     __syncthreads();
 }
 
-// Puts the ids of each run of equal keys of (k, v)[0, n) (sorted by key)
+// Entries in shared memory ((key, id) pairs) or in global memory (two arrays).
+struct SmemEntries {
+    uint2 *kv;
+    __device__ uint32_t key(uint32_t j) const { return kv[j].x; }
+    __device__ uint32_t id(uint32_t j) const { return kv[j].y; }
+    __device__ void set_id(uint32_t j, uint32_t v) const { kv[j].y = v; }
+};
+struct GlobalEntries {
+    const uint32_t *k;
+    uint32_t *v;
+    __device__ uint32_t key(uint32_t j) const { return k[j]; }
+    __device__ uint32_t id(uint32_t j) const { return v[j]; }
+    __device__ void set_id(uint32_t j, uint32_t x) const { v[j] = x; }
+};
+
+// Puts the ids of each run of equal keys of entries [0, n) (sorted by key)
 // in ascending order, in place, when the run holds at most 32 entries (one
 // thread per run); returns true (block-uniform) when a longer run exists,
-// leaving the array sorted by key only.
-__device__ bool fix_ties(BinSortSmem &S, const uint32_t *k, uint32_t *v, uint32_t n) {
+// leaving the entries sorted by key only.
+template <class E>
+__device__ bool fix_ties(BinSortSmem &S, const E &e, uint32_t n) {
     const int tid = threadIdx.x;
     if (tid == 0) S.flag = 0u;
     __syncthreads();
     for (uint32_t j = tid; j + 1 < n; j += BS_THREADS) {
-        const uint32_t kj = k[j];
-        if ((j == 0 || k[j - 1] != kj) && k[j + 1] == kj) {
-            uint32_t e = j + 1;
-            while (e < n && k[e] == kj && e - j <= (uint32_t)BS_RUN_MAX) ++e;
-            if (e - j > (uint32_t)BS_RUN_MAX) {
+        const uint32_t kj = e.key(j);
+        if ((j == 0 || e.key(j - 1) != kj) && e.key(j + 1) == kj) {
+            uint32_t end = j + 1;
+            while (end < n && e.key(end) == kj && end - j <= (uint32_t)BS_RUN_MAX) ++end;
+            if (end - j > (uint32_t)BS_RUN_MAX) {
                 atomicOr(&S.flag, 1u);
             } else {
-                for (uint32_t x = j + 1; x < e; ++x) {  // insertion sort of the run's ids
-                    const uint32_t vx = v[x];
+                for (uint32_t x = j + 1; x < end; ++x) {  // insertion sort of the run's ids
+                    const uint32_t vx = e.id(x);
                     uint32_t y = x;
-                    while (y > j && v[y - 1] > vx) {
-                        v[y] = v[y - 1];
+                    while (y > j && e.id(y - 1) > vx) {
+                        e.set_id(y, e.id(y - 1));
                         --y;
                     }
-                    v[y] = vx;
+                    e.set_id(y, vx);
                 }
             }
         }
@@ -415,31 +425,35 @@ __global__ __launch_bounds__(BS_THREADS, 2) void k_bin_sort(BinArgs a) {
         if (n <= (uint32_t)BS_MAX) {
             for (uint32_t j = tid; j < n; j += BS_THREADS) {
                 const uint32_t k = bk[j], v = bi[j];
-                S.k[0][j] = k;
-                S.v[0][j] = v;
+                S.kv[1][j] = make_uint2(k, v);  // staged; remapped into kv[0] below
                 kmn = min(kmn, k); kmx = max(kmx, k); vmn = min(vmn, v); vmx = max(vmx, v);
             }
             block_minmax(S, kmn, kmx, vmn, vmx);
             const uint32_t kmin = S.red[0], vmin = S.red[2];
             const int kb = sig_bits(kmin, S.red[1]), vb = sig_bits(vmin, S.red[3]);
             const int m = (int)n;
+            for (int j = tid; j < m; j += BS_THREADS) {
+                const uint2 e = S.kv[1][j];
+                S.kv[0][j] = make_uint2(e.x - kmin, e.y);
+            }
+            __syncthreads();
             int src = 0;
             for (int sh = 0; sh < kb; sh += 8) {
-                smem_pass_any(S, src, m, false, kmin, sh);
+                smem_pass_any(S, src, m, false, vmin, sh);
                 src ^= 1;
             }
             // runs of equal depth keys: ids in order (short runs in place)
-            if (fix_ties(S, S.k[src], S.v[src], n)) {  // a long run: the full (depth key, id) order
+            if (fix_ties(S, SmemEntries{S.kv[src]}, n)) {  // a long run: the full (depth key, id) order
                 for (int sh = 0; sh < vb; sh += 8) {
                     smem_pass_any(S, src, m, true, vmin, sh);
                     src ^= 1;
                 }
                 for (int sh = 0; sh < kb; sh += 8) {
-                    smem_pass_any(S, src, m, false, kmin, sh);
+                    smem_pass_any(S, src, m, false, vmin, sh);
                     src ^= 1;
                 }
             }
-            for (int j = tid; j < m; j += BS_THREADS) out[j] = S.v[src][j];
+            for (int j = tid; j < m; j += BS_THREADS) out[j] = S.kv[src][j].y;
             __syncthreads();
         } else {
             // beyond shared memory: the same passes over global memory, chunk by chunk
@@ -453,18 +467,18 @@ __global__ __launch_bounds__(BS_THREADS, 2) void k_bin_sort(BinArgs a) {
             uint32_t *k0 = a.bk_key + first, *k1 = a.tmp_key + first;
             uint32_t *v0 = a.bk_id + first, *v1 = a.tmp_id + first;
             for (int sh = 0; sh < kb; sh += 8) {
-                global_pass(S, k0, v0, k1, v1, n, false, kmin, sh);
+                global_pass(S, k0, v0, k1, v1, n, false, kmin, vmin, sh);
                 uint32_t *t = k0; k0 = k1; k1 = t;
                 t = v0; v0 = v1; v1 = t;
             }
-            if (fix_ties(S, k0, v0, n)) {  // a long run of equal depth keys: id digits first, then depth
+            if (fix_ties(S, GlobalEntries{k0, v0}, n)) {  // a long run of equal depth keys: ids, then depth
                 for (int sh = 0; sh < vb; sh += 8) {
-                    global_pass(S, k0, v0, k1, v1, n, true, vmin, sh);
+                    global_pass(S, k0, v0, k1, v1, n, true, kmin, vmin, sh);
                     uint32_t *t = k0; k0 = k1; k1 = t;
                     t = v0; v0 = v1; v1 = t;
                 }
                 for (int sh = 0; sh < kb; sh += 8) {
-                    global_pass(S, k0, v0, k1, v1, n, false, kmin, sh);
+                    global_pass(S, k0, v0, k1, v1, n, false, kmin, vmin, sh);
                     uint32_t *t = k0; k0 = k1; k1 = t;
                     t = v0; v0 = v1; v1 = t;
                 }
