@@ -469,8 +469,8 @@ static tsplat_status render_tail(tsplat_ctx *c, int64_t n_cap, const uint32_t *n
     bn.tile_order = c->torder.as<uint32_t>();
     bn.tile_ctr = sm + SM_BINCTR;
     bn.status = sm + SM_STATUS;
-    launch_bin_count(bn, s);
-    TRY(check_launch("render: count"));
+    launch_bin_scan(bn, s);
+    TRY(check_launch("render: scan"));
     TRY(mark(c, prof, 2, s));
 
     if (!async_mode) {
@@ -564,6 +564,7 @@ static ProjectOut project_out(tsplat_ctx *c) {
     o.rect = c->rect.as<uint2>();
     o.ntiles = c->ntiles.as<uint32_t>();
     o.tmask = c->tmask.as<uint32_t>();
+    o.tile_cnt = c->tcnt.as<uint32_t>();
     o.dkey = c->dkey.as<uint32_t>();
     o.radius = c->radius.as<float>();
     o.kminmax = small_ptr(c, SM_KMIN);

@@ -96,6 +96,7 @@ struct ProjectOut {
     uint32_t *kminmax;  // [2] min / max depth key of rendered Gaussians (pre-set to ~0u / 0)
     uint32_t *n_vis;    // [1] rendered Gaussians (pre-set to 0)
     uint32_t *tmask;    // [N] kept-tile masks (written with TSPLAT_RENDER_TIGHT)
+    uint32_t *tile_cnt; // [tiles] pairs per tile (zeroed by the launcher, counted by the kernel)
 };
 // Rects of at most this many tiles are tested tile by tile in tight binning.
 constexpr int TIGHT_MAX_TILES = 32;
@@ -138,8 +139,8 @@ struct BinArgs {
     uint32_t *tile_ctr;          // persistent-sort tile counter
     uint32_t *status;            // TSPLAT_ERR_CAPACITY when P > p_cap
 };
-// Per-tile counts, then ranges, cursors and P (two launches).
-void launch_bin_count(const BinArgs &a, cudaStream_t s);
+// Ranges, fill cursors and P from the per-tile counts the projection made.
+void launch_bin_scan(const BinArgs &a, cudaStream_t s);
 // Buckets filled with (depth key, id); P > p_cap: nothing written, empty ranges.
 void launch_bin_fill(const BinArgs &a, cudaStream_t s);
 // Each bucket sorted by (depth key, id) into ids_out (tiles in tile_order).

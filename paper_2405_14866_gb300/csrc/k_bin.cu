@@ -4,12 +4,12 @@
 // emitted in Gaussian-id order -- and each tile's [first, last) range.
 //
 // Built from tile buckets instead of device-wide sorts:
-//   1. k_bin_walk<false>  every instance, in id order, walks its kept tiles;
-//                         lanes of a warp that meet the same tile add their
-//                         count with one atomic (match_any);
+//   1. (in the projection) every instance, in id order, walks its kept
+//                         tiles; lanes of a warp that meet the same tile add
+//                         their count with one atomic (match_any);
 //   2. k_bin_scan         one block: exclusive scan of the tile counts: each
 //                         tile's range and fill cursor, and the total P;
-//   3. k_bin_walk<true>   the same walk; each (warp, tile) group reserves a run
+//   3. k_bin_fill         the same walk; each (warp, tile) group reserves a run
 //                         of its tile's bucket with one atomic and writes
 //                         (depth key, instance id) into it;
 //   4. k_tile_order       tiles longest list first;
@@ -25,6 +25,7 @@
 // not: (depth key, id) is unique within a tile.
 #include <algorithm>
 
+#include "bins.cuh"
 #include "common.cuh"
 #include "internal.h"
 
@@ -68,42 +69,14 @@ __device__ __forceinline__ T block_excl_scan(T v, T *sw, T &total) {
     return pre + x - v;
 }
 
-// The kept tiles of one instance, in row-major order of its rect: the whole
-// rect, or the set bits of its tight-binning mask.
-struct TileWalk {
-    uint32_t row0;  // global id of tile (0, y0) of the rect's view
-    int tiles_x, x0, w;
-    uint32_t rest;  // masked: kept tiles not visited yet (bit = index in the rect)
-    uint32_t inv_w; // masked: ceil(2^16 / w); loc * inv_w >> 16 = loc / w for loc < 32
-    int lx, ly;     // whole rect: the next tile
-    bool masked;
-    __device__ __forceinline__ uint32_t next() {
-        int x, y;
-        if (masked) {
-            const int loc = __ffs(rest) - 1;
-            rest &= rest - 1u;
-            y = (int)(((uint32_t)loc * inv_w) >> 16);
-            x = loc - y * w;
-        } else {
-            x = lx;
-            y = ly;
-            if (++lx == w) {
-                lx = 0;
-                ++ly;
-            }
-        }
-        return row0 + (uint32_t)(y * tiles_x + x0 + x);
-    }
-};
-
-// Steps 1 and 3.  Warps stride over 32-instance chunks in id order; the loop
-// over a chunk's tiles runs to the chunk's largest count, lanes past their
-// own count sitting out.
-template <bool FILL>
-__global__ __launch_bounds__(256) void k_bin_walk(BinArgs a) {
+// Step 3.  Warps stride over 32-instance chunks in id order; the loop over
+// a chunk's tiles runs to the chunk's largest count, lanes past their own
+// count sitting out.  (Step 1 runs inside the projection, which walks the
+// same tiles with warp_count_tiles.)
+__global__ __launch_bounds__(256) void k_bin_fill(BinArgs a) {
     const uint32_t n = *a.n_inst;
-    if (FILL && blockIdx.x == 0 && threadIdx.x == 0) *a.p_eff = *a.p_dev <= a.p_cap ? *a.p_dev : 0u;
-    if (FILL && *a.p_dev > a.p_cap) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a.p_eff = *a.p_dev <= a.p_cap ? *a.p_dev : 0u;
+    if (*a.p_dev > a.p_cap) {
         // the pairs do not fit: nothing is written and every tile is empty
         if (blockIdx.x == 0 && threadIdx.x == 0) set_status(a.status, TSPLAT_ERR_CAPACITY);
         for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < a.n_slots; t += gridDim.x * blockDim.x)
@@ -118,23 +91,15 @@ __global__ __launch_bounds__(256) void k_bin_walk(BinArgs a) {
         const uint64_t i = c0 + lane;
         uint32_t cnt = 0, key = 0;
         TileWalk tw;
-        tw.row0 = 0; tw.tiles_x = 1; tw.x0 = 0; tw.w = 1; tw.rest = 0; tw.inv_w = 0; tw.lx = 0; tw.ly = 0;
-        tw.masked = false;
+        tw.clear();
         if (i < n) {
             cnt = a.ntiles[i];
             if (cnt) {
                 int x0, y0, x1, y1;
                 unpack_rect(a.rect[i], x0, y0, x1, y1);
                 const RenderView &vw = a.views[a.n_views > 1 ? (uint32_t)(i / ns) : 0u];
-                tw.tiles_x = vw.tiles_x;
-                tw.x0 = x0;
-                tw.w = x1 - x0;
-                tw.row0 = vw.tile_base + (uint32_t)(y0 * vw.tiles_x);
-                const uint32_t m = a.tmask ? a.tmask[i] : FULL;
-                tw.masked = m != FULL;  // then the rect has at most 32 tiles
-                tw.rest = m;
-                tw.inv_w = (65535u + (uint32_t)tw.w) / (uint32_t)tw.w;
-                if (FILL) key = a.dkey[i];
+                tw.init(vw.tile_base, vw.tiles_x, x0, y0, x1, a.tmask ? a.tmask[i] : FULL);
+                key = a.dkey[i];
             }
         }
         const uint32_t maxc = __reduce_max_sync(FULL, cnt);
@@ -145,16 +110,12 @@ __global__ __launch_bounds__(256) void k_bin_walk(BinArgs a) {
                 const uint32_t t = tw.next();
                 const uint32_t peers = __match_any_sync(am, t);
                 const int leader = __ffs(peers) - 1;
-                if (!FILL) {
-                    if (lane == leader) atomicAdd(&a.tile_cnt[t], (uint32_t)__popc(peers));
-                } else {
-                    uint32_t b = 0;
-                    if (lane == leader) b = atomicAdd(&a.cursor[t], (uint32_t)__popc(peers));
-                    b = __shfl_sync(peers, b, leader);
-                    const uint32_t slot = b + (uint32_t)__popc(peers & lt);
-                    a.bk_key[slot] = key;
-                    a.bk_id[slot] = (uint32_t)i;
-                }
+                uint32_t b = 0;
+                if (lane == leader) b = atomicAdd(&a.cursor[t], (uint32_t)__popc(peers));
+                b = __shfl_sync(peers, b, leader);
+                const uint32_t slot = b + (uint32_t)__popc(peers & lt);
+                a.bk_key[slot] = key;
+                a.bk_id[slot] = (uint32_t)i;
             }
         }
     }
@@ -556,15 +517,13 @@ int walk_blocks(int64_t inst_cap) {
 
 }  // namespace
 
-void launch_bin_count(const BinArgs &a, cudaStream_t s) {
-    cudaMemsetAsync(a.tile_cnt, 0, sizeof(uint32_t) * std::max<uint32_t>(a.n_slots, 1), s);
-    k_bin_walk<false><<<walk_blocks(a.inst_cap), 256, 0, s>>>(a);
+void launch_bin_scan(const BinArgs &a, cudaStream_t s) {
     k_bin_scan<<<1, 1024, 0, s>>>(a);
-    note_launches(2);
+    note_launches(1);
 }
 
 void launch_bin_fill(const BinArgs &a, cudaStream_t s) {
-    k_bin_walk<true><<<walk_blocks(a.inst_cap), 256, 0, s>>>(a);
+    k_bin_fill<<<walk_blocks(a.inst_cap), 256, 0, s>>>(a);
     note_launches(1);
 }
 

@@ -10,6 +10,7 @@
 
 #include <algorithm>
 
+#include "bins.cuh"
 #include "common.cuh"
 #include "internal.h"
 
@@ -176,14 +177,15 @@ __device__ uint32_t tight_mask(float mx, float my, float a, float b, float c, fl
 // and returns the tiles kept (0 culls).  Whole rects above 32 tiles.
 __device__ __forceinline__ int tighten(const ProjectOut &o, uint64_t i, int nt, float mx, float my, float a,
                                        float b, float c, float op, float alpha_min, int x0, int y0, int x1, int y1,
-                                       int W, int H) {
+                                       int W, int H, uint32_t &mask) {
     if (nt > TIGHT_MAX_TILES) {
-        o.tmask[i] = 0xffffffffu;
+        mask = 0xffffffffu;
+        o.tmask[i] = mask;
         return nt;
     }
-    const uint32_t m = tight_mask(mx, my, a, b, c, op, alpha_min, x0, y0, x1, y1, W, H);
-    o.tmask[i] = m;
-    return __popc(m);
+    mask = tight_mask(mx, my, a, b, c, op, alpha_min, x0, y0, x1, y1, W, H);
+    o.tmask[i] = mask;
+    return __popc(mask);
 }
 
 // Copy the view table to device memory for the kernels after this one.
@@ -207,12 +209,17 @@ __global__ __launch_bounds__(256, 4) void k_project(const float4 *__restrict__ x
     const int tiles_x = view.tiles_x, tiles_y = view.tiles_y;
     const uint64_t n = *n_dev;
     uint32_t tmin = CULLED_KEY, tmax = 0u, tn = 0u;
-    for (uint64_t gi = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; gi < n;
-         gi += (uint64_t)gridDim.x * blockDim.x) {
+    // warps stride over 32-Gaussian chunks (the tile count is warp-synchronous)
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t g0 = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); g0 < n; g0 += stride) {
+    const uint64_t gi = g0 + (threadIdx.x & 31);
     const uint64_t i = (uint64_t)blockIdx.y * n + gi;
     bool vis = false;
     uint32_t key = CULLED_KEY;
-    {
+    uint32_t cnt = 0;
+    TileWalk tw;
+    tw.clear();
+    if (gi < n) {
     const float4 g = xyzo[gi];
     const float *R = cam.R;
     const float px = fadd(fadd(fadd(fmul(R[0], g.x), fmul(R[1], g.y)), fmul(R[2], g.z)), cam.t[0]);
@@ -260,9 +267,10 @@ __global__ __launch_bounds__(256, 4) void k_project(const float4 *__restrict__ x
             int x0, y0, x1, y1;
             int nt = tile_rect(mx, my, r, tiles_x, tiles_y, x0, y0, x1, y1);
             const float ca_ = fdiv(c, det), cb_ = -fdiv(b, det), cc_ = fdiv(a, det);
+            uint32_t mask = 0xffffffffu;
             if (nt > 0 && (par.flags & TSPLAT_RENDER_TIGHT))
                 nt = tighten(o, i, nt, mx, my, ca_, cb_, cc_, g.w, par.alpha_min, x0, y0, x1, y1, cam.width,
-                             cam.height);
+                             cam.height, mask);
             if (nt <= 0) {
                 vis = false;
             } else {
@@ -275,6 +283,8 @@ __global__ __launch_bounds__(256, 4) void k_project(const float4 *__restrict__ x
                 key = __float_as_uint(pz);
                 o.dkey[i] = key;
                 o.radius[i] = r;
+                cnt = (uint32_t)nt;
+                tw.init(view.tile_base, tiles_x, x0, y0, x1, mask);
             }
         }
     }
@@ -286,6 +296,7 @@ __global__ __launch_bounds__(256, 4) void k_project(const float4 *__restrict__ x
         ++tn;
     }
     }
+    warp_count_tiles(tw, cnt, o.tile_cnt);
     }
     account_n(o, tmin, tmax, tn);
 }
@@ -304,6 +315,9 @@ __global__ __launch_bounds__(256) void k_prepare_2d(uint64_t n, const float *__r
     const bool active = i < n;
     bool vis = false;
     uint32_t key = CULLED_KEY;
+    uint32_t cnt = 0;
+    TileWalk tw;
+    tw.clear();
     if (active) {
     const int32_t ri = radius[i];
     const float z = depth[i];
@@ -314,9 +328,10 @@ __global__ __launch_bounds__(256) void k_prepare_2d(uint64_t n, const float *__r
         int x0, y0, x1, y1;
         int nt = tile_rect(mx, my, r, tiles_x, tiles_y, x0, y0, x1, y1);
         const float a = conic[3 * i], b = conic[3 * i + 1], c = conic[3 * i + 2];
+        uint32_t mask = 0xffffffffu;
         if (nt > 0 && (par.flags & TSPLAT_RENDER_TIGHT))
             nt = tighten(o, i, nt, mx, my, a, b, c, opac[i], par.alpha_min, x0, y0, x1, y1, vb.v[0].cam.width,
-                         vb.v[0].cam.height);
+                         vb.v[0].cam.height, mask);
         if (nt <= 0) {
             vis = false;
         } else {
@@ -329,10 +344,13 @@ __global__ __launch_bounds__(256) void k_prepare_2d(uint64_t n, const float *__r
             key = __float_as_uint(z);
             o.dkey[i] = key;
             o.radius[i] = r;
+            cnt = (uint32_t)nt;
+            tw.init(0u, tiles_x, x0, y0, x1, mask);
         }
     }
     if (!vis) write_culled(o, i);
     }
+    warp_count_tiles(tw, cnt, o.tile_cnt);
     account(o, vis, key);
 }
 
@@ -495,6 +513,7 @@ void launch_project(const float4 *xyzo, const float4 *cova, const float2 *covb, 
     // about four waves of 256-thread blocks over all views
     const int64_t gx = std::max<int64_t>(1, std::min<int64_t>((n_cap + 255) / 256, (int64_t)sms * 32 / vb.n_views));
     const dim3 grid((unsigned)gx, (unsigned)vb.n_views);
+    cudaMemsetAsync(o.tile_cnt, 0, sizeof(uint32_t) * std::max<uint32_t>(vb.n_tiles_total, 1u), s);
     k_project<<<grid, 256, 0, s>>>(xyzo, cova, covb, n_dev, vb, views_dev, table_on_device ? 1 : 0, par, o);
     note_launches(1);
 }
@@ -503,6 +522,7 @@ void launch_prepare_2d(int64_t n, const float *mean2d, const float *conic, const
                        const float *depth, const int32_t *radius, const tsplat_render_params &par,
                        const ViewBatch &vb, RenderView *views_dev, const ProjectOut &o, cudaStream_t s) {
     const unsigned blocks = (unsigned)std::max<int64_t>(1, (n + 255) / 256);
+    cudaMemsetAsync(o.tile_cnt, 0, sizeof(uint32_t) * std::max<uint32_t>(vb.n_tiles_total, 1u), s);
     k_prepare_2d<<<blocks, 256, 0, s>>>((uint64_t)n, mean2d, conic, opac, depth, radius, par, vb, views_dev, o);
     note_launches(1);
 }
