@@ -257,7 +257,7 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
                 const float q = gauss_q(dx, dy, h0.z, h0.w, h1.x);
                 bool contrib = false;
                 float al = 0.0f, raw = 0.0f;
-                if (k < lastk && q <= 0.0f) {
+                if (k < lastk) {  // the forward's tests, in the same order
                     const float e2 = fmaf(q, LOG2E, h1.y);
                     if (e2 >= a.log2_alpha_min) {
                         raw = ex2(e2);

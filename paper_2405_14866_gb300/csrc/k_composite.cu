@@ -326,11 +326,14 @@ __global__ __launch_bounds__(NTHR, 2) void k_composite(CompositeArgs a) {
                         const float q = gauss_q(fpx - h0.x, fpy - h0.y, h0.z, h0.w, h1.x);
                         const float e2 = fmaf(q, LOG2E, h1.y);
                         const float al = fminf(amax, ex2(e2));
-                        const bool ok = !done & (q <= 0.0f) & (e2 >= l2min);
-                        const float Tn = T * (1.0f - al);
+                        // (q <= 0 for a positive-definite conic; its rounding near the
+                        // centre is one of the oracle's ambiguous decisions)
+                        const bool ok = !done & (e2 >= l2min);
+                        const float wr = al * T;
+                        const float Tn = T - wr;
                         const bool stop = ok & (Tn < tmin);
                         const bool blend = ok & !stop;
-                        w2[h] = blend ? al * T : 0.0f;
+                        w2[h] = blend ? wr : 0.0f;
                         T = blend ? Tn : T;
                         if (SAVE) last = blend ? (uint32_t)(base + j + 1) : last;
                         done = done | stop;
