@@ -34,7 +34,6 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "views/s & p99 ms, 2M-Gaussian 1024² 32-ch feature splat; % of HBM roofline"
-STAGES = ("project", "depth_sort", "scan_emit", "tile_sort", "ranges", "composite")
 
 
 def parse():

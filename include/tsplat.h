@@ -470,8 +470,9 @@ tsplat_status tsplat_server_reset_stats(tsplat_server *s);
 /* Mean stage durations, in milliseconds, of the renders on `ctx` that used
  * TSPLAT_RENDER_PROFILE since the previous call (at most the last 256),
  * measured with CUDA events on the render's stream; synchronizes and
- * resets.  ms[0..5] = project (A2), depth sort, scan + emission (A3/A4),
- * tile sort (A5), ranges (A6), composite (A7); *n_out = 6. */
+ * resets.  ms[0..4] = projection with the per-tile pair counts (A2/A3),
+ * scan into ranges and tile order (A4/A6), bucket fill (A4), bucket sort
+ * (A5), composite (A7); *n_out = 5. */
 tsplat_status tsplat_ctx_timings(tsplat_ctx *ctx, float *ms, int32_t capacity, int32_t *n_out);
 
 /* Number of kernel launches the library has issued in this process. */

@@ -18,7 +18,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CAPACITY", 4: "TIMEOUT"
                 6: "NOT_READY", 7: "UNSUPPORTED"}
 F32, BF16 = 0, 1
 RENDER_ASYNC, RENDER_SAVE, RENDER_PROFILE, RENDER_TIGHT = 1, 2, 4, 8
-STAGES = ("project", "count_scan", "fill", "tile_order", "bucket_sort", "composite")
+STAGES = ("project", "scan_order", "fill", "bucket_sort", "composite")
 EXPORT = {"rect": 0, "depthkey": 1, "mean2d": 2, "conic": 3, "radius": 4, "pairs": 5, "ranges": 6,
           "tfinal": 7, "last": 8}
 

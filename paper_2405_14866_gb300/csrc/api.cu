@@ -125,7 +125,7 @@ struct tsplat_ctx {
     float alpha_max = 0, alpha_min = 0;
     // stage events of profiled renders (TSPLAT_RENDER_PROFILE): a ring of
     // the last RING renders, averaged and reset by tsplat_ctx_timings
-    static constexpr int N_EV = 7, RING = 256;
+    static constexpr int N_EV = 6, RING = 256;
     cudaEvent_t ev[RING][N_EV] = {};
     int64_t n_prof = 0;
 };
@@ -467,6 +467,7 @@ static tsplat_status render_tail(tsplat_ctx *c, int64_t n_cap, const uint32_t *n
     bn.p_dev = sm + SM_P;
     bn.p_eff = sm + SM_PEFF;
     bn.tile_order = c->torder.as<uint32_t>();
+    bn.tile_order_out = c->torder.as<uint32_t>();
     bn.tile_ctr = sm + SM_BINCTR;
     bn.status = sm + SM_STATUS;
     launch_bin_scan(bn, s);
@@ -488,11 +489,9 @@ static tsplat_status render_tail(tsplat_ctx *c, int64_t n_cap, const uint32_t *n
     bn.ids_out = c->pv1.as<uint32_t>();  // the scratch of a bucket ends before its output is written
     launch_bin_fill(bn, s);
     TRY(mark(c, prof, 3, s));
-    launch_tile_order(c->ranges.as<uint2>(), c->views.as<RenderView>(), vb.n_views, n_tiles, c->torder.as<uint32_t>(), s);
-    TRY(mark(c, prof, 4, s));
     launch_bin_sort(bn, s);
     TRY(check_launch("render: bins"));
-    TRY(mark(c, prof, 5, s));
+    TRY(mark(c, prof, 4, s));
     const uint32_t *ids_sorted = bn.ids_out;
 
     CompositeArgs ca;
@@ -517,7 +516,7 @@ static tsplat_status render_tail(tsplat_ctx *c, int64_t n_cap, const uint32_t *n
     ca.tile_order = c->torder.as<uint32_t>();
     launch_composite(ca, s);
     TRY(check_launch("render: composite"));
-    TRY(mark(c, prof, 6, s));
+    TRY(mark(c, prof, 5, s));
 
     c->stream = s;
     c->n_cap = n_cap;

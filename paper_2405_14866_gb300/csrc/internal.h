@@ -135,7 +135,8 @@ struct BinArgs {
     uint32_t *bk_key, *bk_id;    // [p_cap] buckets: depth keys, instance ids
     uint32_t *tmp_key, *tmp_id;  // [p_cap] scratch of buckets too large for shared memory
     uint32_t *ids_out;           // [p_cap] instance ids in (tile, depth, id) order
-    const uint32_t *tile_order;  // [n_slots]
+    const uint32_t *tile_order;  // [n_slots] order the sort takes the tiles in
+    uint32_t *tile_order_out;    // the same array, written by the scan
     uint32_t *tile_ctr;          // persistent-sort tile counter
     uint32_t *status;            // TSPLAT_ERR_CAPACITY when P > p_cap
 };
@@ -259,11 +260,6 @@ void launch_build_backward(const LiftBwdArgs &a, cudaStream_t s);
 // depth / id = W*H outputs (id may be NULL).
 void launch_zbuffer(const float4 *xyzo, const uint32_t *n_dev, int64_t n_cap, const tsplat_camera &cam,
                     unsigned long long *keys, float *depth, int32_t *id, cudaStream_t s);
-
-// Composite tile order: n_slots tiles (the launch's tile count), longest
-// pair lists first; slots beyond the views' tiles last.
-void launch_tile_order(const uint2 *ranges, const RenderView *views, int n_views, int n_slots, uint32_t *order,
-                       cudaStream_t s);
 
 // small utilities
 void launch_fill_u32(uint32_t *p, uint32_t v, int64_t n, cudaStream_t s);

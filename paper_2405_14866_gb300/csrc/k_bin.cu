@@ -8,12 +8,12 @@
 //                         tiles; lanes of a warp that meet the same tile add
 //                         their count with one atomic (match_any);
 //   2. k_bin_scan         one block: exclusive scan of the tile counts: each
-//                         tile's range and fill cursor, and the total P;
+//                         tile's range and fill cursor, and the total P; then
+//                         the tile order, longest lists first;
 //   3. k_bin_fill         the same walk; each (warp, tile) group reserves a run
 //                         of its tile's bucket with one atomic and writes
 //                         (depth key, instance id) into it;
-//   4. k_tile_order       tiles longest list first;
-//   5. k_bin_sort         persistent blocks take tiles in that order and sort
+//   4. k_bin_sort         persistent blocks take tiles in that order and sort
 //                         each bucket by (depth key, id): an LSD radix sort
 //                         with 8-bit digits over the bits in which the tile's
 //                         depth keys differ, then runs of equal depth keys
@@ -121,6 +121,39 @@ __global__ __launch_bounds__(256) void k_bin_fill(BinArgs a) {
     }
 }
 
+// Step 4, by the scan's block: tile order, longest lists first
+// (largest-processing-time-first scheduling shortens the tail of the
+// persistent kernels).  Tiles are bucketed by 4 log2(pair count); tiles with
+// no pairs follow, then the slots beyond the views' T tiles (graph replays
+// size the launch for their largest batch).  The order within a bucket
+// depends on atomics, which changes no output: every tile is processed
+// independently.
+constexpr int TO_BUCKETS = 64;
+__device__ __forceinline__ int order_bucket(const uint32_t *cnt, uint32_t t, uint32_t T) {
+    if (t >= T) return TO_BUCKETS + 1;  // not a tile of this batch
+    const uint32_t c = cnt[t];
+    if (c == 0) return TO_BUCKETS;
+    const int lg = (int)(4.0f * __log2f((float)c));
+    return TO_BUCKETS - 1 - min(TO_BUCKETS - 1, max(0, lg));  // descending count
+}
+
+__device__ void tile_order_block(const uint32_t *cnt, uint32_t T, uint32_t n_slots, uint32_t *order) {
+    __shared__ uint32_t bc[TO_BUCKETS + 2], boff[TO_BUCKETS + 2];
+    for (int i = threadIdx.x; i < TO_BUCKETS + 2; i += blockDim.x) bc[i] = 0;
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < n_slots; t += blockDim.x) atomicAdd(&bc[order_bucket(cnt, t, T)], 1u);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int b = 0; b < TO_BUCKETS + 2; ++b) {
+            boff[b] = run;
+            run += bc[b];
+        }
+    }
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < n_slots; t += blockDim.x) order[atomicAdd(&boff[order_bucket(cnt, t, T)], 1u)] = t;
+}
+
 // Step 2 (one block of 1024): ranges ([0, 0) for an empty tile), fill
 // cursors and P.  Tile slots past the views' tiles (a graph replayed with
 // smaller views) are empty.  P saturates at 2^32 - 1, which no pair buffer
@@ -143,6 +176,7 @@ __global__ __launch_bounds__(1024) void k_bin_scan(BinArgs a) {
         run += c;
     }
     if (threadIdx.x == 0) *a.p_dev = (uint32_t)min(tot, 0xffffffffull);
+    tile_order_block(a.tile_cnt, T, a.n_slots, a.tile_order_out);
 }
 
 // ---------------------------------------------------------------- step 5
@@ -451,40 +485,6 @@ __global__ __launch_bounds__(BS_THREADS, 2) void k_bin_sort(BinArgs a) {
     }
 }
 
-// Order in which the persistent kernels take the tiles: longest lists first
-// (largest-processing-time-first scheduling shortens the tail of the grid).
-// One block buckets the tiles by 4 log2(pair count); tiles with no pairs
-// follow, then tile slots beyond the views' tile count (graph replays size
-// the launch for their largest batch).  The order within a bucket depends
-// on atomics, which changes no output: every tile is processed independently.
-constexpr int TO_BUCKETS = 64;
-__global__ __launch_bounds__(1024) void k_tile_order(const uint2 *ranges, const RenderView *views, int n_views,
-                                                     uint32_t n_slots, uint32_t *order) {
-    __shared__ uint32_t cnt[TO_BUCKETS + 2], off[TO_BUCKETS + 2];
-    const RenderView &lv = views[n_views - 1];
-    const uint32_t n_tiles = min(n_slots, lv.tile_base + (uint32_t)(lv.tiles_x * lv.tiles_y));
-    for (int i = threadIdx.x; i < TO_BUCKETS + 2; i += blockDim.x) cnt[i] = 0;
-    __syncthreads();
-    auto bucket = [&](uint32_t t) -> int {
-        if (t >= n_tiles) return TO_BUCKETS + 1;  // not a tile of this batch
-        const uint32_t c = ranges[t].y - ranges[t].x;
-        if (c == 0) return TO_BUCKETS;
-        const int lg = (int)(4.0f * __log2f((float)c));
-        return TO_BUCKETS - 1 - min(TO_BUCKETS - 1, max(0, lg));  // descending count
-    };
-    for (uint32_t t = threadIdx.x; t < n_slots; t += blockDim.x) atomicAdd(&cnt[bucket(t)], 1u);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t run = 0;
-        for (int b = 0; b < TO_BUCKETS + 2; ++b) {
-            off[b] = run;
-            run += cnt[b];
-        }
-    }
-    __syncthreads();
-    for (uint32_t t = threadIdx.x; t < n_slots; t += blockDim.x) order[atomicAdd(&off[bucket(t)], 1u)] = t;
-}
-
 __global__ void k_fill_u32(uint32_t *p, uint32_t v, uint64_t n) {
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) p[i] = v;
@@ -544,13 +544,6 @@ void launch_bin_sort(const BinArgs &a, cudaStream_t s) {
     const int grid = bin_sort_setup();
     cudaMemsetAsync(a.tile_ctr, 0, sizeof(uint32_t), s);
     k_bin_sort<<<std::min(grid, (int)std::max<uint32_t>(a.n_slots, 1)), BS_THREADS, sizeof(BinSortSmem), s>>>(a);
-    note_launches(1);
-}
-
-void launch_tile_order(const uint2 *ranges, const RenderView *views, int n_views, int n_slots, uint32_t *order,
-                       cudaStream_t s) {
-    if (n_slots <= 0) return;
-    k_tile_order<<<1, 1024, 0, s>>>(ranges, views, n_views, (uint32_t)n_slots, order);
     note_launches(1);
 }
 
