@@ -191,6 +191,7 @@ struct BinSortSmem {
     uint32_t wcnt[BS_WARPS][256];  // per warp and digit: counts, then offsets within the digit
     uint32_t dbase[256];           // first position of each digit
     uint32_t run[256];             // global path: next position of each digit
+    uint32_t slab[256];            // large buckets: end of each depth slab
     uint32_t sw[BS_WARPS];
     uint32_t red[4];
     uint32_t tile, flag;
@@ -396,6 +397,84 @@ __device__ bool fix_ties(BinSortSmem &S, const E &e, uint32_t n) {
     return longrun;
 }
 
+// Sorts n <= BS_MAX entries (keys k, ids v in global memory) by (key, id)
+// in shared memory and writes the ids to out (which may alias v).
+__device__ void sort_range_smem(BinSortSmem &S, const uint32_t *k, const uint32_t *v, uint32_t n, uint32_t *out) {
+    const int tid = threadIdx.x;
+    if (n <= 1) {
+        if (n == 1 && tid == 0) out[0] = v[0];
+        __syncthreads();
+        return;
+    }
+    uint32_t kmn = FULL, kmx = 0u, vmn = FULL, vmx = 0u;
+    for (uint32_t j = tid; j < n; j += BS_THREADS) {
+        const uint32_t kj = k[j], vj = v[j];
+        S.kv[1][j] = make_uint2(kj, vj);  // staged; remapped into kv[0] below
+        kmn = min(kmn, kj); kmx = max(kmx, kj); vmn = min(vmn, vj); vmx = max(vmx, vj);
+    }
+    block_minmax(S, kmn, kmx, vmn, vmx);
+    const uint32_t kmin = S.red[0], vmin = S.red[2];
+    const int kb = sig_bits(kmin, S.red[1]), vb = sig_bits(vmin, S.red[3]);
+    const int m = (int)n;
+    for (int j = tid; j < m; j += BS_THREADS) {
+        const uint2 e = S.kv[1][j];
+        S.kv[0][j] = make_uint2(e.x - kmin, e.y);
+    }
+    __syncthreads();
+    int src = 0;
+    for (int sh = 0; sh < kb; sh += 8) {
+        smem_pass_any(S, src, m, false, vmin, sh);
+        src ^= 1;
+    }
+    // runs of equal depth keys: ids in order (short runs in place)
+    if (fix_ties(S, SmemEntries{S.kv[src]}, n)) {  // a long run: the full (depth key, id) order
+        for (int sh = 0; sh < vb; sh += 8) {
+            smem_pass_any(S, src, m, true, vmin, sh);
+            src ^= 1;
+        }
+        for (int sh = 0; sh < kb; sh += 8) {
+            smem_pass_any(S, src, m, false, vmin, sh);
+            src ^= 1;
+        }
+    }
+    for (int j = tid; j < m; j += BS_THREADS) out[j] = S.kv[src][j].y;
+    __syncthreads();
+}
+
+// Sorts n entries by radix passes over global memory: (k0, v0) with the
+// scratch (k1, v1); ids to out (which may alias v0 or v1).
+__device__ void sort_range_global(BinSortSmem &S, uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, uint32_t n,
+                                  uint32_t *out) {
+    const int tid = threadIdx.x;
+    uint32_t kmn = FULL, kmx = 0u, vmn = FULL, vmx = 0u;
+    for (uint32_t j = tid; j < n; j += BS_THREADS) {
+        const uint32_t kj = k0[j], vj = v0[j];
+        kmn = min(kmn, kj); kmx = max(kmx, kj); vmn = min(vmn, vj); vmx = max(vmx, vj);
+    }
+    block_minmax(S, kmn, kmx, vmn, vmx);
+    const uint32_t kmin = S.red[0], vmin = S.red[2];
+    const int kb = sig_bits(kmin, S.red[1]), vb = sig_bits(vmin, S.red[3]);
+    for (int sh = 0; sh < kb; sh += 8) {
+        global_pass(S, k0, v0, k1, v1, n, false, kmin, vmin, sh);
+        uint32_t *t = k0; k0 = k1; k1 = t;
+        t = v0; v0 = v1; v1 = t;
+    }
+    if (fix_ties(S, GlobalEntries{k0, v0}, n)) {  // a long run of equal depth keys: ids, then depth
+        for (int sh = 0; sh < vb; sh += 8) {
+            global_pass(S, k0, v0, k1, v1, n, true, kmin, vmin, sh);
+            uint32_t *t = k0; k0 = k1; k1 = t;
+            t = v0; v0 = v1; v1 = t;
+        }
+        for (int sh = 0; sh < kb; sh += 8) {
+            global_pass(S, k0, v0, k1, v1, n, false, kmin, vmin, sh);
+            uint32_t *t = k0; k0 = k1; k1 = t;
+            t = v0; v0 = v1; v1 = t;
+        }
+    }
+    for (uint32_t j = tid; j < n; j += BS_THREADS) out[j] = v0[j];  // the result is in (k0, v0)
+    __syncthreads();
+}
+
 __global__ __launch_bounds__(BS_THREADS, 2) void k_bin_sort(BinArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     BinSortSmem &S = *reinterpret_cast<BinSortSmem *>(smem_raw);
@@ -410,78 +489,44 @@ __global__ __launch_bounds__(BS_THREADS, 2) void k_bin_sort(BinArgs a) {
         const uint2 rg = a.ranges[a.tile_order[q]];
         const uint32_t first = rg.x, n = rg.y - rg.x;
         if (n == 0) continue;
-        const uint32_t *bk = a.bk_key + first, *bi = a.bk_id + first;
+        uint32_t *bk = a.bk_key + first, *bi = a.bk_id + first;
+        uint32_t *tk = a.tmp_key + first, *ti = a.tmp_id + first;
         uint32_t *out = a.ids_out + first;
-        if (n == 1) {
-            if (tid == 0) out[0] = bi[0];
+        if (n <= (uint32_t)BS_MAX) {
+            sort_range_smem(S, bk, bi, n, out);
             continue;
         }
-        uint32_t kmn = FULL, kmx = 0u, vmn = FULL, vmx = 0u;
-        if (n <= (uint32_t)BS_MAX) {
-            for (uint32_t j = tid; j < n; j += BS_THREADS) {
-                const uint32_t k = bk[j], v = bi[j];
-                S.kv[1][j] = make_uint2(k, v);  // staged; remapped into kv[0] below
-                kmn = min(kmn, k); kmx = max(kmx, k); vmn = min(vmn, v); vmx = max(vmx, v);
-            }
-            block_minmax(S, kmn, kmx, vmn, vmx);
-            const uint32_t kmin = S.red[0], vmin = S.red[2];
-            const int kb = sig_bits(kmin, S.red[1]), vb = sig_bits(vmin, S.red[3]);
-            const int m = (int)n;
-            for (int j = tid; j < m; j += BS_THREADS) {
-                const uint2 e = S.kv[1][j];
-                S.kv[0][j] = make_uint2(e.x - kmin, e.y);
-            }
-            __syncthreads();
-            int src = 0;
-            for (int sh = 0; sh < kb; sh += 8) {
-                smem_pass_any(S, src, m, false, vmin, sh);
-                src ^= 1;
-            }
-            // runs of equal depth keys: ids in order (short runs in place)
-            if (fix_ties(S, SmemEntries{S.kv[src]}, n)) {  // a long run: the full (depth key, id) order
-                for (int sh = 0; sh < vb; sh += 8) {
-                    smem_pass_any(S, src, m, true, vmin, sh);
-                    src ^= 1;
-                }
-                for (int sh = 0; sh < kb; sh += 8) {
-                    smem_pass_any(S, src, m, false, vmin, sh);
-                    src ^= 1;
-                }
-            }
-            for (int j = tid; j < m; j += BS_THREADS) out[j] = S.kv[src][j].y;
-            __syncthreads();
-        } else {
-            // beyond shared memory: the same passes over global memory, chunk by chunk
-            for (uint32_t j = tid; j < n; j += BS_THREADS) {
-                const uint32_t k = bk[j], v = bi[j];
-                kmn = min(kmn, k); kmx = max(kmx, k); vmn = min(vmn, v); vmx = max(vmx, v);
-            }
-            block_minmax(S, kmn, kmx, vmn, vmx);
-            const uint32_t kmin = S.red[0], vmin = S.red[2];
-            const int kb = sig_bits(kmin, S.red[1]), vb = sig_bits(vmin, S.red[3]);
-            uint32_t *k0 = a.bk_key + first, *k1 = a.tmp_key + first;
-            uint32_t *v0 = a.bk_id + first, *v1 = a.tmp_id + first;
-            for (int sh = 0; sh < kb; sh += 8) {
-                global_pass(S, k0, v0, k1, v1, n, false, kmin, vmin, sh);
-                uint32_t *t = k0; k0 = k1; k1 = t;
-                t = v0; v0 = v1; v1 = t;
-            }
-            if (fix_ties(S, GlobalEntries{k0, v0}, n)) {  // a long run of equal depth keys: ids, then depth
-                for (int sh = 0; sh < vb; sh += 8) {
-                    global_pass(S, k0, v0, k1, v1, n, true, kmin, vmin, sh);
-                    uint32_t *t = k0; k0 = k1; k1 = t;
-                    t = v0; v0 = v1; v1 = t;
-                }
-                for (int sh = 0; sh < kb; sh += 8) {
-                    global_pass(S, k0, v0, k1, v1, n, false, kmin, vmin, sh);
-                    uint32_t *t = k0; k0 = k1; k1 = t;
-                    t = v0; v0 = v1; v1 = t;
-                }
-            }
-            // the result is in (k0, v0); the output region may be v0 itself
-            for (uint32_t j = tid; j < n; j += BS_THREADS) out[j] = v0[j];
-            __syncthreads();
+        // A bucket beyond shared memory: one pass over global memory on the
+        // highest significant digit splits it into depth slabs; runs of
+        // consecutive slabs of at most BS_MAX entries are then sorted in
+        // shared memory, and a slab larger than that by global passes.
+        uint32_t kmn = FULL, kmx = 0u;
+        for (uint32_t j = tid; j < n; j += BS_THREADS) {
+            const uint32_t kj = bk[j];
+            kmn = min(kmn, kj); kmx = max(kmx, kj);
         }
+        block_minmax(S, kmn, kmx, 0u, 0u);
+        const uint32_t kmin = S.red[0];
+        const int kb = sig_bits(kmin, S.red[1]);
+        if (kb == 0) {  // one depth key: the id order, by global passes
+            sort_range_global(S, bk, bi, tk, ti, n, out);
+            continue;
+        }
+        global_pass(S, bk, bi, tk, ti, n, false, kmin, 0u, ((kb - 1) / 8) * 8);
+        S.slab[tid] = S.run[tid];  // end of each slab (the passes below reuse S.run)
+        __syncthreads();
+        uint32_t c0 = 0;  // start of the pending run of slabs (the same in every thread)
+        for (int d = 0; d < 256; ++d) {
+            const uint32_t beg = d ? S.slab[d - 1] : 0u, end = S.slab[d];
+            if (end - c0 <= (uint32_t)BS_MAX) continue;
+            if (beg > c0) sort_range_smem(S, tk + c0, ti + c0, beg - c0, out + c0);
+            c0 = beg;
+            if (end - beg > (uint32_t)BS_MAX) {
+                sort_range_global(S, tk + beg, ti + beg, bk + beg, bi + beg, end - beg, out + beg);
+                c0 = end;
+            }
+        }
+        if (n > c0) sort_range_smem(S, tk + c0, ti + c0, n - c0, out + c0);
     }
 }
 

@@ -1,9 +1,10 @@
 """Edge cases of the render path on the GPU against the oracle.
 
-- Every Gaussian at exactly the same depth: the depth sort has no digit to
-  sort on, so the (tile, depth, id) order is the emission order by id, and
-  the tile sort's stability alone keeps it; and two interleaved depths
-  (heavy ties in one digit pass).  Pairs and ranges bit-exact.
+- Every Gaussian at exactly the same depth: each bucket's order is the id
+  order alone (one long run of equal keys); and two interleaved depths
+  (heavy ties).  Pairs and ranges bit-exact.
+- Buckets larger than the shared-memory sort: the depth-slab path, a slab
+  beyond shared memory, and a bucket of a single depth.
 - Zero covariances (the footprint is the low-pass filter alone).
 - Non-finite depths and scales: culled by the projection as in the oracle.
 - Limits: channel counts outside [1, 64], batches beyond 8 views.
@@ -103,3 +104,30 @@ def test_limits_are_rejected():
     with pytest.raises(L.TsplatError) as e:
         api.Context().render_batch(g, cams)
     assert e.value.status == 1
+
+
+@pytest.mark.parametrize("mix", ["spread", "one_slab_heavy", "all_equal"])
+def test_buckets_beyond_shared_memory(mix):
+    """15 K Gaussians on a few tiles: buckets larger than the shared-memory
+    sort take the depth-slab path; a slab larger than shared memory (here a
+    run of equal depths) and a bucket of one depth take global passes.
+    Pairs and ranges bit-exact."""
+    rng = np.random.default_rng(71)
+    n = 15000
+    if mix == "spread":
+        z = rng.uniform(1.0, 2.0, n)
+    elif mix == "one_slab_heavy":
+        z = np.where(np.arange(n) % 3 == 0, rng.uniform(1.0, 2.0, n), 1.5)
+    else:
+        z = np.full(n, 1.5)
+    z = z.astype(np.float32)
+    xy = rng.normal(0.0, 0.004, size=(n, 2)) * z[:, None]
+    mean = np.concatenate([xy, z[:, None]], 1).astype(np.float32)
+    cov = np.zeros((n, 6), np.float32)
+    cov[:, 0] = cov[:, 3] = cov[:, 5] = (0.002 * z) ** 2
+    opac = rng.uniform(0.02, 0.2, n).astype(np.float32)
+    feat = rng.standard_normal((n, 2)).astype(np.float32)
+    cam = gen.make_camera(400.0, 64, 48, (0, 0, 0), np.eye(3), cx=40.0, cy=24.0)
+    bins = _check_bins_and_maps(O.Gaussians(mean, cov, opac, feat), cam)
+    counts = bins.ranges[:, 1].astype(np.int64) - bins.ranges[:, 0]
+    assert counts.max() > 6144
