@@ -15,6 +15,7 @@ namespace {
 
 constexpr int BT = 256;                             // threads per block
 constexpr int BI = BUILD_PIX_PER_BLOCK / BT;        // pixels per thread (4)
+static_assert(BI == 4, "k_build_count reads the block's pixels four at a time");
 constexpr uint32_t FULL = 0xffffffffu;
 
 // Blocks are laid out view by view: view v owns blocks [blk0, blk0 +
@@ -68,14 +69,30 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 // Pixels of a block are visited in 4 rounds of 256 consecutive pixels
 // (thread t takes pixel round * 256 + t).
 __global__ __launch_bounds__(BT) void k_build_count(BuildArgs a) {
+    // the block's 1024 pixels, 4 consecutive ones per thread (one 32-bit mask
+    // load where aligned); the same pixels the lift visits in its 4 rounds
     __shared__ uint32_t sw[BT / 32];
     const ViewDesc &vd = a.views[view_of_block(a, blockIdx.x)];
-    const int64_t base = ((int64_t)blockIdx.x - vd.blk0) * BUILD_PIX_PER_BLOCK + threadIdx.x;
+    const int64_t hw = (int64_t)vd.H * vd.W;
+    const int64_t p0 = ((int64_t)blockIdx.x - vd.blk0) * BUILD_PIX_PER_BLOCK + 4 * (int64_t)threadIdx.x;
     uint32_t c = 0;
-    for (int r = 0; r < BI; ++r) c += is_fg(vd, base + (int64_t)r * BT) ? 1u : 0u;
-    uint32_t tot;
-    block_excl_scan<BT / 32>(c, sw, tot);
-    if (threadIdx.x == 0) a.blk_cnt[blockIdx.x] = tot;
+    if (!vd.mask) {
+        c = (uint32_t)max((int64_t)0, min((int64_t)4, hw - p0));
+    } else if (p0 + 3 < hw && (reinterpret_cast<uintptr_t>(vd.mask + p0) & 3u) == 0) {
+        const uint32_t w = *reinterpret_cast<const uint32_t *>(vd.mask + p0);
+        c = (uint32_t)((w & 0xffu) != 0) + (uint32_t)((w & 0xff00u) != 0) + (uint32_t)((w & 0xff0000u) != 0) +
+            (uint32_t)((w >> 24) != 0);
+    } else {
+        for (int k = 0; k < 4; ++k) c += (p0 + k < hw && vd.mask[p0 + k] != 0) ? 1u : 0u;
+    }
+    c = __reduce_add_sync(FULL, c);
+    if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < BT / 32; ++w) t += sw[w];
+        a.blk_cnt[blockIdx.x] = t;
+    }
 }
 
 __global__ __launch_bounds__(1024) void k_build_scan(BuildArgs a) {
