@@ -106,7 +106,7 @@ struct tsplat_ctx {
     DBuf ranges, tfinal, last, views;
     DBuf zkeys;  // point z-buffer scratch
     DBuf torder; // composite tile order
-    // small words: kminmax[2], n_vis, npass, p_dev, p_eff, status, n_dev, totals[4*256]
+    // small words (SM_*): visible count, P, effective P, status, tile and unit counters, N
     DBuf small;
     uint32_t *host_small = nullptr;  // pinned mirror
     int64_t p_cap = 0;
@@ -131,7 +131,7 @@ struct tsplat_ctx {
 };
 
 namespace {
-enum { SM_KMIN = 0, SM_KMAX = 1, SM_NVIS = 2, SM_P = 4, SM_PEFF = 5, SM_STATUS = 6, SM_TILECTR = 7,
+enum { SM_NVIS = 2, SM_P = 4, SM_PEFF = 5, SM_STATUS = 6, SM_TILECTR = 7,
        SM_N = 8, SM_NINST = 9, SM_BINCTR = 10, SM_BWDCTR = 14, SM_WORDS = 16 };
 uint32_t *small_ptr(tsplat_ctx *c, int w) { return c->small.as<uint32_t>() + w; }
 }  // namespace
@@ -566,15 +566,13 @@ static ProjectOut project_out(tsplat_ctx *c) {
     o.tile_cnt = c->tcnt.as<uint32_t>();
     o.dkey = c->dkey.as<uint32_t>();
     o.radius = c->radius.as<float>();
-    o.kminmax = small_ptr(c, SM_KMIN);
     o.n_vis = small_ptr(c, SM_NVIS);
     return o;
 }
 
 static void init_small(tsplat_ctx *c, cudaStream_t s) {
     uint32_t *sm = c->small.as<uint32_t>();
-    launch_fill_u32(sm + SM_KMIN, CULLED_KEY, 1, s);
-    cudaMemsetAsync(sm + SM_KMAX, 0, sizeof(uint32_t) * 7, s);  // kmax, n_vis, (unused), P, P_eff, status, tile counter
+    cudaMemsetAsync(sm + SM_NVIS, 0, sizeof(uint32_t) * 6, s);  // n_vis, (unused), P, P_eff, status, tile counter
 }
 
 tsplat_status tsplat_render(const tsplat_gaussians *g, const tsplat_camera *cam, const tsplat_render_params *params,

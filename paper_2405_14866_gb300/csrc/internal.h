@@ -93,7 +93,6 @@ struct ProjectOut {
     uint32_t *ntiles;   // [N]
     uint32_t *dkey;     // [N] depth key, CULLED_KEY when culled
     float *radius;      // [N]
-    uint32_t *kminmax;  // [2] min / max depth key of rendered Gaussians (pre-set to ~0u / 0)
     uint32_t *n_vis;    // [1] rendered Gaussians (pre-set to 0)
     uint32_t *tmask;    // [N] kept-tile masks (written with TSPLAT_RENDER_TIGHT)
     uint32_t *tile_cnt; // [tiles] pairs per tile (zeroed by the launcher, counted by the kernel)

@@ -54,39 +54,19 @@ __device__ __forceinline__ void write_culled(const ProjectOut &o, uint64_t i) {
     o.radius[i] = 0.0f;
 }
 
-// Rendered-Gaussian bookkeeping: depth-key range (for the radix sort's pass
-// count) and the visible count, reduced per block before one set of
-// atomics.  Called by every thread of a 256-thread block.
-__device__ __forceinline__ void account_n(const ProjectOut &o, uint32_t tmin, uint32_t tmax, uint32_t tn) {
-    __shared__ uint32_t s_min[8], s_max[8], s_n[8];
-    const uint32_t m = 0xffffffffu;
-    const uint32_t kmin = __reduce_min_sync(m, tmin);
-    const uint32_t kmax = __reduce_max_sync(m, tmax);
-    const uint32_t nv = __reduce_add_sync(m, tn);
+// Count of rendered Gaussians, reduced per block before one atomic.
+// Called by every thread of a 256-thread block.
+__device__ __forceinline__ void account_n(const ProjectOut &o, uint32_t tn) {
+    __shared__ uint32_t s_n[8];
+    const uint32_t nv = __reduce_add_sync(0xffffffffu, tn);
     const int warp = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0) {
-        s_min[warp] = kmin;
-        s_max[warp] = kmax;
-        s_n[warp] = nv;
-    }
+    if ((threadIdx.x & 31) == 0) s_n[warp] = nv;
     __syncthreads();
     if (threadIdx.x == 0) {
-        uint32_t bmin = CULLED_KEY, bmax = 0, bn = 0;
-        for (int w = 0; w < 8; ++w) {
-            bmin = min(bmin, s_min[w]);
-            bmax = max(bmax, s_max[w]);
-            bn += s_n[w];
-        }
-        if (bn) {
-            atomicMin(&o.kminmax[0], bmin);
-            atomicMax(&o.kminmax[1], bmax);
-            atomicAdd(o.n_vis, bn);
-        }
+        uint32_t bn = 0;
+        for (int w = 0; w < 8; ++w) bn += s_n[w];
+        if (bn) atomicAdd(o.n_vis, bn);
     }
-}
-
-__device__ __forceinline__ void account(const ProjectOut &o, bool vis, uint32_t key) {
-    account_n(o, vis ? key : CULLED_KEY, vis ? key : 0u, vis ? 1u : 0u);
 }
 
 // Tile rect from mean2d and radius, as the cited rasterizer defines it.
@@ -208,7 +188,7 @@ __global__ __launch_bounds__(256, 4) void k_project(const float4 *__restrict__ x
     const tsplat_camera &cam = view.cam;
     const int tiles_x = view.tiles_x, tiles_y = view.tiles_y;
     const uint64_t n = *n_dev;
-    uint32_t tmin = CULLED_KEY, tmax = 0u, tn = 0u;
+    uint32_t tn = 0u;
     // warps stride over 32-Gaussian chunks (the tile count is warp-synchronous)
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t g0 = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); g0 < n; g0 += stride) {
@@ -291,14 +271,12 @@ __global__ __launch_bounds__(256, 4) void k_project(const float4 *__restrict__ x
     if (!vis) {
         write_culled(o, i);
     } else {
-        tmin = min(tmin, key);
-        tmax = max(tmax, key);
         ++tn;
     }
     }
     warp_count_tiles(tw, cnt, o.tile_cnt);
     }
-    account_n(o, tmin, tmax, tn);
+    account_n(o, tn);
 }
 
 __global__ __launch_bounds__(256) void k_prepare_2d(uint64_t n, const float *__restrict__ mean2d,
@@ -351,7 +329,7 @@ __global__ __launch_bounds__(256) void k_prepare_2d(uint64_t n, const float *__r
     if (!vis) write_culled(o, i);
     }
     warp_count_tiles(tw, cnt, o.tile_cnt);
-    account(o, vis, key);
+    account_n(o, vis ? 1u : 0u);
 }
 
 // export of header fields: 2 = mean2d, 3 = conic
