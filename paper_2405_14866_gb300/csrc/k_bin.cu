@@ -182,7 +182,7 @@ __global__ __launch_bounds__(1024) void k_bin_scan(BinArgs a) {
 // ---------------------------------------------------------------- step 5
 constexpr int BS_THREADS = 256;                  // = the 256 digits: thread d owns digit d in the scans
 constexpr int BS_WARPS = BS_THREADS / 32;
-constexpr int BS_MAX = 6144;                     // bucket size sorted in shared memory
+constexpr int BS_MAX = 3840;                     // bucket size sorted in shared memory (3 blocks per SM)
 constexpr int BS_ROUNDS = BS_MAX / BS_THREADS;   // rounds of 32 per warp for a full chunk
 constexpr int BS_RUN_MAX = 32;                   // longest run of equal depth keys fixed in place
 
@@ -475,7 +475,7 @@ __device__ void sort_range_global(BinSortSmem &S, uint32_t *k0, uint32_t *v0, ui
     __syncthreads();
 }
 
-__global__ __launch_bounds__(BS_THREADS, 2) void k_bin_sort(BinArgs a) {
+__global__ __launch_bounds__(BS_THREADS, 3) void k_bin_sort(BinArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     BinSortSmem &S = *reinterpret_cast<BinSortSmem *>(smem_raw);
     const int tid = threadIdx.x;
