@@ -297,8 +297,8 @@ tsplat_status tsplat_render(const tsplat_gaussians *g, const tsplat_camera *cam,
 /* Several target views of the same Gaussians in one pass (the viewer's left
  * and right eye views, Sec. 4.2; several viewers in serving): 1 <= n_views
  * <= 8 cameras of any sizes.  Every view's Gaussians are projected in one
- * launch (each Gaussian read once), one depth sort covers all
- * (view, Gaussian) instances, the tile ids of all views form one space, and
+ * launch (each Gaussian read once), the tile ids of all views form one
+ * space binned by one bucket pass over all (view, Gaussian) instances, and
  * one compositing launch covers every tile.  out_feat[v] (C x H_v x W_v) and
  * out_alpha[v] (H_v x W_v, or out_alpha == NULL) are device buffers.  Each
  * view's result is bit-identical to tsplat_render of that view alone.

@@ -202,9 +202,9 @@ def test_build_from_bf16_feature_maps_equals_fp32_maps():
         assert torch.equal(a[k], b[k]), k
 
 
-def test_large_ragged_image_three_tile_digit_passes():
-    """4500 x 4500 target (282 x 282 = 79,524 tiles: 17-bit tile ids, so the
-    tile sort takes three digit passes; ragged last tile row and column):
+def test_large_ragged_image_many_tiles():
+    """4500 x 4500 target (282 x 282 = 79,524 tiles, more than one scan
+    block's 1024 threads cover one each; ragged last tile row and column):
     bins bit-exact, feature map on sampled tiles, including the ragged ones."""
     cam = gen.make_camera(2200.0, 4500, 4500, (0, 0, 0), np.eye(3))
     gs = gen.random_gaussians(21, 30000, 3, center=(0, 0, 1.6), spread=0.75, sigma_range=(0.0005, 0.004))
