@@ -277,7 +277,9 @@ tsplat_status tsplat_ctx_export(tsplat_ctx *ctx, int32_t what, void *dst, size_t
  *   (tile, bits of p_z, Gaussian id) -- identical to a stable sort of the
  *   64-bit key tile << 32 | bits(p_z) -- and per-tile ranges.
  * A7 composite, per pixel p, front to back over its tile's list:
- *   q = -1/2 (a dx^2 + c dy^2) - b dx dy, d = p - mean2D; q > 0 skips;
+ *   q = -1/2 (a dx^2 + c dy^2) - b dx dy, d = p - mean2D; q > 0 skips
+ *   (never, for the positive-definite conics projection keeps, but through
+ *   rounding at the centre; the kernels do not test it separately);
  *   alpha = min(alpha_max, o e^q); alpha < alpha_min skips;
  *   T' = T (1 - alpha); T' < t_min stops (that Gaussian is not blended);
  *   F += f alpha T; T = T'.   A = 1 - T at the end.
