@@ -121,7 +121,7 @@ __global__ __launch_bounds__(256) void k_bin_fill(BinArgs a) {
     }
 }
 
-// Step 4, by the scan's block: tile order, longest lists first
+// Step 4, inside the scan kernel: tile order, longest lists first
 // (largest-processing-time-first scheduling shortens the tail of the
 // persistent kernels).  Tiles are bucketed by 4 log2(pair count); tiles with
 // no pairs follow, then the slots beyond the views' T tiles (graph replays
@@ -129,54 +129,107 @@ __global__ __launch_bounds__(256) void k_bin_fill(BinArgs a) {
 // depends on atomics, which changes no output: every tile is processed
 // independently.
 constexpr int TO_BUCKETS = 64;
-__device__ __forceinline__ int order_bucket(const uint32_t *cnt, uint32_t t, uint32_t T) {
+__device__ __forceinline__ uint32_t order_bucket(uint32_t c, uint32_t t, uint32_t T) {
     if (t >= T) return TO_BUCKETS + 1;  // not a tile of this batch
-    const uint32_t c = cnt[t];
     if (c == 0) return TO_BUCKETS;
     const int lg = (int)(4.0f * __log2f((float)c));
     return TO_BUCKETS - 1 - min(TO_BUCKETS - 1, max(0, lg));  // descending count
 }
 
-__device__ void tile_order_block(const uint32_t *cnt, uint32_t T, uint32_t n_slots, uint32_t *order) {
-    __shared__ uint32_t bc[TO_BUCKETS + 2], boff[TO_BUCKETS + 2];
-    for (int i = threadIdx.x; i < TO_BUCKETS + 2; i += blockDim.x) bc[i] = 0;
+// Counts of 4 consecutive slots t0..t0+3 (0 past the batch's T tiles);
+// one 16-byte load when all four are tiles (t0 is a multiple of 4).
+__device__ __forceinline__ void load_counts4(const uint32_t *cnt, uint32_t t0, uint32_t T, uint32_t c[4]) {
+    if (t0 + 4 <= T) {
+        const uint4 v = *reinterpret_cast<const uint4 *>(cnt + t0);
+        c[0] = v.x; c[1] = v.y; c[2] = v.z; c[3] = v.w;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) c[k] = t0 + k < T ? cnt[t0 + k] : 0u;
+    }
+}
+
+// One block of 1024 threads, slots in chunks of 4096 (4 consecutive per
+// thread).  The loop over chunks scans the counts into ranges and cursors,
+// carrying the running total, and counts the tiles of each order bucket; a
+// second loop over the chunks places every slot at its bucket's cursor.
+// Each warp stages its 128 first offsets and counts in shared memory and
+// writes ranges and cursors lane by lane (whole 32-byte sectors: one SM's
+// store throughput bounds the kernel otherwise).
+__global__ __launch_bounds__(1024) void k_bin_scan(BinArgs a) {
+    __shared__ unsigned long long sw[32];
+    __shared__ uint32_t bc[TO_BUCKETS + 2];
+    __shared__ uint4 sf[1024], sc[1024];  // per thread: first offsets and counts of its 4 slots
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const RenderView &lv = a.views[a.n_views - 1];
+    const uint32_t T = min(a.n_slots, lv.tile_base + (uint32_t)(lv.tiles_x * lv.tiles_y));
+    if (threadIdx.x < TO_BUCKETS + 2) bc[threadIdx.x] = 0;
+    unsigned long long carry = 0;
+    for (uint32_t c0 = 0; c0 < a.n_slots; c0 += 4096u) {
+        const uint32_t t0 = c0 + 4u * threadIdx.x;
+        uint32_t c[4], f[4];
+        load_counts4(a.tile_cnt, t0, T, c);
+        const unsigned long long local = (unsigned long long)c[0] + c[1] + c[2] + c[3];
+        unsigned long long tot;
+        unsigned long long run = carry + block_excl_scan<32>(local, sw, tot);  // its barriers also order bc's zeroing
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            f[k] = (uint32_t)min(run, 0xffffffffull);
+            run += c[k];
+            if (t0 + k < a.n_slots) atomicAdd(&bc[order_bucket(c[k], t0 + k, T)], 1u);
+        }
+        sf[threadIdx.x] = make_uint4(f[0], f[1], f[2], f[3]);
+        sc[threadIdx.x] = make_uint4(c[0], c[1], c[2], c[3]);
+        __syncwarp();
+        const uint32_t *wf = reinterpret_cast<const uint32_t *>(sf + 32 * warp);
+        const uint32_t *wc = reinterpret_cast<const uint32_t *>(sc + 32 * warp);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t t = c0 + 128u * warp + 32u * j + lane;
+            if (t < a.n_slots) {
+                const uint32_t fj = wf[32 * j + lane], cj = wc[32 * j + lane];
+                const uint32_t ej = (uint32_t)min((unsigned long long)fj + cj, 0xffffffffull);  // saturates as the offsets do
+                a.ranges[t] = cj ? make_uint2(fj, ej) : make_uint2(0u, 0u);  // empty: [0, 0)
+                a.cursor[t] = fj;
+            }
+        }
+        __syncwarp();
+        carry += tot;
+    }
+    if (threadIdx.x == 0) *a.p_dev = (uint32_t)min(carry, 0xffffffffull);
     __syncthreads();
-    for (uint32_t t = threadIdx.x; t < n_slots; t += blockDim.x) atomicAdd(&bc[order_bucket(cnt, t, T)], 1u);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t run = 0;
-        for (int b = 0; b < TO_BUCKETS + 2; ++b) {
-            boff[b] = run;
-            run += bc[b];
+    // bucket offsets: warp 0 scans the TO_BUCKETS + 2 counts, 3 per lane
+    static_assert(TO_BUCKETS + 2 <= 96, "three buckets per lane");
+    if (threadIdx.x < 32) {
+        uint32_t v[3], sum = 0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int b = 3 * lane + k;
+            v[k] = b < TO_BUCKETS + 2 ? bc[b] : 0u;
+            sum += v[k];
+        }
+        uint32_t x = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, x, o);
+            if (lane >= o) x += y;
+        }
+        uint32_t off = x - sum;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int b = 3 * lane + k;
+            if (b < TO_BUCKETS + 2) bc[b] = off;
+            off += v[k];
         }
     }
     __syncthreads();
-    for (uint32_t t = threadIdx.x; t < n_slots; t += blockDim.x) order[atomicAdd(&boff[order_bucket(cnt, t, T)], 1u)] = t;
-}
-
-// Step 2 (one block of 1024): ranges ([0, 0) for an empty tile), fill
-// cursors and P.  Tile slots past the views' tiles (a graph replayed with
-// smaller views) are empty.  P saturates at 2^32 - 1, which no pair buffer
-// holds.
-__global__ __launch_bounds__(1024) void k_bin_scan(BinArgs a) {
-    __shared__ unsigned long long sw[32];
-    const RenderView &lv = a.views[a.n_views - 1];
-    const uint32_t T = min(a.n_slots, lv.tile_base + (uint32_t)(lv.tiles_x * lv.tiles_y));
-    const uint32_t per = (a.n_slots + 1023u) / 1024u;
-    const uint32_t t0 = min(threadIdx.x * per, a.n_slots), t1 = min(t0 + per, a.n_slots);
-    unsigned long long local = 0;
-    for (uint32_t t = t0; t < t1; ++t) local += t < T ? a.tile_cnt[t] : 0u;
-    unsigned long long tot;
-    unsigned long long run = block_excl_scan<32>(local, sw, tot);
-    for (uint32_t t = t0; t < t1; ++t) {
-        const uint32_t c = t < T ? a.tile_cnt[t] : 0u;
-        const uint32_t f = (uint32_t)min(run, 0xffffffffull);
-        a.ranges[t] = c ? make_uint2(f, (uint32_t)min(run + c, 0xffffffffull)) : make_uint2(0u, 0u);  // empty: [0, 0)
-        a.cursor[t] = f;
-        run += c;
+    for (uint32_t c0 = 0; c0 < a.n_slots; c0 += 4096u) {
+        const uint32_t t0 = c0 + 4u * threadIdx.x;
+        uint32_t c[4];
+        load_counts4(a.tile_cnt, t0, T, c);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (t0 + k < a.n_slots) a.tile_order_out[atomicAdd(&bc[order_bucket(c[k], t0 + k, T)], 1u)] = t0 + k;
     }
-    if (threadIdx.x == 0) *a.p_dev = (uint32_t)min(tot, 0xffffffffull);
-    tile_order_block(a.tile_cnt, T, a.n_slots, a.tile_order_out);
 }
 
 // ---------------------------------------------------------------- step 5
