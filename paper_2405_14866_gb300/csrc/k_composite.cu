@@ -48,6 +48,13 @@ struct Ring {
 
 constexpr uint32_t FINAL_TILE = 0xffffffffu;  // slot tile id of the last slot a CTA produces
 
+// Two consecutive survivors' records, interleaved so that one 64-bit
+// register holds a field of both: a = (mx0, mx1, my0, my1), b = (-a/2 x2,
+// -b x2), c = (-c/2 x2, log2 o x2).
+struct RecPair {
+    float4 a, b, c;
+};
+
 template <int CP, bool F32F>
 struct CompSmem {
     static constexpr int RING = Ring<CP>::N;
@@ -64,7 +71,7 @@ struct CompSmem {
     uint32_t base[RING];       // list position of the slot's first Gaussian
     int32_t done_seq[NCW];     // per consumer warp: sequence number of the last tile it is done with
     uint8_t list[NCW][SB];     // per consumer warp: slot indices of its surviving Gaussians, in order
-    Header wrec[NCW][SB];      // per consumer warp: the survivors' records, compacted
+    RecPair wpair[NCW][SB / 2];  // per consumer warp: the survivors' records, compacted in pairs
     RenderView views[MAX_BATCH];
 };
 
@@ -226,7 +233,8 @@ __global__ __launch_bounds__(NTHR, 2) void k_composite(CompositeArgs a) {
     bool done = true, wdone = true;
     int bx0 = 0, by0 = 0;          // this warp's 8x4 block in the current tile
     int cv = 0, W = 0, H = 0;      // view of the current tile and its size
-    float fpx = 0.f, fpy = 0.f;    // this lane's pixel centre
+    unsigned long long fpx2 = 0, fpy2 = 0;  // this lane's pixel centre, x and y in both halves
+    const unsigned long long log2e2 = f2pack(LOG2E, LOG2E);
     uint32_t cur = FINAL_TILE;     // tile in progress
     int32_t seq = -1;
 
@@ -250,8 +258,9 @@ __global__ __launch_bounds__(NTHR, 2) void k_composite(CompositeArgs a) {
             const int tx = (int)(local % (uint32_t)S.views[cv].tiles_x), ty = (int)(local / (uint32_t)S.views[cv].tiles_x);
             bx0 = tx * TILE + (warp & 1) * 8;
             by0 = ty * TILE + (warp >> 1) * 4;
-            fpx = (float)(bx0 + (lane & 7));
-            fpy = (float)(by0 + (lane >> 3));
+            const float fpx = (float)(bx0 + (lane & 7)), fpy = (float)(by0 + (lane >> 3));
+            fpx2 = f2pack(fpx, fpx);
+            fpy2 = f2pack(fpy, fpy);
 #pragma unroll
             for (int m = 0; m < 2; ++m)
 #pragma unroll
@@ -309,22 +318,39 @@ __global__ __launch_bounds__(NTHR, 2) void k_composite(CompositeArgs a) {
             __syncwarp();
             // the survivors' records, copied in order, so that the recurrence
             // reads them at fixed offsets
-            for (int k = lane; k < ((nrel + 15) & ~15); k += 32) S.wrec[warp][k] = S.hdr[slot][S.list[warp][k]];
+            for (int k = lane; k < ((nrel + 15) & ~15); k += 32) {
+                const Header &hk = S.hdr[slot][S.list[warp][k]];
+                float *f = reinterpret_cast<float *>(&S.wpair[warp][k >> 1]) + (k & 1);
+                f[0] = hk.h0.x;
+                f[2] = hk.h0.y;
+                f[4] = hk.h0.z;
+                f[6] = hk.h0.w;
+                f[8] = hk.h1.x;
+                f[10] = hk.h1.y;
+            }
             __syncwarp();
             for (int g0 = 0; g0 < nrel && !wdone; g0 += 16) {
                 uint32_t wh[8], wl[8];
 #pragma unroll
                 for (int g = 0; g < 16; g += 2) {
+                    // exponents of the pair: the scalar path's operations
+                    // (gauss_q, then q log2 e + log2 o), two lanes at a time
+                    const RecPair &rp = S.wpair[warp][(g0 + g) >> 1];
+                    const ulonglong2 pa = *reinterpret_cast<const ulonglong2 *>(&rp.a);
+                    const ulonglong2 pb = *reinterpret_cast<const ulonglong2 *>(&rp.b);
+                    const ulonglong2 pc = *reinterpret_cast<const ulonglong2 *>(&rp.c);
+                    const unsigned long long dx = f2sub(fpx2, pa.x), dy = f2sub(fpy2, pa.y);
+                    const unsigned long long tq = f2fma(pb.x, dx, f2mul(pb.y, dy));
+                    const unsigned long long qq = f2fma(dx, tq, f2mul(f2mul(pc.x, dy), dy));
+                    float e2v[2];
+                    f2unpack(f2fma(qq, log2e2, pc.y), e2v[0], e2v[1]);
                     float w2[2];
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         // straight-line recurrence: only T / done / last carry a
                         // dependency; padded entries are the empty record (e2 = -inf)
-                        const float4 h0 = S.wrec[warp][g0 + g + h].h0;
-                        const float4 h1 = S.wrec[warp][g0 + g + h].h1;
                         const int j = SAVE ? (int)S.list[warp][g0 + g + h] : 0;
-                        const float q = gauss_q(fpx - h0.x, fpy - h0.y, h0.z, h0.w, h1.x);
-                        const float e2 = fmaf(q, LOG2E, h1.y);
+                        const float e2 = e2v[h];
                         const float al = fminf(amax, ex2(e2));
                         // (q <= 0 for a positive-definite conic; its rounding near the
                         // centre is one of the oracle's ambiguous decisions)
