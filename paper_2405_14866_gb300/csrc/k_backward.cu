@@ -221,6 +221,10 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
         BG.gh[warp][lane][c] = h;
         BG.gl[warp][lane][c] = __float2bfloat16_rn(v - __bfloat162float(h));
     }
+    unsigned long long g2[CP / 2];  // g in (even, odd) channel pairs, for the packed <f, g>
+#pragma unroll
+    for (int c = 0; c < CP / 2; ++c) g2[c] = f2pack(g[2 * c], g[2 * c + 1]);
+    const unsigned long long fp2 = f2pack(fpx, fpy);
     int gs = 0;  // contributing Gaussians collected in this warp's current group
     const uint32_t wmax = __reduce_max_sync(FULL, lastk);
     float sg = 0.0f;  // <S, g>: blended features behind the current Gaussian
@@ -253,7 +257,8 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
                 const uint32_t k = (uint32_t)(c0 + j);
                 const float4 h0 = w_hdr[j].h0;
                 const float4 h1 = w_hdr[j].h1;
-                const float dx = fpx - h0.x, dy = fpy - h0.y;
+                float dx, dy;
+                f2unpack(f2sub(fp2, *reinterpret_cast<const unsigned long long *>(&w_hdr[j].h0.x)), dx, dy);
                 const float q = gauss_q(dx, dy, h0.z, h0.w, h1.x);
                 bool contrib = false;
                 float al = 0.0f, raw = 0.0f;
@@ -272,9 +277,12 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
                 if (contrib) {
                     const float inv = __frcp_rn(1.0f - al);
                     const float Tj = T * inv;
-                    float fg = 0.0f;
+                    unsigned long long fg2 = 0;  // even and odd channels' partial sums, packed
 #pragma unroll
-                    for (int c = 0; c < CP; ++c) fg = fmaf(f[c], g[c], fg);
+                    for (int c = 0; c < CP / 2; ++c) fg2 = f2fma(f2pack(f[2 * c], f[2 * c + 1]), g2[c], fg2);
+                    float fge, fgo;
+                    f2unpack(fg2, fge, fgo);
+                    const float fg = fge + fgo;
                     wgt = al * Tj;
                     const float dal = Tj * fg - sg * inv + gA * Tfin * inv;
                     sg = fmaf(wgt, fg, sg);

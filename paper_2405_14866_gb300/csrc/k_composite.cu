@@ -185,9 +185,15 @@ __device__ void producer(CompSmem<CP, F32F> &S, const CompositeArgs &a, int lane
     }
 }
 
+// The record's alpha_min box (mean2d +- (ex, ey)) meets [bx0, bx1] x [by0, by1]:
+// x and y of each bound by one packed addition or subtraction.
 __device__ __forceinline__ bool box_hit(const Header &h, float bx0, float bx1, float by0, float by1) {
-    return (h.h0.x + h.h1.z >= bx0) && (h.h0.x - h.h1.z <= bx1) && (h.h0.y + h.h1.w >= by0) &&
-           (h.h0.y - h.h1.w <= by1);
+    const unsigned long long mu = *reinterpret_cast<const unsigned long long *>(&h.h0.x);
+    const unsigned long long ext = *reinterpret_cast<const unsigned long long *>(&h.h1.z);
+    float hx, hy, lx, ly;
+    f2unpack(f2add(mu, ext), hx, hy);
+    f2unpack(f2sub(mu, ext), lx, ly);
+    return (hx >= bx0) && (lx <= bx1) && (hy >= by0) && (ly <= by1);
 }
 
 // Persistent: gridDim.x CTAs (a few per SM) share the tiles through
