@@ -75,6 +75,18 @@ struct CompSmem {
     RenderView views[MAX_BATCH];
 };
 
+// Entry k of a slot keeps h0 in its first 16 bytes and h1 in its second,
+// swapped when (k >> 2) is odd: the h0 (or h1) halves of eight consecutive
+// entries then fall into eight distinct groups of four banks, so a warp's
+// 16-byte reads of one half per lane are free of bank conflicts.
+__device__ __forceinline__ int hsw(int k) { return (k >> 2) & 1; }
+__device__ __forceinline__ float4 *hdr_h0(Header *slot_hdr, int k) {
+    return reinterpret_cast<float4 *>(slot_hdr + k) + hsw(k);
+}
+__device__ __forceinline__ float4 *hdr_h1(Header *slot_hdr, int k) {
+    return reinterpret_cast<float4 *>(slot_hdr + k) + (1 - hsw(k));
+}
+
 __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
@@ -87,8 +99,8 @@ template <int CP, bool F32F>
 __device__ __forceinline__ void produce_one(CompSmem<CP, F32F> &S, const CompositeArgs &a, int slot, int k,
                                             uint32_t id, uint32_t ns) {
     const uint4 *hs = reinterpret_cast<const uint4 *>(a.hdr + id);
-    cp_async16(&S.hdr[slot][k], hs);
-    cp_async16(reinterpret_cast<char *>(&S.hdr[slot][k]) + 16, hs + 1);
+    cp_async16(hdr_h0(S.hdr[slot], k), hs);
+    cp_async16(hdr_h1(S.hdr[slot], k), hs + 1);
     const size_t gi = id % ns;  // features are stored once per Gaussian, records per (view, Gaussian)
     if (!F32F && a.C == CP) {
         const uint4 *fs = reinterpret_cast<const uint4 *>(reinterpret_cast<const __nv_bfloat16 *>(a.feat) + gi * CP);
@@ -187,9 +199,10 @@ __device__ void producer(CompSmem<CP, F32F> &S, const CompositeArgs &a, int lane
 
 // The record's alpha_min box (mean2d +- (ex, ey)) meets [bx0, bx1] x [by0, by1]:
 // x and y of each bound by one packed addition or subtraction.
-__device__ __forceinline__ bool box_hit(const Header &h, float bx0, float bx1, float by0, float by1) {
-    const unsigned long long mu = *reinterpret_cast<const unsigned long long *>(&h.h0.x);
-    const unsigned long long ext = *reinterpret_cast<const unsigned long long *>(&h.h1.z);
+__device__ __forceinline__ bool box_hit(Header *slot_hdr, int k, float bx0, float bx1, float by0, float by1) {
+    const ulonglong2 p0 = *reinterpret_cast<const ulonglong2 *>(hdr_h0(slot_hdr, k));  // (mx, my), (-a/2, -b)
+    const ulonglong2 p1 = *reinterpret_cast<const ulonglong2 *>(hdr_h1(slot_hdr, k));  // (-c/2, log2 o), (ex, ey)
+    const unsigned long long mu = p0.x, ext = p1.y;
     float hx, hy, lx, ly;
     f2unpack(f2add(mu, ext), hx, hy);
     f2unpack(f2sub(mu, ext), lx, ly);
@@ -211,8 +224,8 @@ __global__ __launch_bounds__(NTHR, 2) void k_composite(CompositeArgs a) {
         for (int r = 0; r < RING; ++r) {
             mbar_init(&S.full[r], 1 + 32);  // lane 0's arrival + one asynchronous arrival per producer lane
             mbar_init(&S.empty[r], NCW);
-            S.hdr[r][SB].h0 = make_float4(0.f, 0.f, 0.f, 0.f);
-            S.hdr[r][SB].h1 = make_float4(0.f, -INFINITY, -INFINITY, -INFINITY);
+            *hdr_h0(S.hdr[r], SB) = make_float4(0.f, 0.f, 0.f, 0.f);
+            *hdr_h1(S.hdr[r], SB) = make_float4(0.f, -INFINITY, -INFINITY, -INFINITY);
         }
         mbar_init_fence();
     }
@@ -313,8 +326,8 @@ __global__ __launch_bounds__(NTHR, 2) void k_composite(CompositeArgs a) {
             const int base = (int)S.base[slot];
             // survivors of the alpha_min box test, in list order
             const float fbx0 = (float)bx0, fbx1 = (float)(bx0 + 7), fby0 = (float)by0, fby1 = (float)(by0 + 3);
-            const bool r0 = lane < cnt && box_hit(S.hdr[slot][lane], fbx0, fbx1, fby0, fby1);
-            const bool r1 = lane + 32 < cnt && box_hit(S.hdr[slot][lane + 32], fbx0, fbx1, fby0, fby1);
+            const bool r0 = lane < cnt && box_hit(S.hdr[slot], lane, fbx0, fbx1, fby0, fby1);
+            const bool r1 = lane + 32 < cnt && box_hit(S.hdr[slot], lane + 32, fbx0, fbx1, fby0, fby1);
             const uint32_t m0 = __ballot_sync(FULL, r0), m1 = __ballot_sync(FULL, r1);
             const int c0 = __popc(m0), nrel = c0 + __popc(m1);
             if (r0) S.list[warp][__popc(m0 & lt)] = (uint8_t)lane;
@@ -325,14 +338,15 @@ __global__ __launch_bounds__(NTHR, 2) void k_composite(CompositeArgs a) {
             // the survivors' records, copied in order, so that the recurrence
             // reads them at fixed offsets
             for (int k = lane; k < ((nrel + 15) & ~15); k += 32) {
-                const Header &hk = S.hdr[slot][S.list[warp][k]];
+                const int e = S.list[warp][k];
+                const float4 k0 = *hdr_h0(S.hdr[slot], e), k1 = *hdr_h1(S.hdr[slot], e);
                 float *f = reinterpret_cast<float *>(&S.wpair[warp][k >> 1]) + (k & 1);
-                f[0] = hk.h0.x;
-                f[2] = hk.h0.y;
-                f[4] = hk.h0.z;
-                f[6] = hk.h0.w;
-                f[8] = hk.h1.x;
-                f[10] = hk.h1.y;
+                f[0] = k0.x;
+                f[2] = k0.y;
+                f[4] = k0.z;
+                f[6] = k0.w;
+                f[8] = k1.x;
+                f[10] = k1.y;
             }
             __syncwarp();
             for (int g0 = 0; g0 < nrel && !wdone; g0 += 16) {
