@@ -13,13 +13,9 @@ constexpr int TILE = 16;            // tile edge in pixels (the 3DGS rasterizer'
 constexpr int TILE_PIX = TILE * TILE;
 constexpr uint32_t CULLED_KEY = 0xFFFFFFFFu;
 
-// Projected record of one Gaussian in the target view, 32 bytes (one DRAM
-// sector), read by the compositing once per (Gaussian, tile) pair:
-//   h0 = (mean2d.x, mean2d.y, conic a, conic b)
-//   h1 = (conic c, log2(opacity), ex, ey) with (ex, ey) the half extents of
-//        the box that bounds every pixel where alpha can reach alpha_min.
-// The compositing evaluates alpha = min(alpha_max, 2^(q log2(e) + log2(o))).
-// Projected record of one Gaussian instance (32 B):
+// Projected record of one Gaussian instance, 32 bytes (one DRAM sector),
+// read by the compositing once per (Gaussian, tile) pair, which evaluates
+// alpha = min(alpha_max, 2^(q log2(e) + log2(o))):
 //   h0 = (mu_x, mu_y, -a/2, -b), h1 = (-c/2, log2 o, ex, ey)
 // where [[a, b], [b, c]] is the conic (inverse 2D covariance) and (ex, ey)
 // the half extents of the box outside which o e^q < alpha_min.  The conic is
@@ -37,12 +33,13 @@ __device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b)
 __device__ __forceinline__ float fdiv(float a, float b) { return __fdiv_rn(a, b); }
 __device__ __forceinline__ float fsqrt(float a) { return __fsqrt_rn(a); }
 
-// Exponent q of the Gaussian at offset d = p - mean2d:
-//   q = -1/2 (a dx^2 + c dy^2) - b dx dy.
-// Forward and backward kernels both call this function, so both evaluate
-// the same instruction sequence and take identical skip decisions.
-// q = -(a dx^2 + 2 b dx dy + c dy^2) / 2 from the pre-scaled conic
-// (ha, nb, hc) = (-a/2, -b, -c/2): q = dx (ha dx + nb dy) + hc dy^2.
+// Exponent q of the Gaussian at offset d = p - mean2d,
+//   q = -(a dx^2 + 2 b dx dy + c dy^2) / 2,
+// from the pre-scaled conic (ha, nb, hc) = (-a/2, -b, -c/2) as
+// q = dx (ha dx + nb dy) + hc dy^2.  The backward calls this function; the
+// forward composite evaluates the same operations two Gaussians at a time
+// (packed f32x2, rounded as the scalar ones), so both take identical skip
+// decisions.
 __device__ __forceinline__ float gauss_q(float dx, float dy, float ha, float nb, float hc) {
     const float t = __fmaf_rn(ha, dx, __fmul_rn(nb, dy));
     return __fmaf_rn(dx, t, __fmul_rn(__fmul_rn(hc, dy), dy));
