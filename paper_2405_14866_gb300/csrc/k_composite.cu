@@ -352,40 +352,47 @@ __global__ __launch_bounds__(NTHR, 2) void k_composite(CompositeArgs a) {
             for (int g0 = 0; g0 < nrel && !wdone; g0 += 16) {
                 uint32_t wh[8], wl[8];
 #pragma unroll
-                for (int g = 0; g < 16; g += 2) {
-                    // exponents of the pair: the scalar path's operations
-                    // (gauss_q, then q log2 e + log2 o), two lanes at a time
-                    const RecPair &rp = S.wpair[warp][(g0 + g) >> 1];
-                    const ulonglong2 pa = *reinterpret_cast<const ulonglong2 *>(&rp.a);
-                    const ulonglong2 pb = *reinterpret_cast<const ulonglong2 *>(&rp.b);
-                    const ulonglong2 pc = *reinterpret_cast<const ulonglong2 *>(&rp.c);
-                    const unsigned long long dx = f2sub(fpx2, pa.x), dy = f2sub(fpy2, pa.y);
-                    const unsigned long long tq = f2fma(pb.x, dx, f2mul(pb.y, dy));
-                    const unsigned long long qq = f2fma(dx, tq, f2mul(f2mul(pc.x, dy), dy));
-                    float e2v[2];
-                    f2unpack(f2fma(qq, log2e2, pc.y), e2v[0], e2v[1]);
-                    float w2[2];
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        // straight-line recurrence: only T / done / last carry a
-                        // dependency; padded entries are the empty record (e2 = -inf)
-                        const int j = SAVE ? (int)S.list[warp][g0 + g + h] : 0;
-                        const float e2 = e2v[h];
-                        const float al = fminf(amax, ex2(e2));
-                        // (q <= 0 for a positive-definite conic; its rounding near the
-                        // centre is one of the oracle's ambiguous decisions)
-                        const bool ok = !done & (e2 >= l2min);
-                        const float wr = al * T;
-                        const float Tn = T - wr;
-                        const bool stop = ok & (Tn < tmin);
-                        const bool blend = ok & !stop;
-                        w2[h] = blend ? wr : 0.0f;
-                        T = blend ? Tn : T;
-                        if (SAVE) last = blend ? (uint32_t)(base + j + 1) : last;
-                        done = done | stop;
+                for (int g4 = 0; g4 < 16; g4 += 4) {
+                    if (g0 + g4 >= nrel) {  // warp-uniform: only padding left (weight 0, no state change)
+                        wh[g4 / 2] = wh[g4 / 2 + 1] = wl[g4 / 2] = wl[g4 / 2 + 1] = 0u;
+                        continue;
                     }
-                    wh[g / 2] = pack_bf16x2(w2[0], w2[1]);
-                    wl[g / 2] = pack_bf16x2(w2[0] - bf16_lo_f(wh[g / 2]), w2[1] - bf16_hi_f(wh[g / 2]));
+#pragma unroll
+                    for (int g = g4; g < g4 + 4; g += 2) {
+                        // exponents of the pair: the scalar path's operations
+                        // (gauss_q, then q log2 e + log2 o), two lanes at a time
+                        const RecPair &rp = S.wpair[warp][(g0 + g) >> 1];
+                        const ulonglong2 pa = *reinterpret_cast<const ulonglong2 *>(&rp.a);
+                        const ulonglong2 pb = *reinterpret_cast<const ulonglong2 *>(&rp.b);
+                        const ulonglong2 pc = *reinterpret_cast<const ulonglong2 *>(&rp.c);
+                        const unsigned long long dx = f2sub(fpx2, pa.x), dy = f2sub(fpy2, pa.y);
+                        const unsigned long long tq = f2fma(pb.x, dx, f2mul(pb.y, dy));
+                        const unsigned long long qq = f2fma(dx, tq, f2mul(f2mul(pc.x, dy), dy));
+                        float e2v[2];
+                        f2unpack(f2fma(qq, log2e2, pc.y), e2v[0], e2v[1]);
+                        float w2[2];
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            // straight-line recurrence: only T / done / last carry a
+                            // dependency; padded entries are the empty record (e2 = -inf)
+                            const int j = SAVE ? (int)S.list[warp][g0 + g + h] : 0;
+                            const float e2 = e2v[h];
+                            const float al = fminf(amax, ex2(e2));
+                            // (q <= 0 for a positive-definite conic; its rounding near the
+                            // centre is one of the oracle's ambiguous decisions)
+                            const bool ok = !done & (e2 >= l2min);
+                            const float wr = al * T;
+                            const float Tn = T - wr;
+                            const bool stop = ok & (Tn < tmin);
+                            const bool blend = ok & !stop;
+                            w2[h] = blend ? wr : 0.0f;
+                            T = blend ? Tn : T;
+                            if (SAVE) last = blend ? (uint32_t)(base + j + 1) : last;
+                            done = done | stop;
+                        }
+                        wh[g / 2] = pack_bf16x2(w2[0], w2[1]);
+                        wl[g / 2] = pack_bf16x2(w2[0] - bf16_lo_f(wh[g / 2]), w2[1] - bf16_hi_f(wh[g / 2]));
+                    }
                 }
                 // this lane's row of W (pixel = lane), hi and lo parts
                 uint4 *rh = reinterpret_cast<uint4 *>(&S.whi[warp][lane][0]);
