@@ -246,7 +246,9 @@ tsplat_status tsplat_ctx_stats_get(tsplat_ctx *ctx, tsplat_ctx_stats *out);
 tsplat_status tsplat_ctx_status(tsplat_ctx *ctx);
 
 /* Intermediate results of the last render, copied to a caller device
- * buffer of `bytes` bytes (for tests and tools):
+ * buffer of `bytes` bytes (for tests and tools).  The context reads the
+ * Gaussian count of the store it last rendered: keep that store alive until
+ * the exports, the statistics and the backward of that render are done.
  *   TSPLAT_EXPORT_RECT     N x 4 int32 tile rect (x0 y0 x1 y1), culled = 0
  *   TSPLAT_EXPORT_DEPTHKEY N uint32 depth key (bits of camera z), culled = 0xFFFFFFFF
  *   TSPLAT_EXPORT_MEAN2D   N x 2 f32
@@ -255,11 +257,19 @@ tsplat_status tsplat_ctx_status(tsplat_ctx *ctx);
  *   TSPLAT_EXPORT_PAIRS    P uint32 Gaussian ids in (tile, depth, id) order
  *   TSPLAT_EXPORT_RANGES   tiles x 2 uint32 [first, last) per tile
  *   TSPLAT_EXPORT_TFINAL   H x W f32 (needs TSPLAT_RENDER_SAVE)
- *   TSPLAT_EXPORT_LAST     H x W uint32 (needs TSPLAT_RENDER_SAVE) */
+ *   TSPLAT_EXPORT_LAST     H x W uint32 (needs TSPLAT_RENDER_SAVE)
+ *   TSPLAT_EXPORT_TILE_ORDER  one uint32 per tile slot of the render (all
+ *                          views of a batch): the order in which the bucket
+ *                          sort, the composite and the backward take the
+ *                          tiles -- a permutation of the slots, longest pair
+ *                          list first (tiles bucketed by 4 log2 of their pair
+ *                          count; the order within a bucket is unspecified),
+ *                          then the tiles without pairs */
 enum {
     TSPLAT_EXPORT_RECT = 0, TSPLAT_EXPORT_DEPTHKEY = 1, TSPLAT_EXPORT_MEAN2D = 2,
     TSPLAT_EXPORT_CONIC = 3, TSPLAT_EXPORT_RADIUS = 4, TSPLAT_EXPORT_PAIRS = 5,
-    TSPLAT_EXPORT_RANGES = 6, TSPLAT_EXPORT_TFINAL = 7, TSPLAT_EXPORT_LAST = 8
+    TSPLAT_EXPORT_RANGES = 6, TSPLAT_EXPORT_TFINAL = 7, TSPLAT_EXPORT_LAST = 8,
+    TSPLAT_EXPORT_TILE_ORDER = 9
 };
 tsplat_status tsplat_ctx_export(tsplat_ctx *ctx, int32_t what, void *dst, size_t bytes, void *stream);
 

@@ -20,7 +20,7 @@ F32, BF16 = 0, 1
 RENDER_ASYNC, RENDER_SAVE, RENDER_PROFILE, RENDER_TIGHT = 1, 2, 4, 8
 STAGES = ("project", "scan_order", "fill", "bucket_sort", "composite")
 EXPORT = {"rect": 0, "depthkey": 1, "mean2d": 2, "conic": 3, "radius": 4, "pairs": 5, "ranges": 6,
-          "tfinal": 7, "last": 8}
+          "tfinal": 7, "last": 8, "tile_order": 9}
 
 
 class CCamera(Structure):

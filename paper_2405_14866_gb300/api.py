@@ -345,7 +345,8 @@ class Context:
         shapes = {"rect": ((n, 4), torch.int32), "depthkey": ((n,), torch.int32), "mean2d": ((n, 2), torch.float32),
                   "conic": ((n, 3), torch.float32), "radius": ((n,), torch.float32),
                   "pairs": ((min(P, st["pair_capacity"]),), torch.int32), "ranges": ((T, 2), torch.int32),
-                  "tfinal": ((st["height"], st["width"]), torch.float32), "last": ((st["height"], st["width"]), torch.int32)}
+                  "tfinal": ((st["height"], st["width"]), torch.float32), "last": ((st["height"], st["width"]), torch.int32),
+                  "tile_order": ((T,), torch.int32)}  # a single-view render's slots
         shape, dt = shapes[what]
         t = torch.empty(shape, device="cuda", dtype=dt)
         nbytes = t.numel() * t.element_size()

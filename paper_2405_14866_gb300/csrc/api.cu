@@ -116,6 +116,7 @@ struct tsplat_ctx {
     int64_t n_cap = 0;
     const uint32_t *n_dev = nullptr;
     int W = 0, H = 0, C = 0, dtype = TSPLAT_F32, tiles_x = 0, tiles_y = 0;
+    int n_slots = 0;  // tile slots of the last render (all its views)
     const void *feat = nullptr;
     const uint32_t *pairs = nullptr;  // sorted Gaussian ids
     bool saved = false;
@@ -523,6 +524,7 @@ static tsplat_status render_tail(tsplat_ctx *c, int64_t n_cap, const uint32_t *n
     c->n_dev = n_dev;
     c->W = W; c->H = H; c->C = C; c->dtype = dtype;
     c->tiles_x = tiles_x; c->tiles_y = tiles_y;
+    c->n_slots = n_tiles;
     c->feat = feat;
     c->pairs = ids_sorted;
     c->saved = save;
@@ -867,6 +869,7 @@ tsplat_status tsplat_ctx_export(tsplat_ctx *c, int32_t what, void *dst, size_t b
         case TSPLAT_EXPORT_RADIUS: need = (size_t)n * 4; break;
         case TSPLAT_EXPORT_PAIRS: need = (size_t)P * 4; break;
         case TSPLAT_EXPORT_RANGES: need = (size_t)c->tiles_x * c->tiles_y * 8; break;
+        case TSPLAT_EXPORT_TILE_ORDER: need = (size_t)c->n_slots * 4; break;
         case TSPLAT_EXPORT_TFINAL:
         case TSPLAT_EXPORT_LAST:
             if (!c->saved) return fail(TSPLAT_ERR_INVALID_ARG, "ctx_export: render without TSPLAT_RENDER_SAVE");
@@ -885,6 +888,9 @@ tsplat_status tsplat_ctx_export(tsplat_ctx *c, int32_t what, void *dst, size_t b
         case TSPLAT_EXPORT_RANGES: TRY_CUDA(cudaMemcpyAsync(dst, c->ranges.p, need, cudaMemcpyDeviceToDevice, s)); break;
         case TSPLAT_EXPORT_TFINAL: TRY_CUDA(cudaMemcpyAsync(dst, c->tfinal.p, need, cudaMemcpyDeviceToDevice, s)); break;
         case TSPLAT_EXPORT_LAST: TRY_CUDA(cudaMemcpyAsync(dst, c->last.p, need, cudaMemcpyDeviceToDevice, s)); break;
+        case TSPLAT_EXPORT_TILE_ORDER:
+            if (need) TRY_CUDA(cudaMemcpyAsync(dst, c->torder.p, need, cudaMemcpyDeviceToDevice, s));
+            break;
     }
     return check_launch("ctx_export");
 }

@@ -8,6 +8,8 @@
 - Zero covariances (the footprint is the low-pass filter alone).
 - Non-finite depths and scales: culled by the projection as in the oracle.
 - Limits: channel counts outside [1, 64], batches beyond 8 views.
+- The tile order the kernels schedule by: a permutation of the tile slots,
+  longest pair list first, empty tiles last.
 """
 import numpy as np
 import pytest
@@ -22,6 +24,22 @@ pytestmark = pytest.mark.gpu
 PAR = O.params_array()
 
 
+def _check_tile_order(ctx, ranges):
+    """The scheduling order: every tile slot once; tiles with pairs first,
+    in falling pair count up to the width of a count bucket (a quarter
+    octave; the device's log2 is approximate, hence the slack); then the
+    tiles without pairs.  (The order within a bucket is not unique.)"""
+    order = ctx.export("tile_order").cpu().numpy().view(np.uint32).astype(np.int64)
+    T = ranges.shape[0]
+    assert np.array_equal(np.sort(order), np.arange(T))
+    cnt = (ranges[:, 1].astype(np.int64) - ranges[:, 0])[order]
+    k = int((cnt > 0).sum())
+    assert (cnt[:k] > 0).all() and (cnt[k:] == 0).all()
+    c = cnt[:k].astype(np.float64)
+    assert np.all(c[1:] <= c[:-1] * 2.0 ** 0.25 * 1.001 + 1.0)
+    return k
+
+
 def _check_bins_and_maps(g32, cam, tol=P.TOL_F32):
     g = P.gpu_gaussians(g32)
     ctx = api.Context()
@@ -32,6 +50,7 @@ def _check_bins_and_maps(g32, cam, tol=P.TOL_F32):
     assert ctx.stats()["n_pairs"] == bins.P
     assert np.array_equal(ctx.export("pairs").cpu().numpy().view(np.uint32), bins.ids)
     assert np.array_equal(ctx.export("ranges").cpu().numpy().view(np.uint32), bins.ranges)
+    _check_tile_order(ctx, bins.ranges)
     orc = O.render(g32, cam, PAR)
     P.compare_render(F, A, orc, g32, cam, PAR, tol)
     return bins
@@ -131,3 +150,32 @@ def test_buckets_beyond_shared_memory(mix):
     bins = _check_bins_and_maps(O.Gaussians(mean, cov, opac, feat), cam)
     counts = bins.ranges[:, 1].astype(np.int64) - bins.ranges[:, 0]
     assert counts.max() > 6144
+
+
+@pytest.mark.parametrize("res", [(64, 48), (1000, 776), (2048, 2048)])
+def test_tile_order_is_longest_first_permutation(res):
+    """One chunk of the scan (12 tiles, all with pairs, one of 18 K pairs),
+    a ragged last chunk (3,087 tiles), and 16,384 tiles (4 chunks), on the
+    oracle's bit-exact ranges."""
+    W, H = res
+    rng = np.random.default_rng(81)
+    n = 30000
+    z = rng.uniform(1.0, 3.0, n).astype(np.float32)
+    # clustered means: tile counts from 0 to thousands
+    ctr = rng.normal(0.0, 0.25, size=(n, 2)) * rng.choice([0.2, 1.0], size=(n, 1))
+    mean = np.concatenate([ctr * z[:, None], z[:, None]], 1).astype(np.float32)
+    s = rng.uniform(0.0005, 0.01, n).astype(np.float32)
+    cov = np.zeros((n, 6), np.float32)
+    cov[:, 0] = cov[:, 3] = cov[:, 5] = s * s
+    g32 = O.Gaussians(mean, cov, rng.uniform(0.1, 0.9, n).astype(np.float32),
+                      rng.standard_normal((n, 2)).astype(np.float32))
+    cam = gen.make_camera(0.8 * W, W, H, (0, 0, 0), np.eye(3))
+    g = P.gpu_gaussians(g32)  # the context reads the store's count until its next render
+    ctx = api.Context()
+    ctx.render(g, cam)
+    torch.cuda.synchronize()
+    bins = O.bin_gaussians(O.project_f32(g32, cam, PAR), W, H)
+    assert np.array_equal(ctx.export("ranges").cpu().numpy().view(np.uint32), bins.ranges)
+    k = _check_tile_order(ctx, bins.ranges)
+    assert k > 0 and (W == 64 or k < bins.ranges.shape[0])
+    del g
