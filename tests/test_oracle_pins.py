@@ -260,7 +260,7 @@ def test_radius_is_three_sigma_of_major_axis():
         if (ev[1] - ev[0]) ** 2 / 4 < 0.2:        # discriminant floor may be active
             continue
         r = 3 * math.sqrt(ev[1])
-        if abs(r - round(r)) < 1e-3:              # too close to an integer to judge
+        if abs(r - round(r)) < 1e-3:              # too close to an integer to decide
             continue
         assert pr.radius[i] == math.ceil(r), (i, r, pr.radius[i])
         checked += 1
