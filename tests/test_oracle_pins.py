@@ -293,7 +293,11 @@ def test_rect_hand_examples():
 
 def test_depth_key_orders_like_depth_and_culling():
     cam = _cam(f=64.0, cx=32, cy=32)
-    zs = np.array([0.5, 3.0, 1.0, 0.15, 1.0, 2.0, np.nan, 0.9], np.float32)
+    # visible iff z_near < z < z_far (open interval): 8 sits on z_near, 9 on
+    # z_far, 10 just above z_near
+    z_near, z_far = np.float32(cam.z_near), np.float32(cam.z_far)
+    zs = np.array([0.5, 3.0, 1.0, 0.15, 1.0, 2.0, np.nan, 0.9, z_near, z_far,
+                   np.nextafter(z_near, np.float32(1))], np.float32)
     xs = np.zeros_like(zs); xs[5] = 100.0            # index 5 projects far off screen
     mean = np.stack([xs, np.zeros_like(zs), zs], 1)
     cov = np.tile([1e-4, 0, 0, 1e-4, 0, 1e-4], (len(zs), 1))
@@ -301,7 +305,7 @@ def test_depth_key_orders_like_depth_and_culling():
     g = _gset(mean, cov, np.full(len(zs), 0.5), np.ones((len(zs), 1)))
     par0 = O.params_array(lowpass=0.0)
     pr = O.project_f32(g, cam, par0)
-    culled = {3, 5, 6, 7}
+    culled = {3, 5, 6, 7, 8, 9}
     for i in range(len(zs)):
         if i in culled:
             assert pr.ntiles[i] == 0 and pr.dkey[i] == 0xFFFFFFFF
@@ -604,6 +608,8 @@ def test_zbuffer_hand_worked():
         [1.0, 0.0, 1.0],        # 5: x = 12, outside the image
         [-0.1875, 0.0, 1.0],    # 6: x = 2.5 exactly -> floor(3.0) = pixel (3, 4)
         [0.0, 0.0, 0.1],        # 7: nearer than z_near = 0.2
+        [0.0, 5.0e3, 2.0e4],    # 8: pixel (4, 6) but beyond z_far = 1e4: culled
+        [0.0, 0.0, 1.0e4],      # 9: on z_far (open interval): culled
     ], np.float32)
     depth, ids = O.zbuffer(pts, cam)
     exp_ids = np.full((8, 8), -1, np.int32)
@@ -810,6 +816,26 @@ def test_tight_binning_drops_only_tiles_without_a_blendable_pixel():
     # Gaussians whose opacity is below alpha_min have no tile at all
     low = np.where(g32.opac < amin)[0]
     assert np.all(pt.ntiles[low] == 0) and np.any(pr.ntiles[low] > 0)
+
+
+def test_tight_binning_culls_opacity_just_below_alpha_min():
+    """alpha = o e^q <= o, so a Gaussian with o < alpha_min is blended
+    nowhere and keeps no tile, however close o is to alpha_min: the rounding
+    margin of the kept-tile test must not let it through."""
+    g32, cam = _tight_scene()
+    W, H = cam.width, cam.height
+    amin = np.float32(PAR[2])
+    pr0 = O.project_f32(g32, cam, PAR)
+    idx = np.where(pr0.ntiles > 0)[0][:24]
+    op = g32.opac.copy()
+    eps = [2.0 ** -k for k in range(9, 24)] + [0.0] * 9
+    op[idx] = [np.nextafter(amin, np.float32(0)) if e == 0.0 else np.float32(amin * (1.0 - e)) for e in eps]
+    assert np.all(op[idx] < amin)
+    g = O.Gaussians(g32.mean, g32.cov, op, g32.feat)
+    pr = O.project_f32(g, cam, PAR)
+    pt = O.tighten(pr, op, W, H, PAR)
+    assert np.all(pr.ntiles[idx] > 0)   # the full rect keeps them
+    assert np.all(pt.ntiles[idx] == 0)
 
 
 def test_tight_binning_keeps_tiles_the_ellipse_reaches():
