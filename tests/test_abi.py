@@ -65,3 +65,31 @@ def test_sources_use_no_multicast_and_no_trap():
     bad = re.compile(r"multicast|__trap|asm\s*\(\s*\"trap")
     for src in B.sources():
         assert not bad.search(open(src).read()), src
+
+
+def test_binding_constants_match_header():
+    """The binding's enum values (feature types, render flags, source-view
+    flags, export items) and its count of timed stages are the header's."""
+    src = "\n".join(open(h).read() for h in HEADERS)
+    exports = {m.group(1).lower(): int(m.group(2)) for m in re.finditer(r"TSPLAT_EXPORT_(\w+) = (\d+)", src)}
+    assert exports == L.EXPORT
+    flags = {m.group(1): 1 << int(m.group(2)) for m in re.finditer(r"TSPLAT_RENDER_(\w+) = 1u << (\d+)", src)}
+    assert flags == {"ASYNC": L.RENDER_ASYNC, "SAVE": L.RENDER_SAVE, "PROFILE": L.RENDER_PROFILE,
+                     "TIGHT": L.RENDER_TIGHT}
+    assert re.search(r"TSPLAT_F32 = (\d+), TSPLAT_BF16 = (\d+)", src).groups() == (str(L.F32), str(L.BF16))
+    from paper_2405_14866_gb300 import api
+    assert int(re.search(r"TSPLAT_SRC_COMPACT = (\d+)", src).group(1)) == api.SRC_COMPACT
+    assert int(re.search(r"\*n_out = (\d+)", src).group(1)) == len(L.STAGES)
+
+
+def test_product_path_fails_loudly_without_a_gpu():
+    """No CPU fallback: without a CUDA device the product calls raise."""
+    import pytest
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    from paper_2405_14866_gb300 import api
+    with pytest.raises(L.TsplatError):
+        api.Context()
+    with pytest.raises(L.TsplatError):
+        api.Gaussians.create(16, 4)
