@@ -228,7 +228,7 @@ class OracleSample:
 
 
 def run_reference(args):
-    rank, world, _ = dist_env()
+    rank, _, _ = dist_env()
     if rank != 0:
         return 0
     from oracle import oracle as O
@@ -248,7 +248,7 @@ def run_reference(args):
             "impl": "reference",
             "config": {"workload": workload_desc(sc), "step": "one view, scaled from a bounded sample"},
             "cpu_baseline": {"value": value, "unit": "views/s", "cores": O.num_threads(), "kind": "oracle",
-                             "sample": samp.describe()},
+                             "sample": samp.describe(), "sample_wall_s": tot_wall},
             "e2e": {"value": value, "unit": "views/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0

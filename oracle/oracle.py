@@ -313,7 +313,7 @@ def bin_gaussians(proj: Projected, width: int, height: int) -> Bins:
 def emit_unsorted(proj: Projected, width: int, height: int):
     """Pairs in emission order (before the sort): (keys, vals)."""
     n = proj.rect.shape[0]
-    tx, ty = tile_grid(width, height)
+    tx, _ = tile_grid(width, height)
     offsets = np.empty(n, np.int64)
     P = int(lib().orc_scan(_i64(n), _p(proj.ntiles), _p(offsets)))
     keys = np.empty(max(P, 1), np.uint64)

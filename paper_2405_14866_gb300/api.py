@@ -341,7 +341,6 @@ class Context:
     def export(self, what: str) -> torch.Tensor:
         st = self.stats()
         n, P, T = st["n_gaussians"], st["n_pairs"], st["tiles_x"] * st["tiles_y"]
-        HW = st["width"] * st["height"]
         shapes = {"rect": ((n, 4), torch.int32), "depthkey": ((n,), torch.int32), "mean2d": ((n, 2), torch.float32),
                   "conic": ((n, 3), torch.float32), "radius": ((n,), torch.float32),
                   "pairs": ((min(P, st["pair_capacity"]),), torch.int32), "ranges": ((T, 2), torch.int32),
@@ -353,7 +352,6 @@ class Context:
         if nbytes:
             L.call("tsplat_ctx_export", self.handle, L.EXPORT[what], _ptr(t), nbytes, _stream())
         torch.cuda.current_stream().synchronize()
-        del HW
         return t
 
     def close(self):
