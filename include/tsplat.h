@@ -152,9 +152,15 @@ typedef struct {
 typedef struct tsplat_gaussians tsplat_gaussians;
 
 /* Allocate room for `capacity` Gaussians with C channels of type
- * feat_dtype.  N starts at 0. */
+ * feat_dtype.  N starts at 0.  TSPLAT_ERR_INVALID_ARG for C outside
+ * [1, 64] or an unknown type, TSPLAT_ERR_OOM / TSPLAT_ERR_CUDA when the
+ * device allocation fails (no handle is returned then). */
 tsplat_status tsplat_gaussians_create(int64_t capacity, int32_t C, int32_t feat_dtype,
                                       tsplat_gaussians **out);
+/* Synchronizes the device, then frees the store (NULL is a no-op).  A
+ * context that rendered this store must not be asked for its statistics,
+ * exports or backward afterwards: it reads the store's count and features
+ * until its next render. */
 tsplat_status tsplat_gaussians_destroy(tsplat_gaussians *g);
 
 /* Load N Gaussians from caller device arrays: mean N*3 f32, cov N*6 f32
@@ -222,8 +228,17 @@ tsplat_status tsplat_build_into_noalloc(tsplat_gaussians *g, const tsplat_src_vi
  * ---------------------------------------------------------------------- */
 typedef struct tsplat_ctx tsplat_ctx;
 
+/* A context with only its small state word area allocated (synchronizes
+ * the legacy default stream); TSPLAT_ERR_OOM / TSPLAT_ERR_CUDA if that
+ * fails, e.g. without a CUDA device. */
 tsplat_status tsplat_ctx_create(tsplat_ctx **out);
+/* Synchronizes the device, then frees every buffer of the context (NULL is
+ * a no-op). */
 tsplat_status tsplat_ctx_destroy(tsplat_ctx *ctx);
+/* Grows the buffers for renders of up to max_gaussians Gaussians (instances,
+ * for batches), max_pairs pairs and max_width x max_height pixels, and
+ * synchronizes; C is not used (feature buffers belong to the caller).
+ * Needed before TSPLAT_RENDER_ASYNC renders and graph capture. */
 tsplat_status tsplat_ctx_reserve(tsplat_ctx *ctx, int64_t max_gaussians, int64_t max_pairs,
                                  int32_t max_width, int32_t max_height, int32_t C);
 
