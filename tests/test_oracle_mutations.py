@@ -9,7 +9,8 @@ mean a part of the oracle is not tied to anything outside itself.  The cases
 cover the BF16 rounding, the lifting, the key-mode and FP64 projections and
 their near and far planes, the tile rects, the scan, the emission, the sort
 and the ranges, the compositing, the adjoints of the compositing, the
-projection and the lifting, the point z-buffer, the tight binning and its
+projection and the lifting, the ambiguity flags and the alternative outputs
+at threshold decisions, the point z-buffer, the tight binning and its
 key-mode logarithm.
 """
 import os
@@ -213,6 +214,30 @@ MUTATIONS = [
     ('project near plane inclusive',
      '        if (!(pz > znear && pz < zfar)) continue;\n\n        float txz',
      '        if (!(pz >= znear && pz < zfar)) continue;\n\n        float txz'),
+    ('alternatives skip the last subset',
+     'for (int mask = 1; mask < (1 << na); ++mask) {',
+     'for (int mask = 1; mask < (1 << na) - 1; ++mask) {'),
+    ('alternatives alpha output',
+     'out[n_alt * (C + 1) + C] = 1.0 - T;',
+     'out[n_alt * (C + 1) + C] = T;'),
+    ('alpha margin not flagged',
+     'if (fabs(alpha - in->alpha_min) <= in->margin_alpha * in->alpha_min) {',
+     'if (0 && fabs(alpha - in->alpha_min) <= in->margin_alpha * in->alpha_min) {'),
+    ('T margin not flagged',
+     'if (fabs(Tn - in->t_min) <= in->margin_t * in->t_min) {',
+     'if (0 && fabs(Tn - in->t_min) <= in->margin_t * in->t_min) {'),
+    ('flip of T ignored',
+     'if (is_flipped(flips, nflips, k, DEC_T)) stop = !stop;',
+     ';'),
+    ('alpha skip inclusive',
+     'int skip_a = alpha < in->alpha_min;',
+     'int skip_a = alpha <= in->alpha_min;'),
+    ('stop inclusive',
+     'int stop = Tn < in->t_min;',
+     'int stop = Tn <= in->t_min;'),
+    ('T update before weight',
+     'const double w = alpha * T;',
+     'const double w = alpha * T * (1.0 - alpha);'),
 ]
 
 
@@ -243,4 +268,4 @@ def test_every_planted_mistake_fails_a_pin(tmp_path):
         results = list(ex.map(_caught, jobs))
     missed = [(name, why) for name, why in results if why]
     assert not missed, missed
-    assert len(results) >= 60
+    assert len(results) >= 70

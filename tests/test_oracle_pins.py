@@ -518,6 +518,30 @@ def test_pixel_alternatives_flip_one_decision():
     assert alts[0, 0] == pytest.approx(0.5) and alts[0, 1] == pytest.approx(0.5)
 
 
+def test_threshold_equalities_and_the_stop_alternative():
+    """The rules are strict: only alpha < alpha_min skips and only
+    T' < t_min stops, so equality blends.  Both equalities are ambiguous
+    decisions; the alternative of the stop decision stops before the
+    Gaussian.  All values are exact in binary: at the centres q = 0, so
+    alpha = o; 0.75 then 0.5 leave T' = 0.25 * 0.5 = 0.125 = t_min."""
+    mu = np.zeros((2, 2))
+    conic = np.tile([1.0, 0.0, 1.0], (2, 1))
+    opac = np.array([0.75, 0.5])
+    feat = np.array([[1.0], [3.0]])
+    par = O.params_array(t_min=0.125)
+    bins = _bins_single_tile([0, 1])
+    r = O.composite(mu, conic, opac, feat, 1, 1, bins, par)
+    assert r.F[0, 0, 0] == 0.75 * 1.0 + 0.25 * 0.5 * 3.0
+    assert r.A[0, 0] == 0.875 and r.last[0, 0] == 2 and r.flags[0, 0] == 1
+    alts = O.pixel_alternatives(mu, conic, opac, feat, 1, 1, bins, 0, 0, par)
+    assert alts.shape == (1, 2) and alts[0, 0] == 0.75 and alts[0, 1] == 0.75   # F, A = 1 - 0.25
+    # alpha = alpha_min exactly (the opacity is the FP32 parameter itself)
+    amin = float(np.float32(O.ALPHA_MIN))
+    r2 = O.composite(np.zeros((1, 2)), np.array([[1.0, 0.0, 1.0]]), np.array([amin]), np.array([[2.0]]), 1, 1,
+                     _bins_single_tile([0]), PAR)
+    assert r2.F[0, 0, 0] == 2.0 * amin and r2.last[0, 0] == 1 and r2.flags[0, 0] == 1
+
+
 # ---------------------------------------------------------------------------
 # adjoint (Sec. 4.2: the rasterizer is differentiated end to end)
 # ---------------------------------------------------------------------------
