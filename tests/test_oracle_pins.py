@@ -220,6 +220,63 @@ def test_key_mode_projection_matches_numerical_jacobian():
         assert abs(float(pr.dkey[i].view(np.float32)) - p[2]) <= 1e-6 * p[2]
 
 
+def test_key_mode_projection_anisotropic_intrinsics():
+    """Key mode with fx != fy, W != H and the principal point off centre,
+    against the numerical Jacobian of the pinhole map (inside the clamp) and
+    the projected mean, at single-precision tolerance."""
+    base = _cam(f=500.0, W=640, H=360, center=(0.05, -0.03, -0.1),
+                Rc2w=Rotation.from_euler("xyz", [5, -7, 10], degrees=True).as_matrix())
+    cam = gen.Camera(520.0, 410.0, 300.0, 170.0, 640, 360, base.R, base.t)
+    gs = gen.random_gaussians(13, 60, 1, center=(0.0, 0.0, 1.4), spread=0.25)
+    g32 = O.Gaussians(gs.mean, gs.cov, gs.opac, gs.feat)
+    pr = O.project_f32(g32, cam, PAR)
+    assert (pr.ntiles > 0).all()
+    for i in range(g32.n):
+        x = g32.mean[i].astype(np.float64)
+        J = np.zeros((2, 3))
+        for k in range(3):
+            e = np.zeros(3); e[k] = 1e-5
+            J[:, k] = (_proj_map(cam, x + e) - _proj_map(cam, x - e)) / 2e-5
+        c = g32.cov[i].astype(np.float64)
+        S3 = np.array([[c[0], c[1], c[2]], [c[1], c[3], c[4]], [c[2], c[4], c[5]]])
+        S2 = J @ S3 @ J.T + O.LOWPASS * np.eye(2)
+        a, b, cc = pr.conic[i].astype(np.float64)
+        assert np.allclose(np.linalg.inv([[a, b], [b, cc]]), S2, rtol=2e-5, atol=1e-6)
+        assert np.allclose(pr.mu[i], _proj_map(cam, x), rtol=0, atol=2e-4)
+
+
+def test_key_mode_clamped_jacobian_on_every_side():
+    """Key mode, fx != fy, W != H: beyond +-1.3 tan(fov/2) on either side
+    of either axis (1.3 * 0.5 W / fx in x, 1.3 * 0.5 H / fy in y) the
+    Jacobian is the pinhole map's at the clamped direction.  Large
+    footprints keep the Gaussians' rects inside the image."""
+    fx, fy, W, H = 90.0, 130.0, 200, 120
+    cam = gen.Camera(fx, fy, 100.0, 60.0, W, H, np.eye(3, dtype=np.float32), np.zeros(3, np.float32))
+    limx, limy = 1.3 * 0.5 * W / fx, 1.3 * 0.5 * H / fy
+    z = 2.0
+    cov = np.array([0.6, 0.05, -0.03, 0.5, 0.02, 0.4])
+    S3 = np.array([[cov[0], cov[1], cov[2]], [cov[1], cov[3], cov[4]], [cov[2], cov[4], cov[5]]])
+
+    def pin(p):
+        return np.array([fx * p[0] / p[2], fy * p[1] / p[2]])
+
+    for sx, sy in [(1.6, 0.1), (-1.6, 0.1), (0.1, 1.6), (0.1, -1.6), (-1.5, -1.5), (1.5, 1.5)]:
+        x = np.array([sx * limx * z, sy * limy * z, z], np.float32)
+        g = _gset([x], [cov], [0.5], [[1.0]])
+        pr = O.project_f32(g, cam, PAR)
+        assert pr.ntiles[0] > 0
+        p = x.astype(np.float64)
+        pc = np.array([np.clip(p[0] / z, -limx, limx) * z, np.clip(p[1] / z, -limy, limy) * z, z])
+        J = np.zeros((2, 3))
+        for k in range(3):
+            e = np.zeros(3); e[k] = 1e-6
+            J[:, k] = (pin(pc + e) - pin(pc - e)) / 2e-6
+        S2 = J @ S3 @ J.T + O.LOWPASS * np.eye(2)
+        a, b, c = pr.conic[0].astype(np.float64)
+        assert np.allclose(np.linalg.inv([[a, b], [b, c]]), S2, rtol=5e-5), (sx, sy)
+        assert np.allclose(pr.mu[0], pin(p) + [100.0, 60.0], rtol=1e-6), (sx, sy)
+
+
 def test_projection_clamped_jacobian_far_off_axis():
     """Outside +-1.3 tan(fov/2) the Jacobian is evaluated at the clamped
     direction: compare with a numerical Jacobian of the pinhole map taken at
@@ -282,13 +339,22 @@ def test_rect_hand_examples():
         ((79.0, 150.0), (4, 9, 6, 10)),     # x: 76/16 -> 4, 97/16 -> 6 ; y: 147/16 -> 9, 168/16 -> 10
         ((47.0, 15.9), (2, 0, 4, 2)),       # x: 44/16 -> 2, 65/16 -> 4 ; y: 12.9/16 -> 0, 33.9/16 -> 2
         ((77.5, 40.25), (4, 2, 5, 3)),      # x: 74.5/16 -> 4, 95.5/16 -> 5 (just below a boundary)
+        ((40.25, 51.0), (2, 3, 3, 4)),      # y: 48/16 = 3 exactly -> 3 ; 69/16 -> 4
+        ((51.0, 40.25), (3, 2, 4, 3)),      # x: 48/16 = 3 exactly -> 3 ; 69/16 -> 4
     ]
-    for (mx, my), rect in cases:
-        g = _gset([[mx * z / f, my * z / f, z]], [cov], [0.5], [[1.0]])
-        pr = O.project_f32(g, cam, PAR)
-        assert pr.radius[0] == 3
-        assert tuple(pr.rect[0]) == rect, ((mx, my), pr.rect[0], pr.mu[0])
-        assert pr.ntiles[0] == (rect[2] - rect[0]) * (rect[3] - rect[1])
+    # a non-square grid (13 x 6 tiles), rects clamped at the right and bottom
+    cam2 = _cam(f=f, W=200, H=96, cx=0.0, cy=0.0)
+    cases2 = [
+        ((198.0, 94.0), (12, 5, 13, 6)),    # x: 195/16 -> 12, 216/16 -> 13 ; y: 91/16 -> 5, 112/16 -> 7 -> 6
+        ((150.0, 94.0), (9, 5, 10, 6)),     # x: 147/16 -> 9, 168/16 -> 10
+    ]
+    for c_, cs in ((cam, cases), (cam2, cases2)):
+        for (mx, my), rect in cs:
+            g = _gset([[mx * z / f, my * z / f, z]], [cov], [0.5], [[1.0]])
+            pr = O.project_f32(g, c_, PAR)
+            assert pr.radius[0] == 3
+            assert tuple(pr.rect[0]) == rect, ((mx, my), pr.rect[0], pr.mu[0])
+            assert pr.ntiles[0] == (rect[2] - rect[0]) * (rect[3] - rect[1])
 
 
 def test_depth_key_orders_like_depth_and_culling():
