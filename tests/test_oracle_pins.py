@@ -84,6 +84,26 @@ def test_lift_reprojects_to_source_pixel():
     assert np.array_equal(g.feat, v.feat[vv, uu].astype(np.float64))
 
 
+def test_lift_anisotropic_intrinsics_and_unnormalised_quaternion():
+    """With fx != fy and cx != cy, both precisions re-project every lifted
+    mean to its pixel centre.  The Gaussian's rotation is that of the
+    normalised quaternion: scaling q by 2.5 leaves Sigma3D unchanged."""
+    v = _small_rig_view(quat_deg=25.0)
+    v.cam = gen.Camera(44.0, 37.0, 14.2, 17.9, v.cam.width, v.cam.height, v.cam.R, v.cam.t)
+    vv, uu = np.nonzero(v.mask)
+    R = v.cam.R.astype(np.float64)
+    t = v.cam.t.astype(np.float64)
+    for prec, tol in (("f64", 1e-5), ("f32", 2e-4)):
+        g = O.lift_view(v, prec)
+        p = g.mean.astype(np.float64) @ R.T + t
+        assert np.allclose(v.cam.fx * p[:, 0] / p[:, 2] + v.cam.cx, uu, atol=tol), prec
+        assert np.allclose(v.cam.fy * p[:, 1] / p[:, 2] + v.cam.cy, vv, atol=tol), prec
+        v2 = gen.SourceView(v.depth, v.mask, v.scale, (v.quat * 2.5).astype(np.float32), v.opacity, v.feat, v.cam)
+        g2 = O.lift_view(v2, prec)
+        scale = np.abs(g.cov[:, [0, 3, 5]]).max()
+        assert np.abs(g2.cov.astype(np.float64) - g.cov).max() <= 2e-6 * scale, prec
+
+
 def test_lift_covariance_axes_and_scales():
     """Sigma3D has eigenvalues s_i^2 along the world axes R_src^T R(q) e_i
     (quaternion rotation evaluated by scipy, an independent routine)."""
