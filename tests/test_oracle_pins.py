@@ -632,6 +632,27 @@ def test_threshold_equalities_and_the_stop_alternative():
 # adjoint (Sec. 4.2: the rasterizer is differentiated end to end)
 # ---------------------------------------------------------------------------
 
+
+def test_adjoint_of_a_clamped_alpha_and_of_the_stop_equality():
+    """alpha clamped at alpha_max passes no gradient to the opacity, the mean
+    or the conic (alpha does not depend on them there), but the feature
+    still gets alpha T g; and T' = t_min exactly is blended in the backward
+    as in the forward.  Single pixel at the Gaussians' centres (q = 0)."""
+    mu = np.zeros((2, 2))
+    conic = np.tile([1.0, 0.0, 1.0], (2, 1))
+    feat = np.array([[1.0], [3.0]])
+    bins = _bins_single_tile([0, 1])
+    gF, gA = np.ones((1, 1, 1)), np.ones((1, 1))
+    # gA = 0 here: with gA = 1 the loss would not depend on the front alpha at all
+    d_mu, d_conic, d_opac, d_feat = O.backward(mu, conic, np.array([1.0, 0.5]), feat, 1, 1, bins, gF,
+                                               np.zeros((1, 1)), PAR)
+    am = float(np.float32(O.ALPHA_MAX))
+    assert d_opac[0] == 0.0 and not d_mu[0].any() and not d_conic[0].any()
+    assert d_feat[0, 0] == pytest.approx(am) and d_opac[1] != 0.0
+    par = O.params_array(t_min=0.125)
+    d_mu, d_conic, d_opac, d_feat = O.backward(mu, conic, np.array([0.75, 0.5]), feat, 1, 1, bins, gF, gA, par)
+    assert d_feat[0, 0] == 0.75 and d_feat[1, 0] == 0.5 * 0.25
+
 def test_adjoint_matches_central_differences_frozen():
     """Central differences (eps = 1e-3 relative) of a random linear loss of
     (F, A) with the forward's decisions frozen, against the FP64 adjoint."""
@@ -880,6 +901,10 @@ def test_key_ln_matches_math_log():
     xs = xs.astype(np.float32)
     err = max(abs(O.key_ln(float(x)) - math.log(float(x))) for x in xs)
     assert err <= 1.5e-6
+    # within 2 single-precision ulps of ln x (ulps of 0.5 below |ln x| = 0.5)
+    ulps = max(abs(O.key_ln(float(x)) - math.log(float(x)))
+               / float(np.spacing(np.float32(max(abs(math.log(float(x))), 0.5)))) for x in xs)
+    assert ulps <= 2.0, ulps
     assert O.key_ln(1.0) == 0.0 and O.key_ln(2.0) == np.float32(math.log(2.0))
 
 
@@ -946,6 +971,25 @@ def test_tight_binning_culls_opacity_just_below_alpha_min():
     pt = O.tighten(pr, op, W, H, PAR)
     assert np.all(pr.ntiles[idx] > 0)   # the full rect keeps them
     assert np.all(pt.ntiles[idx] == 0)
+
+
+def test_tight_binning_full_masks_and_whole_rects():
+    """A 32-tile rect whose tiles the alpha_min ellipse all reaches keeps all
+    32 (every mask bit, the last included); a rect of more than 32 tiles is
+    kept whole and emits every tile.  The image is 32 x 4 tiles."""
+    cam = gen.make_camera(100.0, 512, 64, (0, 0, 0), np.eye(3), cx=256.0, cy=32.0)
+    z = 2.0
+    s1, s2 = 20.0 * z / 100.0, 50.0 * z / 100.0
+    mean = np.array([[0.0, 0.0, z], [1.0, 0.0, z]], np.float32)
+    cov = np.array([[s1 * s1, 0, 0, s1 * s1, 0, 1e-6], [s2 * s2, 0, 0, s2 * s2, 0, 1e-6]], np.float32)
+    g = O.Gaussians(mean, cov, np.array([0.99, 0.99], np.float32), np.ones((2, 1), np.float32))
+    pr = O.project_f32(g, cam, PAR)
+    pt = O.tighten(pr, g.opac, cam.width, cam.height, PAR)
+    area = (pr.rect[:, 2] - pr.rect[:, 0]) * (pr.rect[:, 3] - pr.rect[:, 1])
+    assert area[0] == 32 and area[1] > 32
+    assert pt.ntiles[0] == 32 and pt.ntiles[1] == area[1]
+    b = O.bin_gaussians(pt, cam.width, cam.height)
+    assert (b.ids == 0).sum() == 32 and (b.ids == 1).sum() == area[1]
 
 
 def test_tight_binning_keeps_tiles_the_ellipse_reaches():
