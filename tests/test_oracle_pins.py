@@ -787,6 +787,35 @@ def test_projection_adjoint_matches_central_differences():
             assert abs(fd - g[idx]) <= 1e-5 * scale, (idx, fd, g[idx])
 
 
+def test_projection_adjoint_anisotropic_intrinsics_and_clamp_band():
+    """The same check with fx != fy, so the clamp limits differ between the
+    axes (1.3 * 0.5 W / fx = 0.693 in x, 1.3 * 0.5 H / fy = 0.6 in y): one
+    Gaussian lies between the two limits in x (inside, so its ratio carries
+    gradient), others beyond the y limit and beyond the negative x limit."""
+    rng = np.random.default_rng(42)
+    cam = gen.Camera(300.0, 260.0, 161.0, 118.5, 320, 240, np.eye(3, dtype=np.float32), np.zeros(3, np.float32))
+    gs = gen.random_gaussians(6, 8, 1, center=(0.0, 0.0, 1.3), spread=0.2, sigma_range=(0.01, 0.05))
+    mean = gs.mean.astype(np.float64)
+    mean[0] = [0.65 * 1.2, 0.1, 1.2]     # x/z = 0.65: inside in x, past the y limit's value
+    mean[1] = [0.2, 0.64 * 1.1, 1.1]     # y/z = 0.64 > 0.6: clamped in y
+    mean[2] = [-0.8, 0.05, 1.0]          # x/z = -0.8 < -0.693: clamped in x
+    cov = gs.cov.astype(np.float64)
+    w_mu, w_con = rng.standard_normal((8, 2)), rng.standard_normal((8, 3))
+    w_mu[:3] = 0.0   # the three placed Gaussians' mean gradients come through the conic alone
+    gm, gc = O.project_backward(mean, cov, cam, w_mu, w_con)
+    for arr, g in ((mean, gm), (cov, gc)):
+        for idx in np.ndindex(arr.shape):
+            h = 1e-6 * max(1.0, abs(arr[idx])) if arr is mean else 1e-4 * cov[idx[0], [0, 3, 5]].max()
+            up, dn = arr.copy(), arr.copy()
+            up[idx] += h
+            dn[idx] -= h
+            args_up = (up, cov) if arr is mean else (mean, up)
+            args_dn = (dn, cov) if arr is mean else (mean, dn)
+            fd = (_proj_loss(*args_up, cam, w_mu, w_con) - _proj_loss(*args_dn, cam, w_mu, w_con)) / (2 * h)
+            scale = max(abs(g[idx]), np.abs(g).max() * 1e-3, 1e-9)
+            assert abs(fd - g[idx]) <= 1e-5 * scale, (idx, fd, g[idx])
+
+
 def _lift_loss(view, w):
     g = O.lift_view(view, "f64")
     return float((w["mean"] * g.mean).sum() + (w["cov"] * g.cov).sum() + (w["op"] * g.opac).sum()
