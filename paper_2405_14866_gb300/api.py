@@ -233,6 +233,9 @@ class Context:
         L.call("tsplat_ctx_create", ctypes.byref(h))
         self.handle = h
         self.n = None
+        # the context reads the last render's inputs (the store's count and
+        # features) until its next render: hold them until then
+        self._keep = ()
 
     def reserve(self, max_gaussians: int, max_pairs: int, max_width: int, max_height: int, C: int = 32):
         L.call("tsplat_ctx_reserve", self.handle, max_gaussians, max_pairs, max_width, max_height, C)
@@ -249,6 +252,7 @@ class Context:
         L.call("tsplat_render", g.handle, ctypes.byref(cc), ctypes.byref(p), _ptr(out_feat), _ptr(out_alpha),
                self.handle, _stream(stream))
         self.n = None
+        self._keep = (g,)
         return out_feat, out_alpha
 
     def render_batch(self, g: Gaussians, cams, params: Optional[L.CParams] = None, async_=False, out_feat=None,
@@ -265,6 +269,7 @@ class Context:
         p = _with_flags(params, False, async_, profile)
         L.call("tsplat_render_batch", g.handle, cc, K, ctypes.byref(p), fp, ap, self.handle, _stream(stream))
         self.n = None
+        self._keep = (g,)
         return out_feat, out_alpha
 
     def rasterize(self, mean2d, conic, opac, depth, radius, feat, width: int, height: int,
@@ -280,6 +285,7 @@ class Context:
         L.call("tsplat_rasterize", n, _ptr(mean2d), _ptr(conic), _ptr(opac), _ptr(depth), _ptr(radius), _ptr(feat),
                C, dt, width, height, ctypes.byref(p), _ptr(out_feat), _ptr(out_alpha), self.handle, _stream(stream))
         self.n = n
+        self._keep = (mean2d, conic, opac, depth, radius, feat)
         return out_feat, out_alpha
 
     def backward(self, dF, dA=None, n: Optional[int] = None, C: Optional[int] = None, stream=None, out=None):
@@ -358,6 +364,7 @@ class Context:
         if self.handle:
             L.lib().tsplat_ctx_destroy(self.handle)
             self.handle = None
+        self._keep = ()
 
     def __del__(self):
         try:

@@ -93,3 +93,48 @@ def test_product_path_fails_loudly_without_a_gpu():
         api.Context()
     with pytest.raises(L.TsplatError):
         api.Gaussians.create(16, 4)
+
+
+def test_context_holds_the_last_render_inputs(monkeypatch):
+    """A context keeps the store it last rendered (and a rasterize call's
+    arrays) until its next render, so a temporary store passed to render is
+    not freed while the context still reads its count and features.  The C
+    calls are stubbed: this is the binding's own bookkeeping."""
+    import gc
+    import weakref
+
+    import numpy as np
+    import torch
+
+    from paper_2405_14866_gb300 import api, gen
+    calls = []
+    monkeypatch.setattr(L, "call", lambda name, *a: calls.append(name))
+    monkeypatch.setattr(api, "_ptr", lambda t: None)
+    monkeypatch.setattr(api, "_stream", lambda s=None: None)
+
+    class Store:
+        C, handle = 2, None
+
+    cam = gen.make_camera(10.0, 8, 8, (0, 0, 0), np.eye(3))
+    F, A = torch.empty(2, 8, 8), torch.empty(8, 8)
+    ctx = api.Context()
+    s = Store()
+    ref = weakref.ref(s)
+    ctx.render(s, cam, out_feat=F, out_alpha=A)
+    del s
+    gc.collect()
+    assert ref() is not None                      # held by the context
+    ctx.render_batch(Store(), [cam], out_feat=[F], out_alpha=[A])
+    gc.collect()
+    assert ref() is None                          # released by the next render
+    feat = torch.empty(5, 2)
+    fref = weakref.ref(feat)
+    ctx.rasterize(torch.empty(5, 2), torch.empty(5, 3), torch.empty(5), torch.empty(5), torch.empty(5), feat,
+                  8, 8, out_feat=F, out_alpha=A)
+    del feat
+    gc.collect()
+    assert fref() is not None
+    ctx.close()
+    gc.collect()
+    assert fref() is None
+    assert calls.count("tsplat_render") == 1 and calls.count("tsplat_render_batch") == 1
