@@ -236,6 +236,7 @@ class Context:
         # the context reads the last render's inputs (the store's count and
         # features) until its next render: hold them until then
         self._keep = ()
+        self._last_shape = (0, 0, 0)  # (C, H, W) of the last single-view render
 
     def reserve(self, max_gaussians: int, max_pairs: int, max_width: int, max_height: int, C: int = 32):
         L.call("tsplat_ctx_reserve", self.handle, max_gaussians, max_pairs, max_width, max_height, C)
@@ -253,6 +254,7 @@ class Context:
                self.handle, _stream(stream))
         self.n = None
         self._keep = (g,)
+        self._last_shape = (g.C, H, W)
         return out_feat, out_alpha
 
     def render_batch(self, g: Gaussians, cams, params: Optional[L.CParams] = None, async_=False, out_feat=None,
@@ -270,6 +272,7 @@ class Context:
         L.call("tsplat_render_batch", g.handle, cc, K, ctypes.byref(p), fp, ap, self.handle, _stream(stream))
         self.n = None
         self._keep = (g,)
+        self._last_shape = (0, 0, 0)  # a batched render keeps no backward state
         return out_feat, out_alpha
 
     def rasterize(self, mean2d, conic, opac, depth, radius, feat, width: int, height: int,
@@ -286,11 +289,19 @@ class Context:
                C, dt, width, height, ctypes.byref(p), _ptr(out_feat), _ptr(out_alpha), self.handle, _stream(stream))
         self.n = n
         self._keep = (mean2d, conic, opac, depth, radius, feat)
+        self._last_shape = (C, height, width)
         return out_feat, out_alpha
 
     def backward(self, dF, dA=None, n: Optional[int] = None, C: Optional[int] = None, stream=None, out=None):
         """Gradients (d_mean2d (N,2), d_conic (N,3), d_opac (N,), d_feat (N,C)); `out` = preallocated
         tensors of at least N rows (no synchronization then)."""
+        # the library reads dF as C x H x W and dA as H x W FP32 of the last render
+        C_r, H_r, W_r = self._last_shape
+        if dF is None or tuple(dF.shape) != (C_r, H_r, W_r) or dF.dtype != torch.float32:
+            raise ValueError(f"tsplat: dF must be float32 of shape {(C_r, H_r, W_r)}, got "
+                             f"{None if dF is None else (tuple(dF.shape), dF.dtype)}")
+        if dA is not None and (tuple(dA.shape) != (H_r, W_r) or dA.dtype != torch.float32):
+            raise ValueError(f"tsplat: dA must be float32 of shape {(H_r, W_r)}, got {(tuple(dA.shape), dA.dtype)}")
         if out is not None:
             outs = tuple(out)
         else:

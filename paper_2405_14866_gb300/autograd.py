@@ -26,13 +26,14 @@ class SplatFn(torch.autograd.Function):
                                  feat.detach().contiguous(), width, height, params, save=True)
         ctx.context = context
         ctx.n, ctx.C = feat.shape
+        ctx.hw = (height, width)
         ctx.feat_dtype = feat.dtype
         return F, A
 
     @staticmethod
     def backward(ctx, dF, dA):
-        if dF is None:
-            dF = torch.zeros((ctx.C, 1, 1), device="cuda")
+        if dF is None:  # the library reads a whole C x H x W gradient
+            dF = torch.zeros((ctx.C, *ctx.hw), device="cuda")
         dm, dc, do, df = ctx.context.backward(dF.contiguous(), None if dA is None else dA.contiguous(),
                                               n=ctx.n, C=ctx.C)
         return dm, dc, do, df.to(ctx.feat_dtype), None, None, None, None, None, None

@@ -4,9 +4,40 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <atomic>
+#include <mutex>
+
 #include "../../include/tsplat.h"
 
 namespace tsp {
+
+// A launch set-up value (a grid size, after any kernel attributes it needs
+// are set) computed once per device, with that device current, under a
+// lock; later launches on that device read it without locking.
+constexpr int MAX_DEVICES = 64;
+class PerDevice {
+    std::mutex mu_;
+    std::atomic<int> val_[MAX_DEVICES] = {};
+
+public:
+    template <class F>
+    int get(F make) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return std::max(1, make(dev));
+        int v = val_[dev].load(std::memory_order_acquire);
+        if (v) return v;
+        std::lock_guard<std::mutex> lock(mu_);
+        v = val_[dev].load(std::memory_order_relaxed);
+        if (!v) {
+            v = std::max(1, make(dev));
+            val_[dev].store(v, std::memory_order_release);
+        }
+        return v;
+    }
+};
+// Streaming multiprocessors of the current device.
+int sm_count();
 
 struct Header;
 

@@ -325,19 +325,13 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
 template <int CP, typename FT>
 void run_backward(const BackwardArgs &a, cudaStream_t s) {
     const size_t smem = CT * sizeof(Header) + (size_t)CT * CP * sizeof(FT) + sizeof(BwdGroup<CP>);
-    static bool attr = false;
-    if (!attr) {
+    static PerDevice cache;
+    const int grid = cache.get([smem](int) {
         cudaFuncSetAttribute(k_backward<CP, FT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-    }
-    static int grid = 0;
-    if (!grid) {
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_backward<CP, FT>, CT, smem);
-        grid = std::max(1, sms) * std::max(1, per_sm);
-    }
+        return sm_count() * std::max(1, per_sm);
+    });
     k_backward<CP, FT><<<std::min(grid, std::max(1, a.tiles_x * a.tiles_y)), CT, smem, s>>>(a);
     note_launches(1);
 }

@@ -595,17 +595,6 @@ __global__ void k_zero_f32_n(float *p, const uint32_t *n_dev, int mult) {
     if (i < (uint64_t)*n_dev * mult) p[i] = 0.0f;
 }
 
-int sm_count() {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        sms = std::max(sms, 1);
-    }
-    return sms;
-}
-
 // Grid of the instance walks: at most a few waves, whatever the capacity is
 // (warps stride over the instance count on the device).
 int walk_blocks(int64_t inst_cap) {
@@ -625,17 +614,24 @@ void launch_bin_fill(const BinArgs &a, cudaStream_t s) {
     note_launches(1);
 }
 
-static int g_sort_grid = 0;
+int sm_count() {
+    static PerDevice cache;
+    return cache.get([](int dev) {
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        return sms;
+    });
+}
 
 int bin_sort_setup() {
-    if (!g_sort_grid) {
+    static PerDevice cache;
+    return cache.get([](int) {
         const size_t smem = sizeof(BinSortSmem);
         cudaFuncSetAttribute(k_bin_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bin_sort, BS_THREADS, smem);
-        g_sort_grid = sm_count() * std::max(1, per_sm);
-    }
-    return g_sort_grid;
+        return sm_count() * std::max(1, per_sm);
+    });
 }
 
 void launch_bin_sort(const BinArgs &a, cudaStream_t s) {

@@ -447,15 +447,13 @@ __global__ __launch_bounds__(NTHR, 2) void k_composite(CompositeArgs a) {
 template <int CP, bool F32F, bool SAVE>
 void run_composite(const CompositeArgs &a, cudaStream_t s) {
     const size_t smem = sizeof(CompSmem<CP, F32F>);
-    static int grid = 0;
-    if (!grid) {
+    static PerDevice cache;
+    const int grid = cache.get([smem](int) {
         cudaFuncSetAttribute(k_composite<CP, F32F, SAVE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_composite<CP, F32F, SAVE>, NTHR, smem);
-        grid = std::max(1, sms) * std::max(1, per_sm);
-    }
+        return sm_count() * std::max(1, per_sm);
+    });
     k_composite<CP, F32F, SAVE><<<std::min(grid, std::max(1, (int)a.n_tiles_total)), NTHR, smem, s>>>(a);
     note_launches(1);
 }

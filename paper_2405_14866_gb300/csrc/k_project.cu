@@ -481,13 +481,7 @@ void launch_export_rect(const uint2 *rect, const uint32_t *n_dev, int64_t n_cap,
 void launch_project(const float4 *xyzo, const float4 *cova, const float2 *covb, const uint32_t *n_dev,
                     int64_t n_cap, const ViewBatch &vb, RenderView *views_dev,
                     const tsplat_render_params &par, const ProjectOut &o, cudaStream_t s, bool table_on_device) {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        sms = std::max(sms, 1);
-    }
+    const int sms = sm_count();
     // about four waves of 256-thread blocks over all views
     const int64_t gx = std::max<int64_t>(1, std::min<int64_t>((n_cap + 255) / 256, (int64_t)sms * 32 / vb.n_views));
     const dim3 grid((unsigned)gx, (unsigned)vb.n_views);

@@ -56,13 +56,7 @@ __global__ void k_zbuf_resolve(const unsigned long long *keys, uint64_t n, float
 }
 
 int zb_grid(uint64_t n) {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        sms = std::max(sms, 1);
-    }
+    const int sms = sm_count();
     return (int)std::max<uint64_t>(1, std::min<uint64_t>((n + 255) / 256, (uint64_t)sms * 16));
 }
 

@@ -83,7 +83,8 @@ extern "C" tsplat_status tsplat_build_into_noalloc(tsplat_gaussians *g, const ts
                  (long long)total, (long long)NOALLOC_MAX_PIXELS);
         return record_error(TSPLAT_ERR_CAPACITY, msg);
     }
-    gaussians_store(g, st, s);
+    // every check runs before the store records this stream as its last writer
+    gaussians_peek(g, st, nullptr);
     if (total > st.cap) {
         snprintf(msg, sizeof(msg), "build_into_noalloc: %lld pixels exceed capacity %lld", (long long)total, (long long)st.cap);
         return record_error(TSPLAT_ERR_CAPACITY, msg);
@@ -104,6 +105,7 @@ extern "C" tsplat_status tsplat_build_into_noalloc(tsplat_gaussians *g, const ts
     const int64_t nblocks = layout_build_blocks(a);
     if (nblocks > NOALLOC_MAX_BLOCKS) return record_error(TSPLAT_ERR_CAPACITY, "build_into_noalloc: too many lifting blocks for the fixed scratch");
     a.nblocks = (int)nblocks;
+    gaussians_store(g, st, s);
     // every entry of the scratch that the kernels read is written earlier in the same call
     a.blk_cnt = scratch;
     a.blk_off = scratch + NOALLOC_MAX_BLOCKS;

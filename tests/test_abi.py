@@ -138,3 +138,59 @@ def test_context_holds_the_last_render_inputs(monkeypatch):
     gc.collect()
     assert fref() is None
     assert calls.count("tsplat_render") == 1 and calls.count("tsplat_render_batch") == 1
+
+
+def test_backward_rejects_gradients_of_the_wrong_shape(monkeypatch):
+    """tsplat_backward reads a C x H x W dF and an H x W dA of the last render
+    through plain pointers, so the binding checks their shapes and types before
+    the call (a short buffer would be read out of bounds on the device).  The C
+    calls are stubbed: this is the binding's own check."""
+    import numpy as np
+    import pytest
+    import torch
+
+    from paper_2405_14866_gb300 import api, gen
+    from paper_2405_14866_gb300.autograd import SplatFn
+    calls = []
+    monkeypatch.setattr(L, "call", lambda name, *a: calls.append(name))
+    monkeypatch.setattr(api, "_ptr", lambda t: None)
+    monkeypatch.setattr(api, "_stream", lambda s=None: None)
+
+    class Store:
+        C, handle = 3, None
+
+    cam = gen.make_camera(10.0, 8, 6, (0, 0, 0), np.eye(3))
+    ctx = api.Context()
+    ctx.render(Store(), cam, out_feat=torch.empty(3, 6, 8), out_alpha=torch.empty(6, 8), save=True)
+    outs = tuple(torch.empty(s) for s in ((4, 2), (4, 3), (4,), (4, 3)))
+    for dF, dA in ((torch.zeros(3, 1, 1), None), (torch.zeros(2, 6, 8), None), (torch.zeros(3, 8, 6), None),
+                   (torch.zeros(3, 6, 8, dtype=torch.float64), None), (torch.zeros(3, 6, 8), torch.zeros(8, 6)),
+                   (None, torch.zeros(6, 8))):
+        with pytest.raises(ValueError):
+            ctx.backward(dF, dA, out=outs)
+    assert "tsplat_backward" not in calls
+    ctx.backward(torch.zeros(3, 6, 8), torch.zeros(6, 8), out=outs)
+    assert calls.count("tsplat_backward") == 1
+    # a batched render keeps no backward state: any gradient is refused
+    ctx.render_batch(Store(), [cam], out_feat=[torch.empty(3, 6, 8)], out_alpha=[torch.empty(6, 8)])
+    with pytest.raises(ValueError):
+        ctx.backward(torch.zeros(3, 6, 8), None, out=outs)
+
+    # SplatFn: a loss that uses only A gives dF = None; the backward supplies
+    # a whole C x H x W zero gradient, not a 1 x 1 one
+    class Ctx:
+        pass
+    seen = {}
+
+    grads = (torch.zeros(4, 2), torch.zeros(4, 3), torch.zeros(4), torch.zeros(4, 3))
+
+    class FakeContext:
+        def backward(self, dF, dA, n, C):
+            seen["dF"], seen["dA"] = tuple(dF.shape), tuple(dA.shape)
+            return grads
+
+    c = Ctx()
+    c.context, c.n, c.C, c.hw, c.feat_dtype = FakeContext(), 4, 3, (6, 8), torch.float32
+    monkeypatch.setattr(torch, "zeros", lambda shape, device=None, **k: torch.empty(shape).fill_(0.0))
+    SplatFn.backward(c, None, torch.ones(6, 8))
+    assert seen["dF"] == (3, 6, 8) and seen["dA"] == (6, 8)
