@@ -173,58 +173,51 @@ def kernel_traffic(kernel: str):
 # CPU oracle on a bounded sample (cpu_baseline and the reference arm)
 # ---------------------------------------------------------------------------
 
-class OracleSample:
-    """Times the FP64 oracle on a bounded sample of the workload and scales
-    it to one view: lifting + projection + binning on every 16th source row
-    (x16), compositing on a fixed set of tiles (x tiles/sample)."""
-
-    ROW_STRIDE = 16
-    N_TILES = 32
+class OracleViews:
+    """The FP64 oracle on whole views of a workload, as it stands: lifting of
+    every source view (single-precision key mode, as the CUDA path computes
+    it), projection and binning in key mode, FP64 compositing of every tile
+    (OpenMP over tiles on the host's cores).  One step = one whole view."""
 
     def __init__(self, sc):
         from oracle import oracle as O
         self.O = O
         self.sc = sc
         self.cam = sc.targets[0]
-        g32 = O.lift_scene(sc, "f32")
-        pr = O.project_f32(g32, self.cam)
-        self.bins = O.bin_gaussians(pr, self.cam.width, self.cam.height)
-        self.g32 = g32
-        self.mu = pr.mu.astype(np.float64)
-        self.conic = pr.conic.astype(np.float64)
-        self.opac = g32.opac.astype(np.float64)
-        self.feat = g32.feat.astype(np.float64)
-        T = self.bins.tiles_x * self.bins.tiles_y
-        nonempty = [t for t in range(T) if self.bins.ranges[t, 1] > self.bins.ranges[t, 0]]
-        # representative sample: evenly spaced over all tiles (empty ones included)
-        self.tiles = list(range(0, T, max(1, T // self.N_TILES)))[: self.N_TILES]
-        self.T = T
-        self.sub_views = []
-        from paper_2405_14866_gb300 import gen
-        for v in sc.views:
-            s = slice(None, None, self.ROW_STRIDE)
-            self.sub_views.append(gen.SourceView(v.depth[s], v.mask[s], v.scale[s], v.quat[s], v.opacity[s],
-                                                 v.feat[s], v.cam))
-        self.nonempty = len(nonempty)
+        self.last = None
 
     def step(self):
-        O = self.O
         t0 = time.perf_counter()
-        parts = [O.lift_view(v, "f32") for v in self.sub_views]
-        g = O.Gaussians(*(np.concatenate([getattr(p, k) for p in parts], 0) for k in ("mean", "cov", "opac", "feat")))
-        pr = O.project_f32(g, self.cam)
-        O.bin_gaussians(pr, self.cam.width, self.cam.height)
-        t1 = time.perf_counter()
-        O.composite(self.mu, self.conic, self.opac, self.feat, self.cam.width, self.cam.height, self.bins,
-                    tiles=self.tiles)
-        t2 = time.perf_counter()
-        view_s = (t1 - t0) * self.ROW_STRIDE + (t2 - t1) * self.T / len(self.tiles)
-        return view_s, t2 - t0
+        g32 = self.O.lift_scene(self.sc, "f32")
+        orc = self.O.render(g32, self.cam)
+        dt = time.perf_counter() - t0
+        self.last = (g32, orc)
+        return dt
 
-    def describe(self):
-        return (f"FP64 oracle: lift+project+bin on every {self.ROW_STRIDE}th source row (x{self.ROW_STRIDE}), "
-                f"composite on {len(self.tiles)} of {self.T} tiles (x{self.T / len(self.tiles):.0f}); "
-                f"scaled to one view")
+    def describe(self, n):
+        return (f"FP64 oracle on {n} whole views of {self.sc.name} (lifting of every source view, key-mode "
+                f"projection and binning, FP64 compositing of all {self.cam.width}x{self.cam.height} pixels); "
+                f"no sampling or scaling")
+
+
+def precision_stats(F, A, Fr, Ar, flags):
+    """Per output channel: max and RMS over the image of
+    e = |g - r| / max(|r|, rho_c), rho_c = RMS of the oracle's channel c (for
+    alpha, of A), over the pixels whose oracle decisions are unambiguous
+    (a threshold decision met within the oracle's margins may go either way
+    in single precision; those pixels are counted, and the tests check them
+    against the oracle's alternative outputs)."""
+    plain = flags == 0
+    rho = np.sqrt((Fr ** 2).mean(axis=(1, 2))) + 1e-30
+    e = np.abs(F[:, plain] - Fr[:, plain]) / np.maximum(np.abs(Fr[:, plain]), rho[:, None])
+    rhoA = np.sqrt((Ar ** 2).mean()) + 1e-30
+    eA = np.abs(A[plain] - Ar[plain]) / np.maximum(np.abs(Ar[plain]), rhoA)
+    r3 = lambda x: float(f"{x:.3g}")
+    return {"F_max_rel": r3(e.max()), "F_rms_rel": r3(np.sqrt((e ** 2).mean())),
+            "A_max_rel": r3(eA.max()), "A_rms_rel": r3(np.sqrt((eA ** 2).mean())),
+            "F_max_rel_per_channel": [r3(x) for x in e.max(axis=1)],
+            "F_rms_rel_per_channel": [r3(x) for x in np.sqrt((e ** 2).mean(axis=1))],
+            "ambiguous_pixels": int((~plain).sum()), "pixels": int(plain.size)}
 
 
 def run_reference(args):
@@ -233,22 +226,20 @@ def run_reference(args):
         return 0
     from oracle import oracle as O
     sc = make_scene(args.workload, 0)
-    samp = OracleSample(sc)
-    for _ in range(max(0, min(args.warmup, 1))):
-        samp.step()
-    tot_view, tot_wall = 0.0, 0.0
-    for _ in range(args.steps):
-        v, w = samp.step()
-        tot_view += v
-        tot_wall += w
-    value = args.steps / tot_view
+    ov = OracleViews(sc)
+    for _ in range(args.warmup):
+        ov.step()
+    t0 = time.perf_counter()
+    per = [ov.step() for _ in range(args.steps)]
+    wall = time.perf_counter() - t0
+    value = args.steps / wall
     line = {"metric": METRIC, "value": value, "unit": "views/s", "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * tot_view / args.steps, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": workload_desc(sc), "step": "one view, scaled from a bounded sample"},
+            "config": {"workload": workload_desc(sc), "step": "one whole view: lifting (A1) + render (A2-A7)"},
             "cpu_baseline": {"value": value, "unit": "views/s", "cores": O.num_threads(), "kind": "oracle",
-                             "sample": samp.describe(), "sample_wall_s": tot_wall},
+                             "sample": ov.describe(args.steps), "view_s_min": min(per), "view_s_max": max(per)},
             "e2e": {"value": value, "unit": "views/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -681,6 +672,66 @@ def rig_bench(api, torch, rank, steps=20, warmup=3):
 
 
 # ---------------------------------------------------------------------------
+# the other workloads of the path (context lines)
+# ---------------------------------------------------------------------------
+
+def config_run(api, torch, sc, steps=50, warmup=5):
+    """Lifting + render of one view of another workload, timed as the
+    headline step is; returns the figures and (F, A, scene) for the
+    precision comparison."""
+    cam = sc.targets[0]
+    up = api.upload_scene(sc, feat_dtype=sc.feat_dtype)
+    views = [api.source_view(v["depth"], v["mask"], v["scale"], v["quat"], v["opacity"], v["feat"], v["cam"])
+             for v in up["views"]]
+    g = api.Gaussians.build(views, sc.C, sc.feat_dtype)
+    ctx = api.Context()
+    F, A = ctx.render(g, cam)
+    st = ctx.stats()
+    ctx.reserve(g.capacity, int(st["n_pairs"] * 1.25) + 65536, cam.width, cam.height, sc.C)
+
+    def step(profile):
+        g.build_into(views)
+        ctx.render(g, cam, async_=True, out_feat=F, out_alpha=A, profile=profile)
+
+    for _ in range(warmup):
+        step(False)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        step(True)
+    e1.record()
+    torch.cuda.synchronize()
+    ctx.status()
+    ms = e0.elapsed_time(e1) / steps
+    stages = ctx.timings()
+    bf = 2 if sc.feat_dtype == api.BF16 else 4
+    P = st["n_pairs"]
+    comp_bytes = P * (4 + 24 + sc.C * bf) + cam.width * cam.height * (4 * sc.C + 4)
+    peak, _ = measured_peaks()
+    out = {"workload": workload_desc(sc), "gaussians": st["n_gaussians"], "pairs": P, "step_ms": ms,
+           "views_per_s": 1e3 / ms, "stages_ms": {k: round(v, 4) for k, v in stages.items()},
+           "composite_frac_of_peak": comp_bytes / (stages["composite"] * 1e-3) / 1e9 / peak}
+    Fn, An = F.cpu().numpy().astype(np.float64), A.cpu().numpy().astype(np.float64)
+    del ctx, g, views, up
+    return out, (Fn, An, sc)
+
+
+def summary_of(roofline, serving, diff, precision):
+    """The figures the targets are stated in, in one short object."""
+    out = {"composite_frac_of_peak": round(roofline["frac"], 4)}
+    if serving:
+        b = serving["best_views_per_s_p99_under_8ms"]
+        out["serving_p99_under_8ms"] = {k: (round(v, 3) if v else v) for k, v in b.items()}
+    if diff:
+        out["backward_ms"] = round(diff["backward_ms"], 4)
+        out["forward_saved_ms"] = round(diff["forward_ms"], 4)
+    if precision:
+        out["precision_max_rel"] = {k: {"F": v["F_max_rel"], "A": v["A_max_rel"]} for k, v in precision.items()
+                                    if isinstance(v, dict)}
+    return out
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 
@@ -878,13 +929,55 @@ def run_ours(args):
     if not args.no_rig and args.workload == "precision":
         rig = rig_bench(api, torch, rank)
 
-    cpu = None
+    # the other two workloads of the same path, for context: the paper-shaped
+    # FP32 render (2 x 1024^2 sources, ~1.26 M Gaussians) and the tiny one
+    configs = {}
+    cfg_out = {}
+    if rank == 0:
+        for name in ("paper", "tiny"):
+            if name == args.workload:
+                continue
+            csc = make_scene(name, 0)
+            configs[name], cfg_out[name] = config_run(api, torch, csc)
+
+    # the oracle leg (rank 0 at N = 1, after every timed region): the FP64
+    # oracle timed on whole views of each workload on the host's cores, and its
+    # maps compared with the GPU's, per output channel
+    cpu = precision = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import oracle as O
-        samp = OracleSample(sc)
-        vals = [samp.step()[0] for _ in range(2)]
-        cpu = {"value": 1.0 / float(np.mean(vals)), "unit": "views/s", "cores": O.num_threads(), "kind": "oracle",
-               "sample": samp.describe()}
+        g.build_into(views)
+        ctx.render(g, cam, out_feat=F, out_alpha=A)
+        torch.cuda.synchronize()
+        Fn, An = F.cpu().numpy().astype(np.float64), A.cpu().numpy().astype(np.float64)
+        ov = OracleViews(sc)
+        ov.step()  # warm-up (page-in of the oracle's buffers)
+        per = [ov.step() for _ in range(2)]
+        cpu = {"value": len(per) / sum(per), "unit": "views/s", "cores": O.num_threads(), "kind": "oracle",
+               "sample": ov.describe(len(per))}
+        g32, orc = ov.last
+        fmt = "bf16" if sc.feat_dtype == api.BF16 else "fp32"
+        precision = {"what": "e = |gpu - oracle| / max(|oracle|, RMS of the oracle's channel), max and RMS over "
+                             "each channel's unambiguous pixels of the whole map"}
+        precision[f"{args.workload}_{fmt}_storage_vs_oracle_fed_stored_features"] = precision_stats(
+            Fn, An, orc.comp.F, orc.comp.A, orc.comp.flags)
+        if sc.feat_dtype == api.BF16:
+            g_orig = O.lift_scene(sc, "f32", bf16_features=False)
+            orc2 = O.render(g32, cam, feat64=g_orig.feat)
+            precision[f"{args.workload}_bf16_storage_vs_oracle_fed_fp32_features"] = precision_stats(
+                Fn, An, orc2.comp.F, orc2.comp.A, orc2.comp.flags)
+            del orc2, g_orig
+        del ov, g32, orc
+        for name, (Fc, Ac, csc) in cfg_out.items():
+            cv = OracleViews(csc)
+            cv.step()
+            t = [cv.step() for _ in range(2)]
+            configs[name]["oracle_views_per_s"] = len(t) / sum(t)
+            _, corc = cv.last
+            cfmt = "bf16" if csc.feat_dtype == api.BF16 else "fp32"
+            precision[f"{name}_{cfmt}_vs_oracle"] = precision_stats(Fc, Ac, corc.comp.F, corc.comp.A,
+                                                                     corc.comp.flags)
+            del cv, corc
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "views/s", "n_gpus": world, "steps": args.steps,
@@ -896,17 +989,19 @@ def run_ours(args):
                            "l2": "inputs larger than L2 (source maps ~424 MB, Gaussians ~220 MB)",
                            "source_feature_maps": "bf16" if sc.feat_dtype == api.BF16 else "f32",
                            "parallelism": f"replicas x{world}"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": int(launches),
+                # detail sections, then the compact summary last
+                "serving": serving, "differentiation": diff, "paper_rig": rig, "tight_binning": tight,
+                "render_2048": render_2048, "zbuffer": zbuffer, "e2e_full_maps": e2e_full,
+                "build_ms": build_ms, "build_gbs": build_bytes / (build_ms * 1e-3) / 1e9,
+                "build_compact_maps_ms": build_compact_ms, "gaussians_per_s": value * N,
                 "step_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
+                "configs": configs, "precision": precision,
+                "stages_ms": {k: round(v, 4) for k, v in stages.items()},
                 "render_only": {"views_per_s": 1e3 / render_ms, "ms": render_ms,
                                 "frac_of_peak": path_bytes / (render_ms * 1e-3) / 1e9 / peak},
-                "build_ms": build_ms, "build_gbs": build_bytes / (build_ms * 1e-3) / 1e9,
-                "build_compact_maps_ms": build_compact_ms,
-                "gaussians_per_s": value * N,
-                "stages_ms": stages, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "e2e_full_maps": e2e_full,
-                "clocks": clocks,
-                "tight_binning": tight, "render_2048": render_2048,
-                "serving": serving, "differentiation": diff, "zbuffer": zbuffer, "paper_rig": rig,
-                "gpu_launches": int(launches)}
+                "summary": summary_of(roofline, serving, diff, precision)}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

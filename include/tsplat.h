@@ -154,7 +154,11 @@ typedef struct tsplat_gaussians tsplat_gaussians;
 /* Allocate room for `capacity` Gaussians with C channels of type
  * feat_dtype.  N starts at 0.  TSPLAT_ERR_INVALID_ARG for C outside
  * [1, 64] or an unknown type, TSPLAT_ERR_OOM / TSPLAT_ERR_CUDA when the
- * device allocation fails (no handle is returned then). */
+ * device allocation fails (no handle is returned then).  An FP32 store also
+ * keeps every feature row as bf16 (hi, lo) parts (hi = bf16(f), lo =
+ * bf16(f - hi); 16, 32 or 64 columns each, 4 bytes per column per
+ * Gaussian), written with the features: the operands of the compositing's
+ * tensor-core products. */
 tsplat_status tsplat_gaussians_create(int64_t capacity, int32_t C, int32_t feat_dtype,
                                       tsplat_gaussians **out);
 /* Synchronizes the device, then frees the store (NULL is a no-op).  A
@@ -237,8 +241,10 @@ tsplat_status tsplat_ctx_create(tsplat_ctx **out);
 tsplat_status tsplat_ctx_destroy(tsplat_ctx *ctx);
 /* Grows the buffers for renders of up to max_gaussians Gaussians (instances,
  * for batches), max_pairs pairs and max_width x max_height pixels, and
- * synchronizes; C is not used (feature buffers belong to the caller).
- * Needed before TSPLAT_RENDER_ASYNC renders and graph capture. */
+ * synchronizes.  C (0 .. 64; 0 = none) sizes the staging of a
+ * tsplat_rasterize call's FP32 features (their bf16 hi, lo parts); feature
+ * buffers themselves belong to the caller or the store.  Needed before
+ * TSPLAT_RENDER_ASYNC renders and graph capture. */
 tsplat_status tsplat_ctx_reserve(tsplat_ctx *ctx, int64_t max_gaussians, int64_t max_pairs,
                                  int32_t max_width, int32_t max_height, int32_t C);
 

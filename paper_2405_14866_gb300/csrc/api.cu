@@ -93,7 +93,7 @@ struct tsplat_gaussians {
     int64_t cap = 0;
     int C = 0;
     int dtype = TSPLAT_F32;
-    DBuf xyzo, cova, covb, feat, n_dev, blk;
+    DBuf xyzo, cova, covb, feat, fsplit, n_dev, blk;
     cudaStream_t last_stream = nullptr;
 };
 
@@ -106,6 +106,7 @@ struct tsplat_ctx {
     DBuf ranges, tfinal, last, views;
     DBuf zkeys;  // point z-buffer scratch
     DBuf torder; // composite tile order
+    DBuf fsplit; // (hi, lo) rows of a rasterize call's FP32 features
     // small words (SM_*): visible count, P, effective P, status, tile and unit counters, N
     DBuf small;
     uint32_t *host_small = nullptr;  // pinned mirror
@@ -146,6 +147,7 @@ void gaussians_store(tsplat_gaussians *g, GaussianStore &out, cudaStream_t write
     out.cova = g->cova.as<float4>();
     out.covb = g->covb.as<float2>();
     out.feat = g->feat.p;
+    out.fsplit = g->fsplit.p;
     out.n_dev = g->n_dev.as<uint32_t>();
     g->last_stream = writer;
 }
@@ -157,6 +159,7 @@ void gaussians_peek(const tsplat_gaussians *g, GaussianStore &out, cudaStream_t 
     out.cova = g->cova.as<float4>();
     out.covb = g->covb.as<float2>();
     out.feat = g->feat.p;
+    out.fsplit = g->fsplit.p;
     out.n_dev = g->n_dev.as<uint32_t>();
     if (last_writer) *last_writer = g->last_stream;
 }
@@ -196,11 +199,15 @@ tsplat_status tsplat_gaussians_create(int64_t capacity, int32_t C, int32_t feat_
     cudaStream_t s = nullptr;
     tsplat_status st = TSPLAT_OK;
     if ((st = grow(g->xyzo, n * 16, s)) || (st = grow(g->cova, n * 16, s)) || (st = grow(g->covb, n * 8, s)) ||
-        (st = grow(g->feat, n * C * feat_size(feat_dtype), s)) || (st = grow(g->n_dev, 16, s))) {
+        (st = grow(g->feat, n * C * feat_size(feat_dtype), s)) || (st = grow(g->n_dev, 16, s)) ||
+        (feat_dtype == TSPLAT_F32 && (st = grow(g->fsplit, n * 4 * padded_channels(C), s)))) {
         tsplat_gaussians_destroy(g);
         return st;
     }
-    if (cudaMemsetAsync(g->n_dev.p, 0, 4, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+    // the split rows' padding columns are never written: zero once
+    if (cudaMemsetAsync(g->n_dev.p, 0, 4, s) != cudaSuccess ||
+        (g->fsplit.p && cudaMemsetAsync(g->fsplit.p, 0, g->fsplit.bytes, s) != cudaSuccess) ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
         tsplat_gaussians_destroy(g);
         return fail(TSPLAT_ERR_CUDA, "gaussians_create: %s", cudaGetErrorString(cudaGetLastError()));
     }
@@ -211,7 +218,8 @@ tsplat_status tsplat_gaussians_create(int64_t capacity, int32_t C, int32_t feat_
 tsplat_status tsplat_gaussians_destroy(tsplat_gaussians *g) {
     if (!g) return TSPLAT_OK;
     cudaDeviceSynchronize();
-    release(g->xyzo); release(g->cova); release(g->covb); release(g->feat); release(g->n_dev); release(g->blk);
+    release(g->xyzo); release(g->cova); release(g->covb); release(g->feat); release(g->fsplit); release(g->n_dev);
+    release(g->blk);
     delete g;
     return TSPLAT_OK;
 }
@@ -223,7 +231,8 @@ tsplat_status tsplat_gaussians_set(tsplat_gaussians *g, int64_t n, const float *
     if (n > 0 && (!mean || !cov || !opac || !feat)) return fail(TSPLAT_ERR_INVALID_ARG, "gaussians_set: NULL array");
     if (feat_dtype_in != TSPLAT_F32 && feat_dtype_in != TSPLAT_BF16) return fail(TSPLAT_ERR_INVALID_ARG, "feat_dtype %d", feat_dtype_in);
     launch_gaussians_set(n, mean, cov, opac, feat, feat_dtype_in, g->C, g->dtype, g->xyzo.as<float4>(),
-                         g->cova.as<float4>(), g->covb.as<float2>(), g->feat.p, g->n_dev.as<uint32_t>(), S(stream));
+                         g->cova.as<float4>(), g->covb.as<float2>(), g->feat.p, g->fsplit.p, g->n_dev.as<uint32_t>(),
+                         S(stream));
     g->last_stream = S(stream);
     return check_launch("gaussians_set");
 }
@@ -286,6 +295,7 @@ static tsplat_status build_args(tsplat_gaussians *g, const tsplat_src_view *view
     a.cova = g->cova.as<float4>();
     a.covb = g->covb.as<float2>();
     a.feat = g->feat.p;
+    a.fsplit = g->fsplit.p;
     a.nblocks = (int)layout_build_blocks(a);
     TRY(grow(g->blk, (size_t)a.nblocks * 8, s));
     a.blk_cnt = g->blk.as<uint32_t>();
@@ -346,7 +356,7 @@ tsplat_status tsplat_ctx_destroy(tsplat_ctx *c) {
     cudaDeviceSynchronize();
     DBuf *bufs[] = {&c->hdr, &c->rect, &c->ntiles, &c->tmask, &c->dkey, &c->radius, &c->pk0, &c->pk1, &c->pv0,
                     &c->pv1, &c->tcnt,
-                    &c->ranges, &c->tfinal, &c->last, &c->views, &c->zkeys, &c->torder, &c->small};
+                    &c->ranges, &c->tfinal, &c->last, &c->views, &c->zkeys, &c->torder, &c->fsplit, &c->small};
     for (DBuf *b : bufs) release(*b);
     for (auto &row : c->ev)
         for (cudaEvent_t e : row)
@@ -406,11 +416,13 @@ static tsplat_status ensure_pix(tsplat_ctx *c, int W, int H, int n_tiles, bool s
 
 tsplat_status tsplat_ctx_reserve(tsplat_ctx *c, int64_t max_gaussians, int64_t max_pairs, int32_t max_width,
                                  int32_t max_height, int32_t C) {
-    (void)C;
     if (!c) return fail(TSPLAT_ERR_INVALID_ARG, "ctx_reserve: ctx is NULL");
     if (max_gaussians < 0 || max_pairs < 0 || max_width < 0 || max_height < 0) return fail(TSPLAT_ERR_INVALID_ARG, "ctx_reserve: negative size");
+    if (C < 0 || C > 64) return fail(TSPLAT_ERR_INVALID_ARG, "ctx_reserve: C = %d not in [0, 64]", C);
     cudaStream_t s = nullptr;
     TRY(ensure_n(c, max_gaussians, s));
+    // tsplat_rasterize with FP32 features stages their (hi, lo) rows here
+    if (C > 0) TRY(grow(c->fsplit, (size_t)std::max<int64_t>(max_gaussians, 1) * 4 * padded_channels(C), s));
     TRY(ensure_p(c, max_pairs, s));
     const int tx = (max_width + TILE - 1) / TILE, ty = (max_height + TILE - 1) / TILE;
     TRY(ensure_pix(c, max_width, max_height, tx * ty, true, s));
@@ -431,7 +443,7 @@ static tsplat_status mark(tsplat_ctx *c, bool prof, int i, cudaStream_t s) {
 // n_cap: Gaussian count bound (grid sizing); n_dev: Gaussian count N on
 // the device; the render has n_views * N instances (instance i = view * N + id).
 static tsplat_status render_tail(tsplat_ctx *c, int64_t n_cap, const uint32_t *n_dev,
-                                 const ViewBatch &vb, const void *feat, int C, int dtype,
+                                 const ViewBatch &vb, const void *feat, const void *fsplit, int C, int dtype,
                                  const tsplat_render_params &par, cudaStream_t s) {
     const int n_tiles = (int)vb.n_tiles_total;
     const int W = vb.v[0].width, H = vb.v[0].height;
@@ -440,6 +452,7 @@ static tsplat_status render_tail(tsplat_ctx *c, int64_t n_cap, const uint32_t *n
     const bool save = (par.flags & TSPLAT_RENDER_SAVE) != 0;
     const bool prof = (par.flags & TSPLAT_RENDER_PROFILE) != 0;
     uint32_t *sm = c->small.as<uint32_t>();
+    if (dtype == TSPLAT_F32 && !fsplit) return fail(TSPLAT_ERR_INVALID_ARG, "render: FP32 features without their split rows");
     if (!tiles_fit(c, n_tiles)) return fail(TSPLAT_ERR_CAPACITY, "render: the context holds fewer than %d tile slots", n_tiles);
     const int64_t inst_cap = n_cap * vb.n_views;
     const uint32_t *n_inst = n_dev;
@@ -501,6 +514,7 @@ static tsplat_status render_tail(tsplat_ctx *c, int64_t n_cap, const uint32_t *n
     ca.ids = ids_sorted;
     ca.hdr = c->hdr.as<Header>();
     ca.feat = feat;
+    ca.fsplit = fsplit;
     ca.n_stride = n_dev;
     ca.C = C;
     ca.feat_dtype = dtype;
@@ -607,7 +621,7 @@ tsplat_status tsplat_render(const tsplat_gaussians *g, const tsplat_camera *cam,
     launch_project(g->xyzo.as<float4>(), g->cova.as<float4>(), g->covb.as<float2>(), g->n_dev.as<uint32_t>(), g->cap,
                    vb, ctx->views.as<RenderView>(), *params, o, s);
     TRY(check_launch("render: project"));
-    TRY(render_tail(ctx, g->cap, g->n_dev.as<uint32_t>(), vb, g->feat.p, g->C, g->dtype, *params, s));
+    TRY(render_tail(ctx, g->cap, g->n_dev.as<uint32_t>(), vb, g->feat.p, g->fsplit.p, g->C, g->dtype, *params, s));
     ctx->has_cam = true;
     ctx->cam = *cam;
     ctx->par = *params;
@@ -661,7 +675,7 @@ tsplat_status render_batch_impl(const tsplat_gaussians *g, const tsplat_camera *
                    vb, ctx->views.as<RenderView>(), *params, o, s, table_on_device);
     TRY(check_launch("render_batch: project"));
     ctx->has_cam = false;
-    return render_tail(ctx, g->cap, g->n_dev.as<uint32_t>(), vb, g->feat.p, g->C, g->dtype, *params, s);
+    return render_tail(ctx, g->cap, g->n_dev.as<uint32_t>(), vb, g->feat.p, g->fsplit.p, g->C, g->dtype, *params, s);
 }
 }  // namespace tsp
 
@@ -736,15 +750,20 @@ tsplat_status tsplat_rasterize(int64_t n, const float *mean2d, const float *coni
     cudaStream_t s = S(stream);
     const int tiles_x = (width + TILE - 1) / TILE, tiles_y = (height + TILE - 1) / TILE;
     const bool async_mode = (params->flags & TSPLAT_RENDER_ASYNC) != 0;
+    const bool split = feat_dtype == TSPLAT_F32;
+    const size_t split_bytes = (size_t)std::max<int64_t>(n, 1) * 4 * padded_channels(C);
     if (async_mode) {
-        if (ctx->hdr.bytes < (size_t)std::max<int64_t>(n, 1) * sizeof(Header) || !tiles_fit(ctx, (int64_t)tiles_x * tiles_y))
+        if (ctx->hdr.bytes < (size_t)std::max<int64_t>(n, 1) * sizeof(Header) || !tiles_fit(ctx, (int64_t)tiles_x * tiles_y) ||
+            (split && ctx->fsplit.bytes < split_bytes))
             return fail(TSPLAT_ERR_CAPACITY, "rasterize: TSPLAT_RENDER_ASYNC needs tsplat_ctx_reserve for these sizes");
     } else {
         TRY(ensure_n(ctx, n, s));
         TRY(ensure_pix(ctx, width, height, tiles_x * tiles_y, (params->flags & TSPLAT_RENDER_SAVE) != 0, s));
+        if (split) TRY(grow(ctx->fsplit, split_bytes, s));
     }
     init_small(ctx, s);
     launch_fill_u32(small_ptr(ctx, SM_N), (uint32_t)n, 1, s);
+    if (split) launch_feat_split((const float *)feat, small_ptr(ctx, SM_N), n, C, ctx->fsplit.p, s);
     TRY(mark(ctx, (params->flags & TSPLAT_RENDER_PROFILE) != 0, 0, s));
     const bool save = (params->flags & TSPLAT_RENDER_SAVE) != 0;
     tsplat_camera cam;
@@ -761,7 +780,8 @@ tsplat_status tsplat_rasterize(int64_t n, const float *mean2d, const float *coni
     launch_prepare_2d(n, mean2d, conic, opac, depth, radius, *params, vb, ctx->views.as<RenderView>(), o, s);
     TRY(check_launch("rasterize: prepare"));
     ctx->has_cam = false;
-    return render_tail(ctx, n, small_ptr(ctx, SM_N), vb, feat, C, feat_dtype, *params, s);
+    return render_tail(ctx, n, small_ptr(ctx, SM_N), vb, feat, split ? ctx->fsplit.p : nullptr, C, feat_dtype,
+                       *params, s);
 }
 
 tsplat_status tsplat_backward(tsplat_ctx *c, const float *dL_dfeat, const float *dL_dalpha, float *d_mean2d,

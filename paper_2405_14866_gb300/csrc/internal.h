@@ -58,6 +58,10 @@ struct ViewDesc {
     tsplat_camera cam;
 };
 
+// Channels of a feature row as the compositing stages it (whole 16-column
+// blocks of its tensor-core products): 16, 32 or 64.
+__host__ __device__ inline int padded_channels(int C) { return C <= 16 ? 16 : (C <= 32 ? 32 : 64); }
+
 struct BuildArgs {
     ViewDesc views[MAX_VIEWS];
     int n_views;
@@ -68,6 +72,10 @@ struct BuildArgs {
     float4 *cova;
     float2 *covb;
     void *feat;
+    // FP32 stores: each feature row also as bf16 (hi, lo) with
+    // hi = bf16(f), lo = bf16(f - hi), rows of 2 x padded_channels(C)
+    // ([hi | lo], padding zero), the operands of the compositing's products
+    void *fsplit;
     uint32_t *blk_cnt;  // [nblocks]
     uint32_t *blk_off;  // [nblocks]
     uint32_t *n_dev;    // N (output)
@@ -86,10 +94,16 @@ inline int64_t layout_build_blocks(BuildArgs &a) {
 }
 void launch_build(const BuildArgs &a, cudaStream_t s);
 
-// Convert/copy caller arrays into a Gaussian store.
+// Convert/copy caller arrays into a Gaussian store (fsplit: as in BuildArgs,
+// or nullptr).
 void launch_gaussians_set(int64_t n, const float *mean, const float *cov, const float *opac,
                           const void *feat, int feat_dtype_in, int C, int out_dtype, float4 *xyzo,
-                          float4 *cova, float2 *covb, void *feat_out, uint32_t *n_dev, cudaStream_t s);
+                          float4 *cova, float2 *covb, void *feat_out, void *fsplit, uint32_t *n_dev,
+                          cudaStream_t s);
+// The (hi, lo) rows of BuildArgs::fsplit from N x C FP32 features (N = *n_dev,
+// n_cap >= N bounds the grid); padding columns written as zero.
+void launch_feat_split(const float *feat, const uint32_t *n_dev, int64_t n_cap, int C, void *fsplit,
+                       cudaStream_t s);
 void launch_gaussians_get(const uint32_t *n_dev, int64_t cap, int C, int dtype, const float4 *xyzo,
                           const float4 *cova, const float2 *covb, const void *feat_in, float *mean,
                           float *cov, float *opac, void *feat_out, cudaStream_t s);
@@ -186,6 +200,7 @@ struct CompositeArgs {
     const uint32_t *ids;       // sorted pairs: instance ids
     const Header *hdr;         // per instance
     const void *feat;          // per Gaussian (instance % N)
+    const void *fsplit;        // FP32 features: their (hi, lo) bf16 rows (see BuildArgs)
     const uint32_t *n_stride;  // N (device)
     int C;
     int feat_dtype;
@@ -236,6 +251,7 @@ struct GaussianStore {
     float4 *cova;
     float2 *covb;
     void *feat;
+    void *fsplit;  // FP32 stores: (hi, lo) rows (see BuildArgs), else nullptr
     uint32_t *n_dev;
 };
 void gaussians_store(tsplat_gaussians *g, GaussianStore &out, cudaStream_t writer);

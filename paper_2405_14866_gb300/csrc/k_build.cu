@@ -6,8 +6,11 @@
 // the lift itself, which numbers Gaussians in (view, row, column) order of
 // the foreground pixels.  Single precision, one rounding per operation in a
 // fixed order (the oracle's key mode follows the same order).
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
+#include "ptx.cuh"
 
 namespace tsp {
 
@@ -134,6 +137,22 @@ __device__ __forceinline__ void copy_feat(const void *src, int src_dtype, int64_
     }
 }
 
+// The (hi, lo) bf16 parts of FP32 features (hi = bf16(v), lo = bf16(v - hi),
+// both rounded to nearest even): four at a time, and one at a time.
+__device__ __forceinline__ void split4(const float (&v)[4], uint2 &hi, uint2 &lo) {
+    hi.x = pack_bf16x2(v[0], v[1]);
+    hi.y = pack_bf16x2(v[2], v[3]);
+    lo.x = pack_bf16x2(v[0] - bf16_lo_f(hi.x), v[1] - bf16_hi_f(hi.x));
+    lo.y = pack_bf16x2(v[2] - bf16_lo_f(hi.y), v[3] - bf16_hi_f(hi.y));
+}
+__device__ __forceinline__ void split1(float v, int C, int64_t row, int c, void *fsplit) {
+    const int cp = padded_channels(C);
+    __nv_bfloat16 *r = (__nv_bfloat16 *)fsplit + row * 2 * cp;
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    r[c] = h;
+    r[cp + c] = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
 // Lift pixel p (row v, column u) of view vd into Gaussian `id`; its maps
 // are read at index k (k = p, or the pixel's foreground rank for compact maps).
 __device__ __forceinline__ void lift_one(const BuildArgs &a, const ViewDesc &vd, int64_t p, int64_t k, int64_t id) {
@@ -209,6 +228,14 @@ __device__ __forceinline__ void copy_rows(const BuildArgs &a, const ViewDesc &vd
             }
             if (a.out_dtype == TSPLAT_F32) {
                 *reinterpret_cast<float4 *>((float *)a.feat + id * C + c0) = make_float4(v[0], v[1], v[2], v[3]);
+                if (a.fsplit) {
+                    uint2 hi, lo;
+                    split4(v, hi, lo);
+                    const int cp = padded_channels(C);
+                    __nv_bfloat16 *row = (__nv_bfloat16 *)a.fsplit + id * 2 * cp;
+                    *reinterpret_cast<uint2 *>(row + c0) = hi;
+                    *reinterpret_cast<uint2 *>(row + cp + c0) = lo;
+                }
             } else {
                 __nv_bfloat162 lo = __floats2bfloat162_rn(v[0], v[1]), hi = __floats2bfloat162_rn(v[2], v[3]);
                 uint2 o;
@@ -219,8 +246,12 @@ __device__ __forceinline__ void copy_rows(const BuildArgs &a, const ViewDesc &vd
         } else {
             float v = vd.feat_dtype == TSPLAT_F32 ? ((const float *)vd.feat)[p * C + part]
                                                   : __bfloat162float(((const __nv_bfloat16 *)vd.feat)[p * C + part]);
-            if (a.out_dtype == TSPLAT_F32) ((float *)a.feat)[id * C + part] = v;
-            else ((__nv_bfloat16 *)a.feat)[id * C + part] = __float2bfloat16_rn(v);
+            if (a.out_dtype == TSPLAT_F32) {
+                ((float *)a.feat)[id * C + part] = v;
+                if (a.fsplit) split1(v, C, id, part, a.fsplit);
+            } else {
+                ((__nv_bfloat16 *)a.feat)[id * C + part] = __float2bfloat16_rn(v);
+            }
         }
     }
 }
@@ -369,7 +400,7 @@ __global__ __launch_bounds__(BT) void k_build_backward(LiftBwdArgs a) {
 
 __global__ void k_gaussians_set(uint64_t n, const float *mean, const float *cov, const float *opac,
                                 const void *feat, int dtype_in, int C, int dtype_out, float4 *xyzo,
-                                float4 *cova, float2 *covb, void *feat_out, uint32_t *n_dev) {
+                                float4 *cova, float2 *covb, void *feat_out, void *fsplit, uint32_t *n_dev) {
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) *n_dev = (uint32_t)n;
     if (i >= n) return;
@@ -377,6 +408,27 @@ __global__ void k_gaussians_set(uint64_t n, const float *mean, const float *cov,
     cova[i] = make_float4(cov[6 * i], cov[6 * i + 1], cov[6 * i + 2], cov[6 * i + 3]);
     covb[i] = make_float2(cov[6 * i + 4], cov[6 * i + 5]);
     copy_feat(feat, dtype_in, (int64_t)i, feat_out, dtype_out, (int64_t)i, C);
+    if (fsplit && dtype_out == TSPLAT_F32)
+        for (int c = 0; c < C; ++c) split1(((const float *)feat_out)[i * C + c], C, (int64_t)i, c, fsplit);
+}
+
+// (hi, lo) rows of N x C FP32 features: thread t of Gaussian i writes
+// columns 4t .. 4t + 3 of both halves, zero beyond C.
+__global__ void k_feat_split(const float *feat, const uint32_t *n_dev, int C, void *fsplit) {
+    const int cp = padded_channels(C), q = cp / 4;
+    const uint64_t n = *n_dev;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * q; t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t i = t / q;
+        const int c0 = (int)(t - i * q) * 4;
+        float v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = c0 + k < C ? feat[i * C + c0 + k] : 0.0f;
+        uint2 hi, lo;
+        split4(v, hi, lo);
+        __nv_bfloat16 *row = (__nv_bfloat16 *)fsplit + i * 2 * cp;
+        *reinterpret_cast<uint2 *>(row + c0) = hi;
+        *reinterpret_cast<uint2 *>(row + cp + c0) = lo;
+    }
 }
 
 __global__ void k_gaussians_get(const uint32_t *n_dev, int C, int dtype, const float4 *xyzo,
@@ -421,10 +473,19 @@ void launch_build_backward(const LiftBwdArgs &a, cudaStream_t s) {
 
 void launch_gaussians_set(int64_t n, const float *mean, const float *cov, const float *opac, const void *feat,
                           int feat_dtype_in, int C, int out_dtype, float4 *xyzo, float4 *cova, float2 *covb,
-                          void *feat_out, uint32_t *n_dev, cudaStream_t s) {
+                          void *feat_out, void *fsplit, uint32_t *n_dev, cudaStream_t s) {
     const int64_t blocks = n > 0 ? (n + 255) / 256 : 1;
     k_gaussians_set<<<(unsigned)blocks, 256, 0, s>>>((uint64_t)n, mean, cov, opac, feat, feat_dtype_in, C,
-                                                     out_dtype, xyzo, cova, covb, feat_out, n_dev);
+                                                     out_dtype, xyzo, cova, covb, feat_out, fsplit, n_dev);
+    note_launches(1);
+}
+
+void launch_feat_split(const float *feat, const uint32_t *n_dev, int64_t n_cap, int C, void *fsplit,
+                       cudaStream_t s) {
+    if (n_cap <= 0) return;
+    const int64_t work = n_cap * (padded_channels(C) / 4);
+    const int blocks = (int)std::min<int64_t>((work + 255) / 256, (int64_t)sm_count() * 16);
+    k_feat_split<<<blocks, 256, 0, s>>>(feat, n_dev, C, fsplit);
     note_launches(1);
 }
 

@@ -91,10 +91,11 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
 
-// Producer side of one Gaussian of a slot: its record (2 x 16 B) and, for
-// BF16 rows of exactly CP channels, its feature row by 16-byte asynchronous
-// copies; other feature layouts are loaded, split (FP32 -> bf16 hi + lo)
-// and zero-padded by the producer lane itself.
+// Producer side of one Gaussian of a slot: its record (2 x 16 B) and its
+// feature row by 16-byte asynchronous copies -- BF16 rows of exactly CP
+// channels as stored, FP32 rows as their pre-split bf16 (hi, lo) rows of CP
+// columns each (zero-padded); BF16 rows of fewer channels are loaded and
+// zero-padded by the producer lane itself.
 template <int CP, bool F32F>
 __device__ __forceinline__ void produce_one(CompSmem<CP, F32F> &S, const CompositeArgs &a, int slot, int k,
                                             uint32_t id, uint32_t ns) {
@@ -102,21 +103,17 @@ __device__ __forceinline__ void produce_one(CompSmem<CP, F32F> &S, const Composi
     cp_async16(hdr_h0(S.hdr[slot], k), hs);
     cp_async16(hdr_h1(S.hdr[slot], k), hs + 1);
     const size_t gi = id % ns;  // features are stored once per Gaussian, records per (view, Gaussian)
-    if (!F32F && a.C == CP) {
+    if (F32F) {
+        const uint4 *fs = reinterpret_cast<const uint4 *>(reinterpret_cast<const __nv_bfloat16 *>(a.fsplit) + gi * 2 * CP);
+#pragma unroll
+        for (int c = 0; c < CP / 8; ++c) {
+            cp_async16(&S.fhi[slot][k][8 * c], fs + c);
+            cp_async16(&S.flo[F32F ? slot : 0][F32F ? k : 0][8 * c], fs + CP / 8 + c);
+        }
+    } else if (a.C == CP) {
         const uint4 *fs = reinterpret_cast<const uint4 *>(reinterpret_cast<const __nv_bfloat16 *>(a.feat) + gi * CP);
 #pragma unroll
         for (int c = 0; c < CP / 8; ++c) cp_async16(&S.fhi[slot][k][8 * c], fs + c);
-    } else if (F32F) {
-        const float *src = reinterpret_cast<const float *>(a.feat) + gi * a.C;
-#pragma unroll 4
-        for (int c = 0; c < CP; c += 2) {
-            const float v0 = c < a.C ? __ldg(src + c) : 0.0f;
-            const float v1 = c + 1 < a.C ? __ldg(src + c + 1) : 0.0f;
-            const uint32_t hi = pack_bf16x2(v0, v1);
-            const uint32_t lo = pack_bf16x2(v0 - bf16_lo_f(hi), v1 - bf16_hi_f(hi));
-            *reinterpret_cast<uint32_t *>(&S.fhi[slot][k][c]) = hi;
-            *reinterpret_cast<uint32_t *>(&S.flo[F32F ? slot : 0][F32F ? k : 0][c]) = lo;
-        }
     } else {
         const __nv_bfloat16 *src = reinterpret_cast<const __nv_bfloat16 *>(a.feat) + gi * a.C;
         for (int c = 0; c < CP; ++c) S.fhi[slot][k][c] = c < a.C ? src[c] : __float2bfloat16_rn(0.0f);
@@ -462,7 +459,7 @@ void run_composite(const CompositeArgs &a, cudaStream_t s) {
 
 void launch_composite(const CompositeArgs &a, cudaStream_t s) {
     if (a.n_tiles_total == 0) return;
-    const bool f32 = a.feat_dtype == TSPLAT_F32;
+    const bool f32 = a.feat_dtype == TSPLAT_F32;  // then a.fsplit holds the split rows
     if (a.save) {
         if (a.C <= 16) { if (f32) run_composite<16, true, true>(a, s); else run_composite<16, false, true>(a, s); }
         else if (a.C <= 32) { if (f32) run_composite<32, true, true>(a, s); else run_composite<32, false, true>(a, s); }

@@ -102,6 +102,7 @@ extern "C" tsplat_status tsplat_build_into_noalloc(tsplat_gaussians *g, const ts
     a.cova = st.cova;
     a.covb = st.covb;
     a.feat = st.feat;
+    a.fsplit = st.fsplit;
     const int64_t nblocks = layout_build_blocks(a);
     if (nblocks > NOALLOC_MAX_BLOCKS) return record_error(TSPLAT_ERR_CAPACITY, "build_into_noalloc: too many lifting blocks for the fixed scratch");
     a.nblocks = (int)nblocks;

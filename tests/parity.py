@@ -71,11 +71,11 @@ def compare_render(F_gpu, A_gpu, orc: O.Render, g32: O.Gaussians, cam, par, tol,
     bad = np.argwhere((eF[:, plain].max(axis=0) > tol) | (eA[plain] > tol))
     assert stats["maxF"] <= tol and stats["maxA"] <= tol, (stats, bad[:5])
     # ambiguous pixels: one of the admissible outputs must match
-    feat = g32.feat if feat64 is None else feat64
+    feat = np.ascontiguousarray(g32.feat if feat64 is None else feat64, np.float64)
+    opac = np.ascontiguousarray(g32.opac, np.float64)
     unchecked = 0
     for (y, x) in np.argwhere(flagged):
-        alts = O.pixel_alternatives(orc.mu64, orc.conic64, g32.opac.astype(np.float64), feat.astype(np.float64),
-                                    W, H, orc.bins, int(x), int(y), par)
+        alts = O.pixel_alternatives(orc.mu64, orc.conic64, opac, feat, W, H, orc.bins, int(x), int(y), par)
         if alts is None:
             unchecked += 1
             continue

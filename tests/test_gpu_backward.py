@@ -56,9 +56,12 @@ def _check(gpu, ref, names=("mean2d", "conic", "opac", "feat")):
     return out
 
 
+# every channel bucket of the kernel (8, 16, 32, 64 padded channels) in both
+# feature types, with ragged channel counts inside the buckets
+@pytest.mark.parametrize("C", [8, 12, 16, 32, 33])
 @pytest.mark.parametrize("feat_dtype", [api.F32, api.BF16])
-def test_backward_matches_fp64_adjoint(feat_dtype):
-    sc, cam, g32 = _case(feat_dtype=feat_dtype)
+def test_backward_matches_fp64_adjoint(feat_dtype, C):
+    sc, cam, g32 = _case(feat_dtype=feat_dtype, C=C)
     g = P.gpu_gaussians(g32, feat_dtype)
     ctx = api.Context()
     F, A = ctx.render(g, cam, save=True)
@@ -94,13 +97,15 @@ def test_splatfn_autograd_matches_adjoint_and_direct_call():
     assert torch.equal(F.detach(), F2) and torch.equal(A.detach(), A2)
 
 
-def test_fp32_central_differences_match_fp64_adjoint():
+@pytest.mark.parametrize("C", [3, 16])
+def test_fp32_central_differences_match_fp64_adjoint(C):
     """Central differences of the GPU forward through the rasterizer on a
     32x32 sub-case, against the FP64 adjoint (gate 1e-2).  The step is 1e-2 of
     the value (0.01 px for means): the single-precision loss carries ~5e-6
     absolute noise, which a 1e-3 step would amplify to ~1% (the FP64 oracle's
-    own central-difference pin uses 1e-3)."""
-    sc = gen.scene_paper(seed=35, res=40, C=3)
+    own central-difference pin uses 1e-3).  C = 16 is the channel count of the
+    differentiation workload."""
+    sc = gen.scene_paper(seed=35, res=40, C=C)
     cam = gen.make_camera(32.0, 32, 32, (0, 0, 0), np.eye(3))
     g32 = O.lift_scene(sc, "f32")
     orc, dF, dA, ref = _oracle(g32, cam)
@@ -169,3 +174,40 @@ def test_fp32_central_differences_match_fp64_adjoint():
             assert abs(fd - an) <= 1e-2 * max(abs(an), rho[key]), (key, j, idx, fd, an)
             checked += 1
     assert checked >= 60, (checked, skipped)
+
+
+def test_backward_differentiation_sample_full_size():
+    """One sample of the differentiation workload at full size, in the launch
+    configuration the benchmark times: two 512x512 source views (~315K
+    Gaussians, 16-channel FP32 features), 512x512 target, the render with
+    saved state into a reserved context and the backward into preallocated
+    gradients, loss = MSE against a seeded N(0,1) map (dL/dF = 2 (F - Y) / n
+    from the oracle's F; zero at pixels with an ambiguous decision).  All
+    four gradient groups against the FP64 adjoint at the 1e-3 gate."""
+    sc = gen.scene_diff_sample(seed=300)
+    cam = sc.targets[0]
+    views, keep = P.device_views(sc)
+    g = api.Gaussians.build(views, sc.C, sc.feat_dtype)
+    ctx = api.Context()
+    ctx.render(g, cam, save=True)
+    st = ctx.stats()
+    assert st["n_pairs"] > 600_000
+    ctx.reserve(g.capacity, int(st["n_pairs"] * 1.25) + 65536, cam.width, cam.height, sc.C)
+    F = torch.empty((sc.C, cam.height, cam.width), device="cuda")
+    A = torch.empty((cam.height, cam.width), device="cuda")
+    ctx.render(g, cam, save=True, async_=True, out_feat=F, out_alpha=A)
+
+    g32 = O.lift_scene(sc, "f32")
+    orc = O.render(g32, cam, PAR)
+    Y = sc.extra["target_map"].astype(np.float64)
+    dF = (orc.comp.F - Y) * (2.0 / orc.comp.F.size)
+    dF[:, orc.comp.flags > 0] = 0.0
+    dF32 = dF.astype(np.float32)
+    n = g32.n
+    grads = tuple(torch.empty(sh, device="cuda") for sh in ((g.capacity, 2), (g.capacity, 3), (g.capacity,),
+                                                           (g.capacity, sc.C)))
+    ctx.backward(torch.from_numpy(dF32).cuda(), None, out=grads)
+    ctx.status()
+    ref = O.backward(orc.mu64, orc.conic64, g32.opac.astype(np.float64), g32.feat.astype(np.float64), cam.width,
+                     cam.height, orc.bins, dF32.astype(np.float64), None, PAR)
+    _check(tuple(t[:n] for t in grads), ref)

@@ -24,10 +24,12 @@ def _close(name, g, r):
     assert e.max() <= TOL, (name, float(e.max()), np.unravel_index(e.argmax(), e.shape))
 
 
-@pytest.mark.parametrize("seed", [61, 62])
-def test_backward_to_source_maps(seed):
-    sc = gen.scene_diff_sample(seed=seed, res=64, C=4)
-    cam = gen.make_camera(60.0, 64, 56, (0.02, -0.01, 0.0), gen.rot_y(2.0))
+# two small cases, and one sample of the differentiation workload at the size
+# the benchmark times (2 x 512^2 sources, ~315K Gaussians, 16 channels)
+@pytest.mark.parametrize("seed,res,C", [(61, 64, 4), (62, 64, 4), (300, 512, 16)])
+def test_backward_to_source_maps(seed, res, C):
+    sc = gen.scene_diff_sample(seed=seed, res=res, C=C)
+    cam = (gen.make_camera(60.0, 64, 56, (0.02, -0.01, 0.0), gen.rot_y(2.0)) if res == 64 else sc.targets[0])
     views, keep = P.device_views(sc)
     g = api.Gaussians.build(views, sc.C, api.F32)
     ctx = api.Context()

@@ -127,8 +127,9 @@ def test_rasterize_equals_render():
     assert torch.equal(F, F2) and torch.equal(A, A2)
 
 
-@pytest.mark.parametrize("C,dtype", [(1, api.F32), (3, api.F32), (5, api.BF16), (8, api.BF16), (16, api.F32),
-                                     (33, api.F32), (64, api.BF16)])
+@pytest.mark.parametrize("C,dtype", [(1, api.F32), (3, api.F32), (5, api.BF16), (8, api.BF16), (12, api.BF16),
+                                     (16, api.F32), (24, api.F32), (32, api.F32), (32, api.BF16), (33, api.F32),
+                                     (64, api.BF16), (64, api.F32)])
 def test_channel_counts_and_dtypes(C, dtype):
     gs = gen.random_gaussians(3, 3000, C, center=(0, 0, 1.2), spread=0.25)
     g32 = O.Gaussians(gs.mean, gs.cov, gs.opac, gs.feat)

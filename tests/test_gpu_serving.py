@@ -207,3 +207,43 @@ def test_plain_mode_matches():
         F1, A1 = _solo(g, cam, sc.C)
         assert torch.equal(F, F1) and torch.equal(A, A1)
     plain.close()
+
+
+def test_server_eye_views_at_full_size_match_oracle():
+    """The serving workload at full size: one 2.1 M-Gaussian frame (four
+    1024x1024 source views, 32-channel BF16 features) and left+right eye views
+    of three viewers at 512x512, 768x768 and 1024x1024, submitted together to
+    a batching server with two lanes.  At 512x512 the frame's Gaussians are
+    sub-pixel and many tiles hold more pairs than one block sorts in shared
+    memory, so those views take the bucket sort's global-memory slab path.
+    Every served view is compared over its whole image with the FP64 oracle
+    (1e-4, the oracle fed the stored BF16 features), not with another GPU
+    render."""
+    from oracle import oracle as O
+    sc = gen.scene_frame(7)
+    g, keep = P.gpu_build(sc)
+    rng = np.random.default_rng(71)
+    cams = []
+    for res in (512, 768, 1024):
+        cams += gen.eye_cameras(rng, res, 1)
+    srv = api.Server(max_views_per_batch=8, max_lanes=2, max_width=1024, max_height=1024,
+                     max_gaussians=g.capacity, C=sc.C, feat_dtype=sc.feat_dtype, budget_bytes=24 << 30)
+    srv.update_frame(g)
+    outs = [(torch.empty((sc.C, c.height, c.width), device="cuda"), torch.empty((c.height, c.width), device="cuda"))
+            for c in cams]
+    torch.cuda.synchronize()
+    ids = [srv.submit(c, F, A) for c, (F, A) in zip(cams, outs)]
+    for i in ids:
+        srv.wait(i)
+    st = srv.stats()
+    assert st["completed"] == len(cams) and st["retried"] == 0
+    srv.close()
+    g32 = O.lift_scene(sc, "f32")
+    par = O.params_array()
+    slab_views = 0
+    for cam, (F, A) in zip(cams, outs):
+        orc = O.render(g32, cam, par)
+        counts = orc.bins.ranges[:, 1].astype(np.int64) - orc.bins.ranges[:, 0]
+        slab_views += int(counts.max() > 3840)
+        P.compare_render(F, A, orc, g32, cam, par, P.TOL_F32)
+    assert slab_views >= 2  # the 512x512 eye pair at least
