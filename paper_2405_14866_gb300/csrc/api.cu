@@ -106,6 +106,7 @@ struct tsplat_ctx {
     DBuf ranges, tfinal, last, views;
     DBuf zkeys;  // point z-buffer scratch
     DBuf torder; // composite tile order
+    DBuf tinfo;  // per position of that order: tile and list range
     DBuf fsplit; // (hi, lo) rows of a rasterize call's FP32 features
     // small words (SM_*): visible count, P, effective P, status, tile and unit counters, N
     DBuf small;
@@ -356,7 +357,8 @@ tsplat_status tsplat_ctx_destroy(tsplat_ctx *c) {
     cudaDeviceSynchronize();
     DBuf *bufs[] = {&c->hdr, &c->rect, &c->ntiles, &c->tmask, &c->dkey, &c->radius, &c->pk0, &c->pk1, &c->pv0,
                     &c->pv1, &c->tcnt,
-                    &c->ranges, &c->tfinal, &c->last, &c->views, &c->zkeys, &c->torder, &c->fsplit, &c->small};
+                    &c->ranges, &c->tfinal, &c->last, &c->views, &c->zkeys, &c->torder, &c->tinfo, &c->fsplit,
+                    &c->small};
     for (DBuf *b : bufs) release(*b);
     for (auto &row : c->ev)
         for (cudaEvent_t e : row)
@@ -394,6 +396,7 @@ static tsplat_status ensure_tiles(tsplat_ctx *c, int64_t n_tiles, cudaStream_t s
     const size_t T = (size_t)std::max<int64_t>(n_tiles, 1);
     TRY(grow(c->ranges, T * 8, s));
     TRY(grow(c->torder, T * 4, s));
+    TRY(grow(c->tinfo, T * 16, s));
     TRY(grow(c->tcnt, T * 8, s));  // counts, then fill cursors
     TRY(grow(c->views, sizeof(RenderView) * MAX_BATCH, s));
     return TSPLAT_OK;
@@ -401,7 +404,7 @@ static tsplat_status ensure_tiles(tsplat_ctx *c, int64_t n_tiles, cudaStream_t s
 
 static bool tiles_fit(const tsplat_ctx *c, int64_t n_tiles) {
     const size_t T = (size_t)std::max<int64_t>(n_tiles, 1);
-    return c->ranges.bytes >= T * 8 && c->torder.bytes >= T * 4 && c->tcnt.bytes >= T * 8 &&
+    return c->ranges.bytes >= T * 8 && c->torder.bytes >= T * 4 && c->tinfo.bytes >= T * 16 && c->tcnt.bytes >= T * 8 &&
            c->views.bytes >= sizeof(RenderView) * MAX_BATCH;
 }
 
@@ -482,6 +485,7 @@ static tsplat_status render_tail(tsplat_ctx *c, int64_t n_cap, const uint32_t *n
     bn.p_eff = sm + SM_PEFF;
     bn.tile_order = c->torder.as<uint32_t>();
     bn.tile_order_out = c->torder.as<uint32_t>();
+    bn.tile_info_out = c->tinfo.as<uint4>();
     bn.tile_ctr = sm + SM_BINCTR;
     bn.status = sm + SM_STATUS;
     launch_bin_scan(bn, s);
@@ -528,7 +532,7 @@ static tsplat_status render_tail(tsplat_ctx *c, int64_t n_cap, const uint32_t *n
     ca.status = sm + SM_STATUS;
     ca.tile_counter = sm + SM_TILECTR;
     ca.save = save ? 1 : 0;
-    ca.tile_order = c->torder.as<uint32_t>();
+    ca.tile_info = c->tinfo.as<uint4>();
     launch_composite(ca, s);
     TRY(check_launch("render: composite"));
     TRY(mark(c, prof, 5, s));

@@ -181,6 +181,7 @@ struct BinArgs {
     uint32_t *ids_out;           // [p_cap] instance ids in (tile, depth, id) order
     const uint32_t *tile_order;  // [n_slots] order the sort takes the tiles in
     uint32_t *tile_order_out;    // the same array, written by the scan
+    uint4 *tile_info_out;        // [n_slots] per position of that order: (tile, first, end, 0)
     uint32_t *tile_ctr;          // persistent-sort tile counter
     uint32_t *status;            // TSPLAT_ERR_CAPACITY when P > p_cap
 };
@@ -212,7 +213,7 @@ struct CompositeArgs {
     uint32_t *status;      // TSPLAT_ERR_TIMEOUT if a bounded wait expired
     uint32_t *tile_counter;  // next tile to hand out (0 at launch)
     int save;                // record T_final and the last blended index (backward)
-    const uint32_t *tile_order;  // tile taken at each ticket (longest lists first), or NULL
+    const uint4 *tile_info;  // per ticket (longest lists first): (tile, first, end, 0)
 };
 void launch_composite(const CompositeArgs &a, cudaStream_t s);
 

@@ -79,8 +79,12 @@ __global__ __launch_bounds__(256) void k_bin_fill(BinArgs a) {
     if (*a.p_dev > a.p_cap) {
         // the pairs do not fit: nothing is written and every tile is empty
         if (blockIdx.x == 0 && threadIdx.x == 0) set_status(a.status, TSPLAT_ERR_CAPACITY);
-        for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < a.n_slots; t += gridDim.x * blockDim.x)
+        for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < a.n_slots; t += gridDim.x * blockDim.x) {
             a.ranges[t] = make_uint2(0u, 0u);
+            uint32_t *info = reinterpret_cast<uint32_t *>(a.tile_info_out + t);  // (tile, first, end, 0)
+            info[1] = 0u;
+            info[2] = 0u;
+        }
         return;
     }
     const uint32_t ns = *a.n_stride;
@@ -228,7 +232,13 @@ __global__ __launch_bounds__(1024) void k_bin_scan(BinArgs a) {
         load_counts4(a.tile_cnt, t0, T, c);
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-            if (t0 + k < a.n_slots) a.tile_order_out[atomicAdd(&bc[order_bucket(c[k], t0 + k, T)], 1u)] = t0 + k;
+            if (t0 + k < a.n_slots) {
+                const uint32_t pos = atomicAdd(&bc[order_bucket(c[k], t0 + k, T)], 1u);
+                a.tile_order_out[pos] = t0 + k;
+                // the tile's range (written by this block's first loop, before the barriers)
+                const uint2 rg = a.ranges[t0 + k];
+                a.tile_info_out[pos] = make_uint4(t0 + k, rg.x, rg.y, 0u);
+            }
     }
 }
 

@@ -9,8 +9,10 @@
 // gathering each Gaussian's 32-byte projected record and feature row with
 // 16-byte asynchronous copies (cp.async) whose completion arrives on the
 // slot's mbarrier; consumer warps advance at their own pace and release
-// slots, so no CTA-wide barrier couples them.  (One-bulk-copy-per-record
-// staging through the TMA engine measured slower for this gather.)
+// slots, so no CTA-wide barrier couples them.  (Gathers through the TMA
+// engine measured slower for these 32- and 64-byte rows: one bulk copy per
+// row, and tensor-map gathers of four rows per instruction alike.)  The ids
+// of the next two slots are loaded ahead.
 //
 // Per slot a warp tests the 64 records against its block with each
 // Gaussian's alpha_min box (exact: outside it alpha < alpha_min, so skipping
@@ -41,9 +43,11 @@ constexpr int NTHR = (NCW + 1) * 32; // + 1 producer warp
 constexpr int SB = 64;               // Gaussians per ring slot
 constexpr int WROW = 24;             // bf16 per W row (16 used; 48-byte stride avoids bank conflicts)
 
-template <int CP>
+// Ring slots: as deep as two CTAs per SM allow (the ring is the slack that
+// lets a warp with little work in a slot run ahead of the slowest one).
+template <int CP, bool F32F>
 struct Ring {
-    static constexpr int N = CP <= 32 ? 8 : 4;  // ring slots (deeper where shared memory allows)
+    static constexpr int N = CP <= 16 ? 8 : (CP <= 32 ? (F32F ? 6 : 8) : (F32F ? 3 : 4));
 };
 
 constexpr uint32_t FINAL_TILE = 0xffffffffu;  // slot tile id of the last slot a CTA produces
@@ -57,7 +61,7 @@ struct RecPair {
 
 template <int CP, bool F32F>
 struct CompSmem {
-    static constexpr int RING = Ring<CP>::N;
+    static constexpr int RING = Ring<CP, F32F>::N;
     Header hdr[RING][SB + 1];  // entry SB of each slot: an empty record (alpha = 0 everywhere)
     __nv_bfloat16 fhi[RING][SB][CP + 8];  // rows padded by 16 B: spreads ldmatrix row reads over the banks
     __nv_bfloat16 flo[F32F ? RING : 1][F32F ? SB : 1][CP + 8];
@@ -138,20 +142,19 @@ __device__ void producer(CompSmem<CP, F32F> &S, const CompositeArgs &a, int lane
     uint32_t i = 0;  // slots produced so far (ring position and phase)
     bool timed_out = false;
     for (int32_t seq = 0;; ++seq) {
-        uint32_t t = 0;
-        if (lane == 0) t = atomicAdd(a.tile_counter, 1u);
-        t = __shfl_sync(FULL, t, 0);
-        const bool last_tile = t >= n_tiles;
-        if (!last_tile && a.tile_order) t = a.tile_order[t];
-        uint32_t first = 0;
-        int n = 0;
-        if (!last_tile) {
-            const uint2 rg = a.ranges[t];
-            first = rg.x;
-            n = (int)(rg.y - rg.x);
-        }
+        uint32_t tk = 0;
+        if (lane == 0) tk = atomicAdd(a.tile_counter, 1u);
+        tk = __shfl_sync(FULL, tk, 0);
+        const bool last_tile = tk >= n_tiles;
+        // the scan's table: tile and list range of each ticket in one load
+        const uint4 info = last_tile ? make_uint4(0u, 0u, 0u, 0u) : a.tile_info[tk];
+        const uint32_t t = info.x, first = info.y;
+        const int n = (int)(info.z - info.y);
+        // ids of the next two slots' Gaussians (two per lane each), loaded ahead
         uint32_t nid0 = lane < n ? a.ids[first + lane] : 0u;
         uint32_t nid1 = lane + 32 < n ? a.ids[first + lane + 32] : 0u;
+        uint32_t mid0 = SB + lane < n ? a.ids[first + SB + lane] : 0u;
+        uint32_t mid1 = SB + lane + 32 < n ? a.ids[first + SB + lane + 32] : 0u;
         for (int b = 0;; b += SB, ++i) {
             const int slot = (int)(i % RING);
             if (!mbar_wait(&S.empty[slot], ((i / RING) & 1) ^ 1, a.status)) {
@@ -165,9 +168,11 @@ __device__ void producer(CompSmem<CP, F32F> &S, const CompositeArgs &a, int lane
             const int cnt = end ? 0 : min(SB, n - b);
             if (!end) {
                 const uint32_t id0 = nid0, id1 = nid1;
-                const int nb = b + SB;
-                nid0 = nb + lane < n ? a.ids[first + nb + lane] : 0u;
-                nid1 = nb + lane + 32 < n ? a.ids[first + nb + lane + 32] : 0u;
+                nid0 = mid0;
+                nid1 = mid1;
+                const int nb = b + 2 * SB;
+                mid0 = nb + lane < n ? a.ids[first + nb + lane] : 0u;
+                mid1 = nb + lane + 32 < n ? a.ids[first + nb + lane + 32] : 0u;
                 if (lane < cnt) produce_one<CP, F32F>(S, a, slot, lane, id0, ns);
                 if (lane + 32 < cnt) produce_one<CP, F32F>(S, a, slot, lane + 32, id1, ns);
             }
@@ -321,8 +326,15 @@ __global__ __launch_bounds__(NTHR, 2) void k_composite(CompositeArgs a) {
             cur = FINAL_TILE;
         } else if (!wdone) {
             const int base = (int)S.base[slot];
-            // survivors of the alpha_min box test, in list order
-            const float fbx0 = (float)bx0, fbx1 = (float)(bx0 + 7), fby0 = (float)by0, fby1 = (float)(by0 + 3);
+            // survivors of the alpha_min box test, in list order, against the
+            // bounding box of the block's pixels that are still blending (a
+            // Gaussian that reaches only saturated pixels changes nothing)
+            const uint32_t live = __ballot_sync(FULL, !done);  // bit 8 r + c: pixel (c, r) of the block
+            const uint32_t rows = ((live & 0xffu) ? 1u : 0u) | ((live & 0xff00u) ? 2u : 0u) |
+                                  ((live & 0xff0000u) ? 4u : 0u) | ((live & 0xff000000u) ? 8u : 0u);
+            const uint32_t cols = (live | (live >> 8) | (live >> 16) | (live >> 24)) & 0xffu;
+            const float fbx0 = (float)(bx0 + __ffs(cols) - 1), fbx1 = (float)(bx0 + 31 - __clz(cols));
+            const float fby0 = (float)(by0 + __ffs(rows) - 1), fby1 = (float)(by0 + 31 - __clz(rows));
             const bool r0 = lane < cnt && box_hit(S.hdr[slot], lane, fbx0, fbx1, fby0, fby1);
             const bool r1 = lane + 32 < cnt && box_hit(S.hdr[slot], lane + 32, fbx0, fbx1, fby0, fby1);
             const uint32_t m0 = __ballot_sync(FULL, r0), m1 = __ballot_sync(FULL, r1);

@@ -1,5 +1,5 @@
 // Thin inline-PTX wrappers used by the compositing kernels: mbarriers,
-// non-tensor bulk copies (TMA engine), ldmatrix and the warp-level bf16 MMA.
+// ldmatrix and the warp-level bf16 MMA.
 // Every wait is bounded: a wait that exceeds its limit returns false so the
 // caller can record TSPLAT_ERR_TIMEOUT and leave.
 #pragma once
@@ -26,11 +26,6 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -53,16 +48,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, const 
         if ((it & 63) == 63 && abort && *reinterpret_cast<const volatile uint32_t *>(abort) != 0) return false;
     }
     return false;
-}
-
-// Bulk copy global -> shared (TMA engine, non-tensor), completion counted in
-// bytes on `bar`.  dst/src 16-byte aligned, bytes a multiple of 16.
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
 }
 
 __device__ __forceinline__ void ldsm_x4(uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3, const void *p) {
