@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-diff", action="store_true")
     ap.add_argument("--no-rig", action="store_true")
+    ap.add_argument("--only", choices=["all", "diff"], default="all",
+                    help="diff: only the differentiation section (a small case for profiling its kernels)")
     return ap.parse_args()
 
 
@@ -1013,6 +1015,13 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.only == "diff":
+        import torch
+
+        from paper_2405_14866_gb300 import api
+        torch.cuda.set_device(0)
+        print(json.dumps({"differentiation": diff_bench(api, torch, steps=args.steps, warmup=args.warmup)}), flush=True)
+        return 0
     return run_ours(args)
 
 

@@ -70,58 +70,46 @@ __device__ __forceinline__ void stage(const Header *__restrict__ hdr, const FT *
     }
 }
 
-// Warp totals of NV per-lane values (NV a power of two) with NV - 1 + ...
-// shuffles instead of 5 NV: at each level a lane keeps one half of its
-// values and receives the partner's partial sums of that half.  Afterwards,
-// for NV >= 32, lane l holds in v[i] the total of value l * (NV / 32) + i;
-// for NV < 32, lanes with (l & (32 / NV - 1)) == 0 hold in v[0] the total of
-// value l / (32 / NV).
-template <int NV>
-__device__ __forceinline__ void warp_transpose_sum(float (&v)[NV], int lane) {
-    int n = NV;
-#pragma unroll
-    for (int b = 16; b > 0; b >>= 1) {
-        if (n > 1) {
-            const int half = n / 2;
-            const bool upper = (lane & b) != 0;
-#pragma unroll
-            for (int i = 0; i < NV / 2; ++i) {
-                if (i < half) {
-                    const float keep = upper ? v[i + half] : v[i];
-                    const float send = upper ? v[i] : v[i + half];
-                    v[i] = keep + __shfl_xor_sync(FULL, send, b);
-                }
-            }
-            n = half;
-        } else {
-            v[0] += __shfl_xor_sync(FULL, v[0], b);
-        }
-    }
-}
-
-// Feature gradients of a group of up to 16 contributing Gaussians of one
-// warp as a tensor-core product: dF_j[c] = sum over the warp's 32 pixels of
+// Per-warp shared state of the gradient reductions.
+//
+// Feature gradients of a group of up to 16 contributing Gaussians as a
+// tensor-core product: dF_j[c] = sum over the warp's 32 pixels of
 // w_j(p) g_p[c], i.e. D (16 x C) = W^T (16 x 32) G (32 x C), with W and G
-// split into bf16 hi + lo parts (three products, FP32 accumulation).
-// W is stored per pixel row ([32][BWROW]), G likewise ([32][CP16 + 8]).
-constexpr int BWROW = 24;
+// split into bf16 hi + lo parts (three products, FP32 accumulation).  W^T is
+// stored row per Gaussian (each lane writes its pixel's column: no bank
+// conflicts), G row per pixel.
+//
+// Geometric gradients of a batch of MB Gaussians from per-pixel moments:
+// with dq the gradient of the exponent at a pixel and (dx, dy) its offset
+// from the mean, sum_p dq (a dx + b dy) = a M1 + b M2 for the mean and
+// -M3/2, -M4, -M5/2 for the conic, where M1 = sum dq dx, M2 = sum dq dy,
+// M3 = sum dq dx^2, M4 = sum dq dx dy, M5 = sum dq dy^2 (M0 = sum of the
+// opacity terms).  Each lane writes its pixel's six terms into its own row
+// (odd row stride: conflict-free writes and column reads); a flush sums the
+// 6 MB columns over the 32 pixels, one column per lane, instead of a chain
+// of shuffles per Gaussian.
+constexpr int WTROW = 40;  // bf16 per W^T row (32 used; 80-byte stride spreads ldmatrix rows over the banks)
 template <int CP>
 struct BwdGroup {
     static constexpr int GP = CP < 16 ? 16 : CP;  // channels padded to whole k16 / n16 blocks
-    __nv_bfloat16 wh[CT / 32][32][BWROW];
-    __nv_bfloat16 wl[CT / 32][32][BWROW];
+    static constexpr int MB = CP <= 16 ? 4 : 2;   // Gaussians per geometric batch
+    static constexpr int MW = 6 * MB + 1;         // floats per moment row (odd)
+    __nv_bfloat16 wth[CT / 32][16][WTROW];
+    __nv_bfloat16 wtl[CT / 32][16][WTROW];
     __nv_bfloat16 gh[CT / 32][32][GP + 8];
     __nv_bfloat16 gl[CT / 32][32][GP + 8];
     uint32_t gid[CT / 32][16];
+    float mom[CT / 32][32][MW];  // per pixel: the pending batch's moment terms, Gaussian-major
+    float4 mrec[CT / 32][MB];    // the batch's Gaussians: conic (a, b, c) and id (bits)
 };
 
 template <int CP>
 __device__ __forceinline__ void flush_feat_grads(BwdGroup<CP> &B, int warp, int lane, int cnt, int C,
                                                  float *d_feat) {
     constexpr int GP = BwdGroup<CP>::GP;
-    for (int k = cnt; k < 16; ++k) {  // unused columns contribute nothing
-        B.wh[warp][lane][k] = __float2bfloat16_rn(0.0f);
-        B.wl[warp][lane][k] = __float2bfloat16_rn(0.0f);
+    for (int k = cnt; k < 16; ++k) {  // unused rows contribute nothing
+        B.wth[warp][k][lane] = __float2bfloat16_rn(0.0f);
+        B.wtl[warp][k][lane] = __float2bfloat16_rn(0.0f);
     }
     __syncwarp();
     float acc[GP / 8][4];
@@ -130,13 +118,13 @@ __device__ __forceinline__ void flush_feat_grads(BwdGroup<CP> &B, int warp, int 
 #pragma unroll
         for (int e = 0; e < 4; ++e) acc[t][e] = 0.0f;
     const int kl = ((lane >> 3) & 1) * 8 + (lane & 7);        // B: pixel row this lane addresses
-    const int arow = ((lane >> 4) & 1) * 8 + (lane & 7);      // A (transposed load): pixel row
-    const int acol = ((lane >> 3) & 1) * 8, bcol = (lane >> 4) * 8;
+    const int arow = ((lane >> 3) & 1) * 8 + (lane & 7);      // A: Gaussian row this lane addresses
+    const int acol = (lane >> 4) * 8, bcol = (lane >> 4) * 8;
 #pragma unroll
     for (int ks = 0; ks < 2; ++ks) {  // two k-steps of 16 pixels
         uint32_t ah[4], al[4];
-        ldsm_x4_t(ah[0], ah[1], ah[2], ah[3], &B.wh[warp][ks * 16 + arow][acol]);
-        ldsm_x4_t(al[0], al[1], al[2], al[3], &B.wl[warp][ks * 16 + arow][acol]);
+        ldsm_x4(ah[0], ah[1], ah[2], ah[3], &B.wth[warp][arow][ks * 16 + acol]);
+        ldsm_x4(al[0], al[1], al[2], al[3], &B.wtl[warp][arow][ks * 16 + acol]);
 #pragma unroll
         for (int p = 0; p < GP / 16; ++p) {
             uint32_t bh[4], bl[4];
@@ -158,6 +146,36 @@ __device__ __forceinline__ void flush_feat_grads(BwdGroup<CP> &B, int warp, int 
             const int j = (lane >> 2) + ((e >> 1) << 3), c = t * 8 + 2 * (lane & 3) + (e & 1);
             if (j < cnt && c < C) atomicAdd(&d_feat[(size_t)B.gid[warp][j] * C + c], acc[t][e]);
         }
+    __syncwarp();
+}
+
+// Geometric gradients of the nb pending Gaussians: lane 6 g + k sums moment
+// column k of Gaussian g over the 32 pixels and adds its gradient (k = 0:
+// opacity; 1, 2: mean x, y; 3, 4, 5: conic a, b, c).
+template <int CP>
+__device__ __forceinline__ void flush_geo_grads(BwdGroup<CP> &B, int warp, int lane, int nb, const BackwardArgs &a) {
+    __syncwarp();
+    const int col = lane < 6 * nb ? lane : 0;
+    float s[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int p = 0; p < 32; ++p) s[p & 3] += B.mom[warp][p][col];
+    const float S = (s[0] + s[1]) + (s[2] + s[3]);
+    // mean x needs M2 of the next lane, mean y M1 of the previous one
+    const float next = __shfl_down_sync(FULL, S, 1), prev = __shfl_up_sync(FULL, S, 1);
+    if (lane < 6 * nb) {
+        const int g = lane / 6, k = lane - 6 * g;
+        const float4 r = B.mrec[warp][g];
+        const size_t id = __float_as_uint(r.w);
+        const float v = k == 0 ? S
+                      : k == 1 ? fmaf(r.x, S, r.y * next)
+                      : k == 2 ? fmaf(r.y, prev, r.z * S)
+                      : k == 4 ? -S
+                               : -0.5f * S;
+        float *dst = k == 0 ? (a.d_opac ? a.d_opac + id : nullptr)
+                   : k <= 2 ? (a.d_mean2d ? a.d_mean2d + 2 * id + (k - 1) : nullptr)
+                            : (a.d_conic ? a.d_conic + 3 * id + (k - 3) : nullptr);
+        if (dst) atomicAdd(dst, v);
+    }
     __syncwarp();
 }
 
@@ -225,7 +243,8 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
 #pragma unroll
     for (int c = 0; c < CP / 2; ++c) g2[c] = f2pack(g[2 * c], g[2 * c + 1]);
     const unsigned long long fp2 = f2pack(fpx, fpy);
-    int gs = 0;  // contributing Gaussians collected in this warp's current group
+    int gs = 0;  // contributing Gaussians collected in this warp's current feature group
+    int bs = 0;  // and in its current geometric batch
     const uint32_t wmax = __reduce_max_sync(FULL, lastk);
     float sg = 0.0f;  // <S, g>: blended features behind the current Gaussian
     // Each warp walks its own list range [0, wmax) back to front in chunks of
@@ -295,30 +314,34 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
                 const uint32_t id = w_id[j];
                 if (a.d_feat) {  // collect w for the group's tensor-core product
                     const __nv_bfloat16 wh = __float2bfloat16_rn(wgt);
-                    BG.wh[warp][lane][gs] = wh;
-                    BG.wl[warp][lane][gs] = __float2bfloat16_rn(wgt - __bfloat162float(wh));
+                    BG.wth[warp][gs][lane] = wh;
+                    BG.wtl[warp][gs][lane] = __float2bfloat16_rn(wgt - __bfloat162float(wh));
                     if (lane == 0) BG.gid[warp][gs] = id;
                     if (++gs == 16) {
                         flush_feat_grads<CP>(BG, warp, lane, 16, a.C, a.d_feat);
                         gs = 0;
                     }
                 }
-                const float ca = -2.0f * h0.z, cb = -h0.w, cc = -2.0f * h1.x;  // conic from the record
-                float gv[8] = {d_o, dq * (ca * dx + cb * dy), dq * (cb * dx + cc * dy), dq * (-0.5f * dx * dx),
-                               dq * (-dx * dy), dq * (-0.5f * dy * dy), 0.0f, 0.0f};
-                warp_transpose_sum<8>(gv, lane);
-                if ((lane & 3) == 0) {  // lane 4k holds value k: opacity, mean x, y, conic a, b, c
-                    const int k = lane >> 2;
-                    float *dst = nullptr;
-                    if (k == 0) dst = a.d_opac ? a.d_opac + id : nullptr;
-                    else if (k <= 2) dst = a.d_mean2d ? a.d_mean2d + 2 * (size_t)id + (k - 1) : nullptr;
-                    else if (k <= 5) dst = a.d_conic ? a.d_conic + 3 * (size_t)id + (k - 3) : nullptr;
-                    if (dst) atomicAdd(dst, gv[0]);
+                // this pixel's moment terms (zero where it does not contribute)
+                float *mm = &BG.mom[warp][lane][6 * bs];
+                const float m1 = dq * dx, m2 = dq * dy;
+                mm[0] = d_o;
+                mm[1] = m1;
+                mm[2] = m2;
+                mm[3] = m1 * dx;
+                mm[4] = m1 * dy;
+                mm[5] = m2 * dy;
+                if (lane == 0)  // the conic (a, b, c) from the record, and the id
+                    BG.mrec[warp][bs] = make_float4(-2.0f * h0.z, -h0.w, -2.0f * h1.x, __uint_as_float(id));
+                if (++bs == BwdGroup<CP>::MB) {
+                    flush_geo_grads<CP>(BG, warp, lane, bs, a);
+                    bs = 0;
                 }
             }
         }
     }
     if (gs > 0) flush_feat_grads<CP>(BG, warp, lane, gs, a.C, a.d_feat);
+    if (bs > 0) flush_geo_grads<CP>(BG, warp, lane, bs, a);
     }
 }
 
