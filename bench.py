@@ -352,9 +352,11 @@ class ServeLoad:
         return out
 
 
-def serving_bench(api, torch, sc, g, views, seconds=1.5):
+def serving_bench(api, torch, sc, g, views, seconds=1.0, repeats=3):
     """Batched, graph-replayed, overlapped serving vs plain one launch
-    sequence per view behind the same queue (same frames, same requests)."""
+    sequence per view behind the same queue (same frames, same requests).
+    Every offered rate is run `repeats` times (different arrival seeds); the
+    p99 < 8 ms gate is decided on the median p99 of the repeats."""
     g2 = api.Gaussians.build(views, sc.C, sc.feat_dtype)
     torch.cuda.synchronize()
     load = ServeLoad(api, torch, sc, [g, g2], views)
@@ -381,15 +383,25 @@ def serving_bench(api, torch, sc, g, views, seconds=1.5):
     sat = {k: load.burst(srv, viewers4, 400) for k, srv in servers.items()}
     sat["ratio"] = sat["server"]["views_per_s"] / max(sat["plain"]["views_per_s"], 1e-9)
     out["saturation"] = sat
+    def repeated(srv, nv):
+        """`repeats` open-loop runs at nv viewers: median p99 and views/s, spread."""
+        viewers = load.viewers(nv, seed=100 + nv)
+        runs = [load.poisson(srv, viewers, seconds, seed=1000 * r + nv) for r in range(repeats)]
+        p99 = sorted(r["p99_ms"] for r in runs)
+        vps = sorted(r["views_per_s"] for r in runs)
+        return {"p99_ms": p99[len(p99) // 2], "p99_ms_min": p99[0], "p99_ms_max": p99[-1],
+                "views_per_s": vps[len(vps) // 2], "views_per_s_min": vps[0], "views_per_s_max": vps[-1],
+                "p50_ms": sorted(r["p50_ms"] for r in runs)[len(runs) // 2], "repeats": len(runs),
+                "retried": sum(r["retried"] for r in runs)}
+
     sweep = []
     for nv in (4, 8, 12, 16, 20, 24, 28, 32, 40):
-        viewers = load.viewers(nv, seed=100 + nv)
         row = {"viewers": nv, "offered_views_per_s": 60.0 * nv}
         for k, srv in servers.items():
             if 60.0 * nv > 1.1 * sat[k]["views_per_s"]:
                 row[k] = None  # beyond this server's saturation throughput: the queue only grows
                 continue
-            row[k] = load.poisson(srv, viewers, seconds, seed=nv)
+            row[k] = repeated(srv, nv)
         sweep.append(row)
     out["poisson"] = sweep
 
@@ -406,7 +418,7 @@ def serving_bench(api, torch, sc, g, views, seconds=1.5):
             if lo is None or hi is None or hi - lo < 2:
                 break
             mid = (lo + hi) // 2
-            r = load.poisson(srv, load.viewers(mid, seed=100 + mid), seconds, seed=mid)
+            r = repeated(srv, mid)
             refine[k].append({"viewers": mid, **r})
             if r["p99_ms"] < 8.0:
                 lo = mid
@@ -423,8 +435,43 @@ def serving_bench(api, torch, sc, g, views, seconds=1.5):
     b = out["best_views_per_s_p99_under_8ms"]
     b["ratio"] = b["server"] / b["plain"] if b["server"] and b["plain"] else None
     out["frames_rebuilt"] = load.frames
+    out["server"]["pair_scale"] = servers["server"].stats()["pair_scale"]
     for srv in servers.values():
         srv.close()
+    # where a batch's time goes: stage split of one batched render of eight
+    # eye views (two viewers per size), against each size rendered alone
+    from paper_2405_14866_gb300 import gen
+    rng = np.random.default_rng(5)
+    cams = []
+    for res in (512, 768, 1024, 1024):
+        cams += gen.eye_cameras(rng, res, 1)
+    bctx, sctx = api.Context(), api.Context()
+    Fs = [torch.empty((sc.C, c.height, c.width), device="cuda") for c in cams]
+    As = [torch.empty((c.height, c.width), device="cuda") for c in cams]
+    bctx.render_batch(g, cams, out_feat=Fs, out_alpha=As)
+    for _ in range(3):
+        bctx.render_batch(g, cams, async_=True, out_feat=Fs, out_alpha=As)
+    torch.cuda.synchronize()
+    for _ in range(10):
+        bctx.render_batch(g, cams, async_=True, out_feat=Fs, out_alpha=As, profile=True)
+    batch_stages = bctx.timings()
+    bctx.status()
+    solo = {}
+    for res in (512, 768, 1024):
+        c = [x for x in cams if x.width == res][0]
+        F1, A1 = sctx.render(g, c)
+        sctx.reserve(g.capacity, int(sctx.stats()["n_pairs"] * 1.25) + 65536, res, res, sc.C)
+        for _ in range(3):
+            sctx.render(g, c, async_=True, out_feat=F1, out_alpha=A1)
+        for _ in range(10):
+            sctx.render(g, c, async_=True, out_feat=F1, out_alpha=A1, profile=True)
+        solo[f"{res}x{res}"] = {"stages_ms": {k: round(v, 4) for k, v in sctx.timings().items()},
+                                "pairs": sctx.stats()["n_pairs"]}
+        sctx.status()
+    out["stage_split"] = {"batch_of_8": {"views": [f"{c.width}x{c.height}" for c in cams],
+                                         "stages_ms": {k: round(v, 4) for k, v in batch_stages.items()},
+                                         "ms_per_view": round(sum(batch_stages.values()) / len(cams), 4)},
+                          "single_views": solo}
     return out
 
 

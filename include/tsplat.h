@@ -455,7 +455,9 @@ typedef struct {
     int32_t C, feat_dtype;        /* of the frames (32, TSPLAT_BF16) */
     /* admission estimate of a view's (Gaussian, tile) pairs:
      * pairs_per_gaussian x frame capacity + pairs_per_pixel x width x height;
-     * a lane holds max_views_per_batch maximal views' worth */
+     * a lane's pair buffer holds max_views_per_batch maximal views' worth.
+     * Once batches retire, admission scales the estimates by the running
+     * ratio of their measured to estimated pairs (plus a 10 % margin) */
     float pairs_per_gaussian;     /* (2.5) */
     float pairs_per_pixel;        /* (1.0) */
     int32_t flags;                /* TSPLAT_SERVER_* (0) */
@@ -470,6 +472,7 @@ typedef struct {
     int32_t lanes, reserved;
     double p50_ms, p99_ms, max_ms;  /* request latency, submission to completion */
     double views_per_s;             /* completed / (last completion - first submission) */
+    double pair_scale;              /* measured / estimated pairs of retired batches (running; 0 = none yet) */
 } tsplat_server_stats;
 
 void tsplat_server_config_default(tsplat_server_config *cfg);

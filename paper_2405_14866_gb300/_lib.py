@@ -55,7 +55,8 @@ class CServerConfig(Structure):
 class CServerStats(Structure):
     _fields_ = [("completed", c_int64), ("batches", c_int64), ("views_launched", c_int64), ("retried", c_int64),
                 ("pending", c_int64), ("lane_bytes", c_int64), ("lanes", c_int32), ("reserved", c_int32), ("p50_ms", ctypes.c_double),
-                ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double), ("views_per_s", ctypes.c_double)]
+                ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double), ("views_per_s", ctypes.c_double),
+                ("pair_scale", ctypes.c_double)]
 
 
 class CStats(Structure):

@@ -932,4 +932,5 @@ tsplat_status ctx_reserve_batch(tsplat_ctx *c, int64_t instances, int64_t pairs,
 RenderView *ctx_view_table(tsplat_ctx *c) { return c->views.as<RenderView>(); }
 int64_t ctx_pair_capacity(const tsplat_ctx *c) { return c->p_cap; }
 uint32_t *ctx_status_word(tsplat_ctx *c) { return small_ptr(c, SM_STATUS); }
+uint32_t *ctx_pairs_word(tsplat_ctx *c) { return small_ptr(c, SM_P); }
 }  // namespace tsp

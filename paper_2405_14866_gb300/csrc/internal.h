@@ -268,6 +268,7 @@ tsplat_status ctx_reserve_batch(tsplat_ctx *c, int64_t instances, int64_t pairs,
 RenderView *ctx_view_table(tsplat_ctx *c);
 int64_t ctx_pair_capacity(const tsplat_ctx *c);
 uint32_t *ctx_status_word(tsplat_ctx *c);  // device word written by the kernels of a render
+uint32_t *ctx_pairs_word(tsplat_ctx *c);   // device word: the last render's pair count P (all its views)
 // tsplat_render_batch; with table_on_device the projection reads the view
 // table from ctx_view_table(ctx), written there by the caller before the
 // launch (so that a captured graph can be replayed for other views).

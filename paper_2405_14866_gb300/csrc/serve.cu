@@ -8,7 +8,9 @@
 // the device at a time, so up to n_lanes batches overlap.  The number of
 // lanes follows from the memory budget.  Whenever a lane is free and
 // requests are pending, the worker admits them in arrival order while the
-// batch's estimated (Gaussian, tile) pairs fit the lane's pair buffer, and
+// batch's estimated (Gaussian, tile) pairs fit the lane's pair buffer (the
+// configured per-view estimate, scaled by the running ratio of measured to
+// estimated pairs of the batches already retired), and
 // launches the batch as one replay of a CUDA graph captured per (frame
 // Gaussians, number of views); only the view table (cameras, output
 // buffers, tile offsets) of the graph's projection launch is rewritten
@@ -81,6 +83,8 @@ struct Lane {
     size_t prepared = 0;                       // prepare requests this lane has carried out
     float *dummy = nullptr;          // output of the warm-up run (16 x 16 views)
     uint32_t *status_host = nullptr; // pinned copy of the batch's device status word
+    uint32_t *pairs_host = nullptr;  // pinned copy of the batch's pair count
+    int64_t est = 0;                 // the batch's estimated pairs (configured estimate, unscaled)
     RenderView *table_host = nullptr; // pinned staging of the batch's view table
 };
 
@@ -105,6 +109,9 @@ struct tsplat_server {
     // statistics
     std::vector<double> latencies;
     uint64_t batches = 0, views = 0, retries = 0;
+    // admission: measured / estimated pairs of retired batches, a running
+    // average (0 until the first batch retires, then the estimates scale by it)
+    double pair_scale = 0.0;
     double t_first = 0, t_last = 0;
     int device = 0;
 };
@@ -246,9 +253,13 @@ tsplat_status issue_batch(tsplat_server &S, Lane &L, const tsplat_gaussians *g, 
     if (st != TSPLAT_OK) return st;
     if (cudaMemcpyAsync(L.status_host, ctx_status_word(L.ctx), sizeof(uint32_t), cudaMemcpyDeviceToHost, L.stream) !=
             cudaSuccess ||
+        cudaMemcpyAsync(L.pairs_host, ctx_pairs_word(L.ctx), sizeof(uint32_t), cudaMemcpyDeviceToHost, L.stream) !=
+            cudaSuccess ||
         cudaEventRecord(L.done, L.stream) != cudaSuccess)
         return record_error(TSPLAT_ERR_CUDA, "serve: status copy or event record failed");
     std::lock_guard<std::mutex> lock(S.mu);
+    L.est = 0;
+    for (uint64_t id : ids) L.est += S.reqs[id].est_pairs;
     L.busy = true;
     L.frame = g;
     L.reqs = ids;
@@ -286,8 +297,13 @@ void worker_main(tsplat_server *Sp) {
         for (Lane &L : S.lanes) {
             if (!L.busy || cudaEventQuery(L.done) != cudaSuccess) continue;
             const tsplat_status dst = (tsplat_status)*reinterpret_cast<volatile uint32_t *>(L.status_host);
+            const uint32_t pairs = *reinterpret_cast<volatile uint32_t *>(L.pairs_host);
             const double t = now_ms();
             std::lock_guard<std::mutex> lock(S.mu);
+            if ((dst == TSPLAT_OK || dst == TSPLAT_ERR_CAPACITY) && L.est > 0) {  // the scan counts P either way
+                const double r = (double)pairs / (double)L.est;
+                S.pair_scale = S.pair_scale > 0.0 ? 0.8 * S.pair_scale + 0.2 * r : r;
+            }
             if (dst == TSPLAT_ERR_CAPACITY && L.reqs.size() > 1) {
                 // pairs overflowed the lane: run these views again one at a time
                 for (auto it = L.reqs.rbegin(); it != L.reqs.rend(); ++it) {
@@ -337,14 +353,16 @@ void worker_main(tsplat_server *Sp) {
                 }
                 frame = S.frame;
                 const int64_t cap = (int64_t)(0.9 * (double)ctx_pair_capacity(L.ctx));
+                const double scale = S.pair_scale > 0.0 ? 1.1 * S.pair_scale : 1.0;  // 10 % margin
                 int64_t used = 0;
                 while (!S.pending.empty() && (int)batch.size() < room) {
                     Request &r = S.reqs[S.pending.front()];
-                    if (!batch.empty() && (r.solo || used + r.est_pairs > cap)) break;
+                    const int64_t need = (int64_t)ceil(scale * (double)r.est_pairs);
+                    if (!batch.empty() && (r.solo || used + need > cap)) break;
                     batch.push_back(S.pending.front());
                     S.pending.pop_front();
                     r.state = REQ_RUNNING;
-                    used += r.est_pairs;
+                    used += need;
                     if (r.solo) break;
                 }
             }
@@ -427,6 +445,7 @@ tsplat_status tsplat_server_create(const tsplat_server_config *cfg, tsplat_serve
                                 cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming) != cudaSuccess ||
                                 cudaMalloc(&L.dummy, sizeof(float) * 16 * 16 * (cfg->C + 1)) != cudaSuccess ||
                                 cudaMallocHost(&L.status_host, sizeof(uint32_t)) != cudaSuccess ||
+                                cudaMallocHost(&L.pairs_host, sizeof(uint32_t)) != cudaSuccess ||
                                 cudaMallocHost(&L.table_host, sizeof(RenderView) * MAX_BATCH) != cudaSuccess))
             st = record_error(TSPLAT_ERR_CUDA, "server_create: stream/event allocation failed");
         if (st != TSPLAT_OK) {
@@ -456,6 +475,7 @@ tsplat_status tsplat_server_destroy(tsplat_server *S) {
         if (L.stream) cudaStreamDestroy(L.stream);
         if (L.dummy) cudaFree(L.dummy);
         if (L.status_host) cudaFreeHost(L.status_host);
+        if (L.pairs_host) cudaFreeHost(L.pairs_host);
         if (L.table_host) cudaFreeHost(L.table_host);
         if (L.ctx) tsplat_ctx_destroy(L.ctx);
     }
@@ -584,6 +604,7 @@ tsplat_status tsplat_server_get_stats(tsplat_server *S, tsplat_server_stats *out
     out->lanes = (int32_t)S->lanes.size();
     out->lane_bytes = S->lane_bytes;
     out->pending = (int64_t)S->pending.size();
+    out->pair_scale = S->pair_scale;
     if (!l.empty()) {
         std::sort(l.begin(), l.end());
         auto pct = [&](double q) { return l[std::min(l.size() - 1, (size_t)floor(q * (double)(l.size() - 1) + 0.5))]; };

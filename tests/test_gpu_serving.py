@@ -117,15 +117,29 @@ def test_server_admission_overflow_is_retried_one_view_at_a_time():
     assert two.stats()["lanes"] == 2
     two.close()
     srv = api.Server(max_lanes=4, budget_bytes=int(1.5 * lane), **kw)
-    srv.update_frame(g)
     cams = _cams(np.random.default_rng(4), 8, [(96, 96)])
     outs = [(torch.empty((sc.C, 96, 96), device="cuda"), torch.empty((96, 96), device="cuda")) for _ in cams]
     torch.cuda.synchronize()
+    # all eight wait for a frame, so the first batch takes them together on
+    # the underestimate alone
     ids = [srv.submit(c, F, A) for c, (F, A) in zip(cams, outs)]
+    srv.update_frame(g)
     for i in ids:
         srv.wait(i)
     st = srv.stats()
     assert st["lanes"] == 1 and st["retried"] > 0 and st["completed"] == 8
+    for cam, (F, A) in zip(cams, outs):
+        F1, A1 = _solo(g, cam, sc.C)
+        assert torch.equal(F, F1) and torch.equal(A, A1)
+    # the retired batches taught admission the real pair count (about 1 / 0.35
+    # of the estimate): a second round is admitted without overflowing
+    assert 1.5 < st["pair_scale"] < 6.0, st["pair_scale"]
+    retried = st["retried"]
+    ids = [srv.submit(c, F, A) for c, (F, A) in zip(cams, outs)]
+    for i in ids:
+        srv.wait(i)
+    st = srv.stats()
+    assert st["completed"] == 16 and st["retried"] == retried, st
     for cam, (F, A) in zip(cams, outs):
         F1, A1 = _solo(g, cam, sc.C)
         assert torch.equal(F, F1) and torch.equal(A, A1)
