@@ -84,28 +84,30 @@ __device__ __forceinline__ void stage(const Header *__restrict__ hdr, const FT *
 // from the mean, sum_p dq (a dx + b dy) = a M1 + b M2 for the mean and
 // -M3/2, -M4, -M5/2 for the conic, where M1 = sum dq dx, M2 = sum dq dy,
 // M3 = sum dq dx^2, M4 = sum dq dx dy, M5 = sum dq dy^2 (M0 = sum of the
-// opacity terms).  Each lane writes its pixel's six terms into its own row
-// (odd row stride: conflict-free writes and column reads); a flush sums the
-// 6 MB columns over the 32 pixels, one column per lane, instead of a chain
-// of shuffles per Gaussian.
+// opacity terms).  The batch's 6 MB moment terms are stored column-major, a
+// column of 32 pixels per term: each lane writes its pixel's entry of six
+// columns (consecutive words: conflict-free), and a flush sums the columns,
+// one per lane, with 16-byte loads (column stride 36 words: the eight lanes
+// of a load phase fall into distinct bank groups), instead of a chain of
+// shuffles per Gaussian.
 constexpr int WTROW = 40;  // bf16 per W^T row (32 used; 80-byte stride spreads ldmatrix rows over the banks)
+constexpr int MSTRIDE = 36;  // floats per moment column (32 used)
 template <int CP>
 struct BwdGroup {
     static constexpr int GP = CP < 16 ? 16 : CP;  // channels padded to whole k16 / n16 blocks
-    static constexpr int MB = CP <= 16 ? 4 : 2;   // Gaussians per geometric batch
-    static constexpr int MW = 6 * MB + 1;         // floats per moment row (odd)
+    static constexpr int MB = CP <= 16 ? 5 : 2;   // Gaussians per geometric batch (6 MB columns <= 32 lanes)
     __nv_bfloat16 wth[CT / 32][16][WTROW];
     __nv_bfloat16 wtl[CT / 32][16][WTROW];
     __nv_bfloat16 gh[CT / 32][32][GP + 8];
     __nv_bfloat16 gl[CT / 32][32][GP + 8];
     uint32_t gid[CT / 32][16];
-    float mom[CT / 32][32][MW];  // per pixel: the pending batch's moment terms, Gaussian-major
-    float4 mrec[CT / 32][MB];    // the batch's Gaussians: conic (a, b, c) and id (bits)
+    float mom[CT / 32][6 * MB][MSTRIDE];  // per moment term of the pending batch: its 32 pixels
+    float4 mrec[CT / 32][MB];              // the batch's Gaussians: conic (a, b, c) and id (bits)
 };
 
 template <int CP>
 __device__ __forceinline__ void flush_feat_grads(BwdGroup<CP> &B, int warp, int lane, int cnt, int C,
-                                                 float *d_feat) {
+                                                 float *d_feat, bool vec4) {
     constexpr int GP = BwdGroup<CP>::GP;
     for (int k = cnt; k < 16; ++k) {  // unused rows contribute nothing
         B.wth[warp][k][lane] = __float2bfloat16_rn(0.0f);
@@ -139,13 +141,29 @@ __device__ __forceinline__ void flush_feat_grads(BwdGroup<CP> &B, int warp, int 
         }
     }
     // D fragment: Gaussian rows lane/4 (+8), channel columns 2(lane%4) (+1)
+    if (vec4) {
+        // lanes 2i and 2i + 1 swap halves: the even lane then holds four
+        // consecutive channels of row lane/4, the odd lane those of row
+        // lane/4 + 8, each added by one 16-byte atomic
+        const bool odd = lane & 1;
+        const int j = (lane >> 2) + (odd ? 8 : 0);
 #pragma unroll
-    for (int t = 0; t < GP / 8; ++t)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int j = (lane >> 2) + ((e >> 1) << 3), c = t * 8 + 2 * (lane & 3) + (e & 1);
-            if (j < cnt && c < C) atomicAdd(&d_feat[(size_t)B.gid[warp][j] * C + c], acc[t][e]);
+        for (int t = 0; t < GP / 8; ++t) {
+            const float sx = odd ? acc[t][0] : acc[t][2], sy = odd ? acc[t][1] : acc[t][3];
+            const float rx = __shfl_xor_sync(FULL, sx, 1), ry = __shfl_xor_sync(FULL, sy, 1);
+            const float4 v = odd ? make_float4(rx, ry, acc[t][2], acc[t][3]) : make_float4(acc[t][0], acc[t][1], rx, ry);
+            const int c = t * 8 + 4 * ((lane >> 1) & 1);
+            if (j < cnt && c < C) atomicAdd(reinterpret_cast<float4 *>(&d_feat[(size_t)B.gid[warp][j] * C + c]), v);
         }
+    } else {
+#pragma unroll
+        for (int t = 0; t < GP / 8; ++t)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int j = (lane >> 2) + ((e >> 1) << 3), c = t * 8 + 2 * (lane & 3) + (e & 1);
+                if (j < cnt && c < C) atomicAdd(&d_feat[(size_t)B.gid[warp][j] * C + c], acc[t][e]);
+            }
+    }
     __syncwarp();
 }
 
@@ -156,10 +174,20 @@ template <int CP>
 __device__ __forceinline__ void flush_geo_grads(BwdGroup<CP> &B, int warp, int lane, int nb, const BackwardArgs &a) {
     __syncwarp();
     const int col = lane < 6 * nb ? lane : 0;
-    float s[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    // pixels p = 4 i + r summed per r in pixel order, two r at a time
+    const float4 *cv = reinterpret_cast<const float4 *>(&B.mom[warp][col][0]);
+    float4 v = cv[0];
+    unsigned long long s01 = f2pack(v.x, v.y), s23 = f2pack(v.z, v.w);
 #pragma unroll
-    for (int p = 0; p < 32; ++p) s[p & 3] += B.mom[warp][p][col];
-    const float S = (s[0] + s[1]) + (s[2] + s[3]);
+    for (int i = 1; i < 8; ++i) {
+        v = cv[i];
+        s01 = f2add(s01, f2pack(v.x, v.y));
+        s23 = f2add(s23, f2pack(v.z, v.w));
+    }
+    float s0, s1, s2, s3;
+    f2unpack(s01, s0, s1);
+    f2unpack(s23, s2, s3);
+    const float S = (s0 + s1) + (s2 + s3);
     // mean x needs M2 of the next lane, mean y M1 of the previous one
     const float next = __shfl_down_sync(FULL, S, 1), prev = __shfl_up_sync(FULL, S, 1);
     if (lane < 6 * nb) {
@@ -216,6 +244,8 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
     const size_t HW = (size_t)a.W * a.H, pix = (size_t)py * a.W + px;
     const uint2 rg = a.ranges[tile];
     const bool vec_ok = (a.C % FeatIO<FT>::VEC) == 0;
+    // feature gradients by 16-byte atomics: rows of a multiple of 4 channels on a 16-byte boundary
+    const bool vec4 = (a.C % 4) == 0 && (reinterpret_cast<uintptr_t>(a.d_feat) & 15u) == 0;
 
     float g[CP];
     float T = 1.0f, Tfin = 1.0f, gA = 0.0f;
@@ -318,19 +348,19 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
                     BG.wtl[warp][gs][lane] = __float2bfloat16_rn(wgt - __bfloat162float(wh));
                     if (lane == 0) BG.gid[warp][gs] = id;
                     if (++gs == 16) {
-                        flush_feat_grads<CP>(BG, warp, lane, 16, a.C, a.d_feat);
+                        flush_feat_grads<CP>(BG, warp, lane, 16, a.C, a.d_feat, vec4);
                         gs = 0;
                     }
                 }
                 // this pixel's moment terms (zero where it does not contribute)
-                float *mm = &BG.mom[warp][lane][6 * bs];
+                float *mm = &BG.mom[warp][6 * bs][lane];
                 const float m1 = dq * dx, m2 = dq * dy;
-                mm[0] = d_o;
-                mm[1] = m1;
-                mm[2] = m2;
-                mm[3] = m1 * dx;
-                mm[4] = m1 * dy;
-                mm[5] = m2 * dy;
+                mm[0 * MSTRIDE] = d_o;
+                mm[1 * MSTRIDE] = m1;
+                mm[2 * MSTRIDE] = m2;
+                mm[3 * MSTRIDE] = m1 * dx;
+                mm[4 * MSTRIDE] = m1 * dy;
+                mm[5 * MSTRIDE] = m2 * dy;
                 if (lane == 0)  // the conic (a, b, c) from the record, and the id
                     BG.mrec[warp][bs] = make_float4(-2.0f * h0.z, -h0.w, -2.0f * h1.x, __uint_as_float(id));
                 if (++bs == BwdGroup<CP>::MB) {
@@ -340,7 +370,7 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
             }
         }
     }
-    if (gs > 0) flush_feat_grads<CP>(BG, warp, lane, gs, a.C, a.d_feat);
+    if (gs > 0) flush_feat_grads<CP>(BG, warp, lane, gs, a.C, a.d_feat, vec4);
     if (bs > 0) flush_geo_grads<CP>(BG, warp, lane, bs, a);
     }
 }

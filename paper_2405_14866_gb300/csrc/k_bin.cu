@@ -344,6 +344,51 @@ __device__ __forceinline__ void smem_pass_any(BinSortSmem &S, int src, int m, bo
     else smem_pass<BS_ROUNDS>(S, src, m, by_id, vmin, shift);
 }
 
+constexpr int LD_BATCH = 8;  // global loads per thread issued together in the streaming loops
+
+// (k - kmin, v) of entries [0, m), m <= BS_MAX, into dst: all loads of a
+// thread issued before its first store, so that they are in flight together.
+__device__ __forceinline__ void load_chunk(uint2 *dst, const uint32_t *k, const uint32_t *v, uint32_t m, uint32_t kmin) {
+    const uint32_t tid = threadIdx.x;
+    uint32_t kr[BS_ROUNDS], vr[BS_ROUNDS];
+#pragma unroll
+    for (int r = 0; r < BS_ROUNDS; ++r) {
+        const uint32_t j = tid + r * BS_THREADS;
+        kr[r] = j < m ? k[j] : 0u;
+        vr[r] = j < m ? v[j] : 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < BS_ROUNDS; ++r) {
+        const uint32_t j = tid + r * BS_THREADS;
+        if (j < m) dst[j] = make_uint2(kr[r] - kmin, vr[r]);
+    }
+}
+
+// This thread's share of the minimum and maximum of k[0, n) (and of v[0, n)
+// when v is given), LD_BATCH loads in flight per step.
+__device__ __forceinline__ void range_minmax(const uint32_t *k, const uint32_t *v, uint32_t n, uint32_t &kmn,
+                                             uint32_t &kmx, uint32_t &vmn, uint32_t &vmx) {
+    kmn = FULL; kmx = 0u; vmn = FULL; vmx = 0u;
+    for (uint32_t j0 = 0; j0 < n; j0 += LD_BATCH * BS_THREADS) {
+        uint32_t kr[LD_BATCH], vr[LD_BATCH];
+#pragma unroll
+        for (int r = 0; r < LD_BATCH; ++r) {
+            const uint32_t j = j0 + threadIdx.x + r * BS_THREADS;
+            kr[r] = j < n ? k[j] : FULL;
+            vr[r] = (v && j < n) ? v[j] : FULL;
+        }
+#pragma unroll
+        for (int r = 0; r < LD_BATCH; ++r) {
+            const bool ok = j0 + threadIdx.x + r * BS_THREADS < n;
+            if (ok) {
+                kmn = min(kmn, kr[r]); kmx = max(kmx, kr[r]);
+                vmn = min(vmn, vr[r]); vmx = max(vmx, vr[r]);
+            }
+        }
+    }
+    if (!v) { vmn = 0u; vmx = 0u; }
+}
+
 // One stable pass over a bucket in global memory, chunk by chunk:
 // (ka, va)[0, n) -> (kb, vb)[0, n); keys are remapped by kmin while in
 // shared memory.
@@ -352,8 +397,17 @@ __device__ void global_pass(BinSortSmem &S, const uint32_t *ka, const uint32_t *
     const int tid = threadIdx.x;
     S.dbase[tid] = 0u;
     __syncthreads();
-    for (uint32_t j = tid; j < n; j += BS_THREADS)
-        atomicAdd(&S.dbase[digit_of(make_uint2(ka[j] - kmin, va[j]), by_id, vmin, shift)], 1u);
+    for (uint32_t j0 = 0; j0 < n; j0 += LD_BATCH * BS_THREADS) {  // LD_BATCH loads per thread in flight
+        uint32_t d[LD_BATCH];
+#pragma unroll
+        for (int r = 0; r < LD_BATCH; ++r) {
+            const uint32_t j = j0 + tid + r * BS_THREADS;
+            d[r] = j < n ? digit_of(make_uint2(ka[j] - kmin, by_id ? va[j] : 0u), by_id, vmin, shift) : 256u;
+        }
+#pragma unroll
+        for (int r = 0; r < LD_BATCH; ++r)
+            if (d[r] < 256u) atomicAdd(&S.dbase[d[r]], 1u);
+    }
     __syncthreads();
     {
         uint32_t tot;
@@ -364,7 +418,7 @@ __device__ void global_pass(BinSortSmem &S, const uint32_t *ka, const uint32_t *
     const int warp = tid >> 5, lane = tid & 31;
     for (uint32_t c0 = 0; c0 < n; c0 += BS_MAX) {
         const int m = (int)min((uint32_t)BS_MAX, n - c0);
-        for (int j = tid; j < m; j += BS_THREADS) S.kv[0][j] = make_uint2(ka[c0 + j] - kmin, va[c0 + j]);
+        load_chunk(S.kv[0], ka + c0, va + c0, (uint32_t)m, kmin);
         __syncthreads();
         uint32_t dig[BS_ROUNDS], rank[BS_ROUNDS], count;
         rank_chunk<BS_ROUNDS>(S, S.kv[0], m, by_id, vmin, shift, dig, rank, count);
@@ -469,19 +523,28 @@ __device__ void sort_range_smem(BinSortSmem &S, const uint32_t *k, const uint32_
         __syncthreads();
         return;
     }
-    uint32_t kmn = FULL, kmx = 0u, vmn = FULL, vmx = 0u;
-    for (uint32_t j = tid; j < n; j += BS_THREADS) {
-        const uint32_t kj = k[j], vj = v[j];
-        S.kv[1][j] = make_uint2(kj, vj);  // staged; remapped into kv[0] below
-        kmn = min(kmn, kj); kmx = max(kmx, kj); vmn = min(vmn, vj); vmx = max(vmx, vj);
+    // the whole bucket in registers first (BS_ROUNDS loads per thread in flight together)
+    uint32_t kr[BS_ROUNDS], vr[BS_ROUNDS];
+#pragma unroll
+    for (int r = 0; r < BS_ROUNDS; ++r) {
+        const uint32_t j = tid + r * BS_THREADS;
+        kr[r] = j < n ? k[j] : 0u;
+        vr[r] = j < n ? v[j] : 0u;
     }
+    uint32_t kmn = FULL, kmx = 0u, vmn = FULL, vmx = 0u;
+#pragma unroll
+    for (int r = 0; r < BS_ROUNDS; ++r)
+        if (tid + r * BS_THREADS < n) {
+            kmn = min(kmn, kr[r]); kmx = max(kmx, kr[r]); vmn = min(vmn, vr[r]); vmx = max(vmx, vr[r]);
+        }
     block_minmax(S, kmn, kmx, vmn, vmx);
     const uint32_t kmin = S.red[0], vmin = S.red[2];
     const int kb = sig_bits(kmin, S.red[1]), vb = sig_bits(vmin, S.red[3]);
     const int m = (int)n;
-    for (int j = tid; j < m; j += BS_THREADS) {
-        const uint2 e = S.kv[1][j];
-        S.kv[0][j] = make_uint2(e.x - kmin, e.y);
+#pragma unroll
+    for (int r = 0; r < BS_ROUNDS; ++r) {
+        const uint32_t j = tid + r * BS_THREADS;
+        if (j < n) S.kv[0][j] = make_uint2(kr[r] - kmin, vr[r]);
     }
     __syncthreads();
     int src = 0;
@@ -509,11 +572,8 @@ __device__ void sort_range_smem(BinSortSmem &S, const uint32_t *k, const uint32_
 __device__ void sort_range_global(BinSortSmem &S, uint32_t *k0, uint32_t *v0, uint32_t *k1, uint32_t *v1, uint32_t n,
                                   uint32_t *out) {
     const int tid = threadIdx.x;
-    uint32_t kmn = FULL, kmx = 0u, vmn = FULL, vmx = 0u;
-    for (uint32_t j = tid; j < n; j += BS_THREADS) {
-        const uint32_t kj = k0[j], vj = v0[j];
-        kmn = min(kmn, kj); kmx = max(kmx, kj); vmn = min(vmn, vj); vmx = max(vmx, vj);
-    }
+    uint32_t kmn, kmx, vmn, vmx;
+    range_minmax(k0, v0, n, kmn, kmx, vmn, vmx);
     block_minmax(S, kmn, kmx, vmn, vmx);
     const uint32_t kmin = S.red[0], vmin = S.red[2];
     const int kb = sig_bits(kmin, S.red[1]), vb = sig_bits(vmin, S.red[3]);
@@ -534,7 +594,21 @@ __device__ void sort_range_global(BinSortSmem &S, uint32_t *k0, uint32_t *v0, ui
             t = v0; v0 = v1; v1 = t;
         }
     }
-    for (uint32_t j = tid; j < n; j += BS_THREADS) out[j] = v0[j];  // the result is in (k0, v0)
+    if (out != v0) {  // the result is in (k0, v0)
+        for (uint32_t j0 = 0; j0 < n; j0 += LD_BATCH * BS_THREADS) {
+            uint32_t vr[LD_BATCH];
+#pragma unroll
+            for (int r = 0; r < LD_BATCH; ++r) {
+                const uint32_t j = j0 + tid + r * BS_THREADS;
+                vr[r] = j < n ? v0[j] : 0u;
+            }
+#pragma unroll
+            for (int r = 0; r < LD_BATCH; ++r) {
+                const uint32_t j = j0 + tid + r * BS_THREADS;
+                if (j < n) out[j] = vr[r];
+            }
+        }
+    }
     __syncthreads();
 }
 
@@ -563,12 +637,9 @@ __global__ __launch_bounds__(BS_THREADS, 3) void k_bin_sort(BinArgs a) {
         // highest significant digit splits it into depth slabs; runs of
         // consecutive slabs of at most BS_MAX entries are then sorted in
         // shared memory, and a slab larger than that by global passes.
-        uint32_t kmn = FULL, kmx = 0u;
-        for (uint32_t j = tid; j < n; j += BS_THREADS) {
-            const uint32_t kj = bk[j];
-            kmn = min(kmn, kj); kmx = max(kmx, kj);
-        }
-        block_minmax(S, kmn, kmx, 0u, 0u);
+        uint32_t kmn, kmx, vmn, vmx;
+        range_minmax(bk, nullptr, n, kmn, kmx, vmn, vmx);
+        block_minmax(S, kmn, kmx, vmn, vmx);
         const uint32_t kmin = S.red[0];
         const int kb = sig_bits(kmin, S.red[1]);
         if (kb == 0) {  // one depth key: the id order, by global passes
