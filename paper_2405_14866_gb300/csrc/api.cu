@@ -120,6 +120,7 @@ struct tsplat_ctx {
     int W = 0, H = 0, C = 0, dtype = TSPLAT_F32, tiles_x = 0, tiles_y = 0;
     int n_slots = 0;  // tile slots of the last render (all its views)
     const void *feat = nullptr;
+    const void *feat_split = nullptr;  // FP32 features: their split rows
     const uint32_t *pairs = nullptr;  // sorted Gaussian ids
     bool saved = false;
     bool has_cam = false;        // the last render had a camera (tsplat_render)
@@ -544,6 +545,7 @@ static tsplat_status render_tail(tsplat_ctx *c, int64_t n_cap, const uint32_t *n
     c->tiles_x = tiles_x; c->tiles_y = tiles_y;
     c->n_slots = n_tiles;
     c->feat = feat;
+    c->feat_split = fsplit;
     c->pairs = ids_sorted;
     c->saved = save;
     c->alpha_max = par.alpha_max;
@@ -792,6 +794,8 @@ tsplat_status tsplat_backward(tsplat_ctx *c, const float *dL_dfeat, const float 
                               float *d_conic, float *d_opac, float *d_feat, void *stream) {
     if (!c || !dL_dfeat) return fail(TSPLAT_ERR_INVALID_ARG, "backward: NULL argument");
     if (!c->saved) return fail(TSPLAT_ERR_INVALID_ARG, "backward: the last render on this context did not use TSPLAT_RENDER_SAVE");
+    if (c->dtype == TSPLAT_F32 && !c->feat_split)
+        return fail(TSPLAT_ERR_INVALID_ARG, "backward: the last render's FP32 features have no split rows");
     cudaStream_t s = S(stream);
     launch_zero_f32_n(d_mean2d, c->n_dev, 2, c->n_cap, s);
     launch_zero_f32_n(d_conic, c->n_dev, 3, c->n_cap, s);
@@ -803,6 +807,7 @@ tsplat_status tsplat_backward(tsplat_ctx *c, const float *dL_dfeat, const float 
     b.ids = c->pairs;
     b.hdr = c->hdr.as<Header>();
     b.feat = c->feat;
+    b.fsplit = c->feat_split;
     b.C = c->C;
     b.feat_dtype = c->dtype;
     b.W = c->W; b.H = c->H; b.tiles_x = c->tiles_x; b.tiles_y = c->tiles_y;

@@ -238,6 +238,7 @@ struct BackwardArgs {
     float *d_feat;
     uint32_t *unit_counter;  // next (tile, warp block) unit to hand out (0 at launch)
     const uint32_t *tile_order;  // the forward's tile order (longest lists first), or NULL
+    const void *fsplit;          // FP32 features: their (hi, lo) bf16 rows, as the forward read them
 };
 void launch_backward(const BackwardArgs &a, cudaStream_t s);
 

@@ -6,6 +6,7 @@
 // one, and repeats the forward's blend decisions with the forward's
 // arithmetic, so the contributor set is the forward's.
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "internal.h"
@@ -19,56 +20,6 @@ constexpr uint32_t FULL = 0xffffffffu;
 constexpr float LOG2E = 1.4426950408889634f;
 
 constexpr int CT = 256;
-
-template <typename FT>
-struct FeatIO;
-
-template <>
-struct FeatIO<float> {
-    static constexpr int VEC = 4;
-    template <int CP>
-    __device__ static __forceinline__ void load(float (&f)[CP], const float *row) {
-        const float4 *r4 = reinterpret_cast<const float4 *>(row);
-#pragma unroll
-        for (int i = 0; i < CP / 4; ++i) {
-            const float4 v = r4[i];
-            f[4 * i] = v.x; f[4 * i + 1] = v.y; f[4 * i + 2] = v.z; f[4 * i + 3] = v.w;
-        }
-    }
-};
-
-template <>
-struct FeatIO<__nv_bfloat16> {
-    static constexpr int VEC = 8;
-    template <int CP>
-    __device__ static __forceinline__ void load(float (&f)[CP], const __nv_bfloat16 *row) {
-        const uint4 *r4 = reinterpret_cast<const uint4 *>(row);
-#pragma unroll
-        for (int i = 0; i < CP / 8; ++i) {
-            const uint4 v = r4[i];
-            f[8 * i + 0] = bf16_lo_f(v.x); f[8 * i + 1] = bf16_hi_f(v.x);
-            f[8 * i + 2] = bf16_lo_f(v.y); f[8 * i + 3] = bf16_hi_f(v.y);
-            f[8 * i + 4] = bf16_lo_f(v.z); f[8 * i + 5] = bf16_hi_f(v.z);
-            f[8 * i + 6] = bf16_lo_f(v.w); f[8 * i + 7] = bf16_hi_f(v.w);
-        }
-    }
-};
-
-template <int CP, typename FT>
-__device__ __forceinline__ void stage(const Header *__restrict__ hdr, const FT *__restrict__ feat, int C,
-                                      bool vec_ok, uint32_t id, Header *s_hdr, FT *s_feat, int slot) {
-    s_hdr[slot] = hdr[id];
-    FT *dst = s_feat + (size_t)slot * CP;
-    const FT *src = feat + (size_t)id * C;
-    if (vec_ok) {
-        constexpr int V = FeatIO<FT>::VEC;
-        const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
-        uint4 *d4 = reinterpret_cast<uint4 *>(dst);
-        for (int i = 0; i < C / V; ++i) d4[i] = __ldg(s4 + i);
-    } else {
-        for (int c = 0; c < C; ++c) dst[c] = src[c];
-    }
-}
 
 // Per-warp shared state of the gradient reductions.
 //
@@ -90,6 +41,7 @@ __device__ __forceinline__ void stage(const Header *__restrict__ hdr, const FT *
 // one per lane, with 16-byte loads (column stride 36 words: the eight lanes
 // of a load phase fall into distinct bank groups), instead of a chain of
 // shuffles per Gaussian.
+constexpr int NB = 8;      // survivors per batch of the reverse walk (the n of one MMA)
 constexpr int WTROW = 40;  // bf16 per W^T row (32 used; 80-byte stride spreads ldmatrix rows over the banks)
 constexpr int MSTRIDE = 36;  // floats per moment column (32 used)
 template <int CP>
@@ -103,6 +55,7 @@ struct BwdGroup {
     uint32_t gid[CT / 32][16];
     float mom[CT / 32][6 * MB][MSTRIDE];  // per moment term of the pending batch: its 32 pixels
     float4 mrec[CT / 32][MB];              // the batch's Gaussians: conic (a, b, c) and id (bits)
+    float fg[CT / 32][32][NB];             // <f_j, g_p> of a survivor batch: pixel rows
 };
 
 template <int CP>
@@ -212,21 +165,43 @@ __device__ __forceinline__ void flush_geo_grads(BwdGroup<CP> &B, int warp, int l
 // saved final transmittance.  The blend decisions repeat the forward's
 // arithmetic exactly (same instructions), so the contributor set is the
 // forward's.
+//
+// The box survivors of a staged chunk are taken in batches of NB, back to
+// front.  Per batch: <f_j, g_p> for the warp's 32 pixels and the NB
+// Gaussians as one tensor-core product G (32 x GP) F^T (GP x NB) on bf16
+// hi + lo parts (feature rows staged as bf16 rows: BF16 features as stored,
+// FP32 features as the split (hi, lo) rows the forward reads); then each
+// lane's terms of the NB Gaussians, which are independent of one another;
+// then the two recurrences that are not (the transmittance T and the
+// suffix <S, g>), one multiply and one FMA per Gaussian.
+// 1 / x with the hardware approximation (rcp.approx, relative error ~2^-23)
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 template <int CP, typename FT>
 __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
+    constexpr bool F32 = std::is_same<FT, float>::value;
+    constexpr int GP = BwdGroup<CP>::GP;
+    constexpr int RW = (F32 ? 2 : 1) * GP;  // bf16 per staged feature row: hi (then lo)
     extern __shared__ __align__(16) unsigned char smem[];
     Header *s_hdr = reinterpret_cast<Header *>(smem);
-    FT *s_feat = reinterpret_cast<FT *>(smem + CT * sizeof(Header));
-    BwdGroup<CP> &BG = *reinterpret_cast<BwdGroup<CP> *>(smem + CT * sizeof(Header) + (size_t)CT * CP * sizeof(FT));
+    __nv_bfloat16 *s_row = reinterpret_cast<__nv_bfloat16 *>(smem + CT * sizeof(Header));
+    BwdGroup<CP> &BG = *reinterpret_cast<BwdGroup<CP> *>(smem + CT * sizeof(Header) + (size_t)CT * RW * 2);
     __shared__ uint32_t s_id[CT];
-    const FT *feat = reinterpret_cast<const FT *>(a.feat);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // each warp zeroes the channel padding of its own staging rows
-    if (a.C < CP)
-        for (int i = lane; i < 32 * CP; i += 32) s_feat[(size_t)warp * 32 * CP + i] = FT(0.0f);
+    // BF16 rows of fewer than GP channels: the padding columns stay zero
+    if (!F32 && a.C < GP)
+        for (int i = lane; i < 32 * RW; i += 32) s_row[(size_t)warp * 32 * RW + i] = __float2bfloat16_rn(0.0f);
     __syncwarp();
     const int n_units = a.tiles_x * a.tiles_y * 8;
+    const bool bvec = !F32 && a.C == GP;  // BF16 rows of exactly GP channels: 16-byte copies
+    // feature gradients by 16-byte atomics: rows of a multiple of 4 channels on a 16-byte boundary
+    const bool vec4 = (a.C % 4) == 0 && (reinterpret_cast<uintptr_t>(a.d_feat) & 15u) == 0;
+    const int arow = ((lane >> 3) & 1) * 8 + (lane & 7), acol = (lane >> 4) * 8;  // A fragment rows / columns
     // Persistent: every warp takes (tile, 8x4 block) units from a counter, so
     // the load balances at warp granularity whatever the tiles' list lengths.
     for (;;) {
@@ -243,35 +218,23 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
     const float fbx0 = (float)bx0, fbx1 = (float)(bx0 + 7), fby0 = (float)by0, fby1 = (float)(by0 + 3);
     const size_t HW = (size_t)a.W * a.H, pix = (size_t)py * a.W + px;
     const uint2 rg = a.ranges[tile];
-    const bool vec_ok = (a.C % FeatIO<FT>::VEC) == 0;
-    // feature gradients by 16-byte atomics: rows of a multiple of 4 channels on a 16-byte boundary
-    const bool vec4 = (a.C % 4) == 0 && (reinterpret_cast<uintptr_t>(a.d_feat) & 15u) == 0;
 
-    float g[CP];
     float T = 1.0f, Tfin = 1.0f, gA = 0.0f;
     uint32_t lastk = 0;
-#pragma unroll
-    for (int c = 0; c < CP; ++c) g[c] = 0.0f;
     if (inside) {
         Tfin = a.T_final[pix];
         T = Tfin;
         lastk = a.last[pix];
         gA = a.dA ? a.dA[pix] : 0.0f;
-#pragma unroll
-        for (int c = 0; c < CP; ++c)
-            if (c < a.C) g[c] = a.dF[c * HW + pix];
     }
-    // this pixel's row of G for the feature-gradient products (hi + lo)
+    // this pixel's row of G = dL/dF (hi + lo), the operand of both products
 #pragma unroll
-    for (int c = 0; c < BwdGroup<CP>::GP; ++c) {
-        const float v = c < CP ? g[c] : 0.0f;
+    for (int c = 0; c < GP; ++c) {
+        const float v = (inside && c < a.C) ? a.dF[c * HW + pix] : 0.0f;
         const __nv_bfloat16 h = __float2bfloat16_rn(v);
         BG.gh[warp][lane][c] = h;
         BG.gl[warp][lane][c] = __float2bfloat16_rn(v - __bfloat162float(h));
     }
-    unsigned long long g2[CP / 2];  // g in (even, odd) channel pairs, for the packed <f, g>
-#pragma unroll
-    for (int c = 0; c < CP / 2; ++c) g2[c] = f2pack(g[2 * c], g[2 * c + 1]);
     const unsigned long long fp2 = f2pack(fpx, fpy);
     int gs = 0;  // contributing Gaussians collected in this warp's current feature group
     int bs = 0;  // and in its current geometric batch
@@ -281,66 +244,122 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
     // 32, staged into its own slice of shared memory: no block-wide barrier,
     // so a warp whose pixels stopped early does not wait for the others.
     Header *w_hdr = s_hdr + warp * 32;
-    FT *w_feat = s_feat + (size_t)warp * 32 * CP;
+    __nv_bfloat16 *w_row = s_row + (size_t)warp * 32 * RW;
     uint32_t *w_id = s_id + warp * 32;
+    uint32_t nid = 0;  // ids of the next chunk, loaded one chunk ahead
     {
-        for (int c1 = (int)wmax; c1 > 0; c1 -= 32) {
-            const int c0 = max(0, c1 - 32);
-            __syncwarp();
-            if (c0 + lane < c1) {
-                const uint32_t gid = a.ids[rg.x + c0 + lane];
-                w_id[lane] = gid;
-                stage<CP, FT>(a.hdr, feat, a.C, vec_ok, gid, w_hdr, w_feat, lane);
+        const int c0 = max(0, (int)wmax - 32);
+        if (c0 + lane < (int)wmax) nid = a.ids[rg.x + c0 + lane];
+    }
+    for (int c1 = (int)wmax; c1 > 0; c1 -= 32) {
+        const int c0 = max(0, c1 - 32);
+        const uint32_t gid = nid;
+        if (c0 > 0) {
+            const int n0 = max(0, c0 - 32);
+            nid = n0 + lane < c0 ? a.ids[rg.x + n0 + lane] : 0u;
+        }
+        __syncwarp();
+        if (c0 + lane < c1) {
+            w_id[lane] = gid;
+            w_hdr[lane] = a.hdr[gid];
+            __nv_bfloat16 *dst = w_row + (size_t)lane * RW;
+            if (F32) {
+                const uint4 *src = reinterpret_cast<const uint4 *>(reinterpret_cast<const __nv_bfloat16 *>(a.fsplit) +
+                                                                   (size_t)gid * 2 * GP);
+#pragma unroll
+                for (int i = 0; i < 2 * GP / 8; ++i) reinterpret_cast<uint4 *>(dst)[i] = __ldg(src + i);
+            } else if (bvec) {
+                const uint4 *src = reinterpret_cast<const uint4 *>(reinterpret_cast<const __nv_bfloat16 *>(a.feat) +
+                                                                   (size_t)gid * GP);
+#pragma unroll
+                for (int i = 0; i < GP / 8; ++i) reinterpret_cast<uint4 *>(dst)[i] = __ldg(src + i);
+            } else {
+                const __nv_bfloat16 *src = reinterpret_cast<const __nv_bfloat16 *>(a.feat) + (size_t)gid * a.C;
+                for (int c = 0; c < a.C; ++c) dst[c] = src[c];
             }
-            __syncwarp();
-            bool rel = false;
-            if (c0 + lane < c1) {
-                const Header h = w_hdr[lane];
-                rel = (h.h0.x + h.h1.z >= fbx0) && (h.h0.x - h.h1.z <= fbx1) && (h.h0.y + h.h1.w >= fby0) &&
-                      (h.h0.y - h.h1.w <= fby1);
+        }
+        __syncwarp();
+        bool rel = false;
+        if (c0 + lane < c1) {
+            const Header h = w_hdr[lane];
+            rel = (h.h0.x + h.h1.z >= fbx0) && (h.h0.x - h.h1.z <= fbx1) && (h.h0.y + h.h1.w >= fby0) &&
+                  (h.h0.y - h.h1.w <= fby1);
+        }
+        uint32_t m = __ballot_sync(FULL, rel);
+        while (m) {
+            // the next batch: up to NB survivors, highest list position first
+            uint32_t mb = 0;
+#pragma unroll
+            for (int s = 0; s < NB; ++s)
+                if (m) {
+                    const uint32_t top = 1u << (31 - __clz(m));
+                    mb |= top;
+                    m &= ~top;
+                }
+            // <f_j, g_p> of the batch: D (32 px x NB) = G (32 x GP) F^T (GP x NB) on the
+            // tensor cores (hi/lo parts); lane l addresses the B row of survivor l % 8
+            {
+                uint32_t t = mb;
+                for (int i = 0; i < (lane & 7) && t; ++i) t &= ~(1u << (31 - __clz(t)));
+                const int jr = t ? 31 - __clz(t) : 0;
+                float d[2][4];
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) d[mt][e] = 0.0f;
+#pragma unroll
+                for (int ks = 0; ks < GP / 16; ++ks) {
+                    uint32_t bh0, bh1, bl0 = 0u, bl1 = 0u;
+                    const __nv_bfloat16 *rowp = w_row + (size_t)jr * RW + ks * 16 + ((lane >> 3) & 1) * 8;
+                    if (F32) ldsm_x4(bh0, bh1, bl0, bl1, rowp + (lane >> 4) * GP);  // hi k 0-7, 8-15; lo k 0-7, 8-15
+                    else ldsm_x2(bh0, bh1, rowp);
+#pragma unroll
+                    for (int mt = 0; mt < 2; ++mt) {
+                        uint32_t ah[4], al[4];
+                        ldsm_x4(ah[0], ah[1], ah[2], ah[3], &BG.gh[warp][mt * 16 + arow][ks * 16 + acol]);
+                        ldsm_x4(al[0], al[1], al[2], al[3], &BG.gl[warp][mt * 16 + arow][ks * 16 + acol]);
+                        mma_bf16(d[mt], ah[0], ah[1], ah[2], ah[3], bh0, bh1);
+                        mma_bf16(d[mt], al[0], al[1], al[2], al[3], bh0, bh1);
+                        if (F32) mma_bf16(d[mt], ah[0], ah[1], ah[2], ah[3], bl0, bl1);
+                    }
+                }
+                // D fragment: pixel rows 16 mt + lane/4 (+8), survivor columns 2(lane%4) (+1)
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                    for (int hh = 0; hh < 2; ++hh)
+                        *reinterpret_cast<float2 *>(&BG.fg[warp][mt * 16 + hh * 8 + (lane >> 2)][2 * (lane & 3)]) =
+                            make_float2(d[mt][2 * hh], d[mt][2 * hh + 1]);
+                __syncwarp();
             }
-            uint32_t m = __ballot_sync(FULL, rel);
-            while (m) {
-                const int j = 31 - __clz(m);  // highest first: back to front
-                m &= ~(1u << j);
+            for (int s = 0; mb; ++s) {
+                const int j = 31 - __clz(mb);  // highest first: back to front
+                mb &= ~(1u << j);
                 const uint32_t k = (uint32_t)(c0 + j);
                 const float4 h0 = w_hdr[j].h0;
                 const float4 h1 = w_hdr[j].h1;
                 float dx, dy;
-                f2unpack(f2sub(fp2, *reinterpret_cast<const unsigned long long *>(&w_hdr[j].h0.x)), dx, dy);
+                f2unpack(f2sub(fp2, f2pack(h0.x, h0.y)), dx, dy);
                 const float q = gauss_q(dx, dy, h0.z, h0.w, h1.x);
-                bool contrib = false;
-                float al = 0.0f, raw = 0.0f;
-                if (k < lastk) {  // the forward's tests, in the same order
-                    const float e2 = fmaf(q, LOG2E, h1.y);
-                    if (e2 >= a.log2_alpha_min) {
-                        raw = ex2(e2);
-                        al = fminf(a.alpha_max, raw);
-                        contrib = true;
-                    }
-                }
+                // the forward's tests, in the same order
+                const float e2 = fmaf(q, LOG2E, h1.y);
+                const bool contrib = k < lastk && e2 >= a.log2_alpha_min;
                 if (!__any_sync(FULL, contrib)) continue;
-                float f[CP];
-                FeatIO<FT>::template load<CP>(f, w_feat + (size_t)j * CP);
-                float wgt = 0.0f, d_o = 0.0f, dq = 0.0f;
-                if (contrib) {
-                    const float inv = __frcp_rn(1.0f - al);
-                    const float Tj = T * inv;
-                    unsigned long long fg2 = 0;  // even and odd channels' partial sums, packed
-#pragma unroll
-                    for (int c = 0; c < CP / 2; ++c) fg2 = f2fma(f2pack(f[2 * c], f[2 * c + 1]), g2[c], fg2);
-                    float fge, fgo;
-                    f2unpack(fg2, fge, fgo);
-                    const float fg = fge + fgo;
-                    wgt = al * Tj;
-                    const float dal = Tj * fg - sg * inv + gA * Tfin * inv;
-                    sg = fmaf(wgt, fg, sg);
-                    T = Tj;
-                    if (raw < a.alpha_max) {
-                        d_o = ex2(q * LOG2E) * dal;  // d alpha / d o = e^q
-                        dq = al * dal;
-                    }
-                }
+                const float raw = ex2(e2);
+                const float al = contrib ? fminf(a.alpha_max, raw) : 0.0f;
+                // a lane that does not blend this Gaussian has al = 0: inv = 1 and
+                // wgt = 0, so its T and sg stay as they are
+                const float inv = rcp_approx(1.0f - al);
+                const float fg = BG.fg[warp][lane][s];
+                const float Tj = T * inv;
+                const float wgt = al * Tj;
+                const float dal = Tj * fg - sg * inv + gA * Tfin * inv;
+                sg = fmaf(wgt, fg, sg);
+                T = Tj;
+                // a clamped alpha (= alpha_max) passes no gradient to o or q
+                const bool g_ok = contrib && raw < a.alpha_max;
+                const float d_o = g_ok ? ex2(q * LOG2E) * dal : 0.0f;  // d alpha / d o = e^q
+                const float dq = g_ok ? al * dal : 0.0f;
                 const uint32_t id = w_id[j];
                 if (a.d_feat) {  // collect w for the group's tensor-core product
                     const __nv_bfloat16 wh = __float2bfloat16_rn(wgt);
@@ -368,6 +387,7 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
                     bs = 0;
                 }
             }
+            __syncwarp();  // the batch's <f, g> tile is read before the next batch rewrites it
         }
     }
     if (gs > 0) flush_feat_grads<CP>(BG, warp, lane, gs, a.C, a.d_feat, vec4);
@@ -377,7 +397,8 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
 
 template <int CP, typename FT>
 void run_backward(const BackwardArgs &a, cudaStream_t s) {
-    const size_t smem = CT * sizeof(Header) + (size_t)CT * CP * sizeof(FT) + sizeof(BwdGroup<CP>);
+    const size_t smem = CT * sizeof(Header) + (size_t)CT * (std::is_same<FT, float>::value ? 2 : 1) * BwdGroup<CP>::GP * 2 +
+                        sizeof(BwdGroup<CP>);
     static PerDevice cache;
     const int grid = cache.get([smem](int) {
         cudaFuncSetAttribute(k_backward<CP, FT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
