@@ -209,10 +209,10 @@ tsplat_status tsplat_build_into(tsplat_gaussians *g, const tsplat_src_view *view
 /* tsplat_build_into without any device allocation (the paper has no
  * counterpart).  For callers that cannot call cudaMalloc at this point: a
  * frame loop with a fixed latency budget (device allocation and release
- * synchronize the device), work being recorded into a CUDA graph, or a
- * process whose device memory is fully owned by another allocator.  Same
- * inputs, outputs and results as tsplat_build_into; `g` is allocated by the
- * caller beforehand (tsplat_gaussians_create).
+ * synchronize the device), or a process whose device memory is fully owned
+ * by another allocator.  Same inputs, outputs and results as
+ * tsplat_build_into; `g` is allocated by the caller beforehand
+ * (tsplat_gaussians_create).
  * Limit: at most 64 Mi source pixels in total per call (e.g. 16 views of
  * 2048 x 2048); larger inputs return TSPLAT_ERR_CAPACITY before any work.
  * The per-block scratch of the compaction is one fixed 512 KiB device array

@@ -1,9 +1,8 @@
 // tsplat_build_into_noalloc: lifting (tsplat_build_into) without any device
 // allocation.  The paper has no counterpart; this exists for callers that
 // must not allocate device memory at call time -- a frame loop with a fixed
-// latency budget (cudaMalloc/cudaFree synchronize the device), code running
-// inside a CUDA-graph capture, or a host whose device memory is fully owned
-// by another allocator.  Its only scratch, the per-block foreground counts
+// latency budget (cudaMalloc/cudaFree synchronize the device), or a host
+// whose device memory is fully owned by another allocator.  Its only scratch, the per-block foreground counts
 // and offsets of the stream compaction, lives in a fixed device array below.
 #include <stdio.h>
 #include <string.h>

@@ -1,8 +1,8 @@
 """tsplat_build_into_noalloc against tsplat_build_into, through the C ABI.
 
 The allocation-free variant serves callers that may not allocate device
-memory while they run (a fixed-budget frame loop, CUDA-graph capture, a
-process whose device memory belongs to another allocator).  It must lift
+memory while they run (a fixed-budget frame loop, a process whose device
+memory belongs to another allocator).  It must lift
 exactly the same Gaussians as the regular call -- lifting is bit-exact, so
 the comparison is too -- on two calls in a row, and refuse inputs beyond its
 fixed scratch limit.  Collected last on purpose.
