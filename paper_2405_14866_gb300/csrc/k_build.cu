@@ -210,10 +210,25 @@ __device__ __forceinline__ void lift_one(const BuildArgs &a, const ViewDesc &vd,
 __device__ __forceinline__ void copy_rows(const BuildArgs &a, const ViewDesc &vd, const int64_t *s_src, int rows,
                                           int64_t first) {
     const int C = a.C;
+    if (vd.feat_dtype == TSPLAT_BF16 && a.out_dtype == TSPLAT_BF16 && (C & 7) == 0 &&
+        (reinterpret_cast<uintptr_t>(vd.feat) & 15u) == 0) {
+        // BF16 rows stored as they come: 16-byte chunks, no conversion
+        const int cpr = C >> 3;
+        const bool pow2 = (cpr & (cpr - 1)) == 0;
+        const int sh = __ffs(cpr) - 1;
+        for (int ch = threadIdx.x; ch < rows * cpr; ch += BT) {
+            const int row = pow2 ? ch >> sh : ch / cpr, part = ch - row * cpr;
+            const uint4 x = __ldg(reinterpret_cast<const uint4 *>((const __nv_bfloat16 *)vd.feat + s_src[row] * C) + part);
+            reinterpret_cast<uint4 *>((__nv_bfloat16 *)a.feat + (first + row) * C)[part] = x;
+        }
+        return;
+    }
     const bool vec = (C & 3) == 0;
     const int cpr = vec ? C / 4 : C;  // chunks per row
+    const bool pow2 = (cpr & (cpr - 1)) == 0;
+    const int sh = __ffs(cpr) - 1;
     for (int ch = threadIdx.x; ch < rows * cpr; ch += BT) {
-        const int row = ch / cpr, part = ch - row * cpr;
+        const int row = pow2 ? ch >> sh : ch / cpr, part = ch - row * cpr;
         const int64_t p = s_src[row], id = first + row;
         if (vec) {
             const int c0 = part * 4;
