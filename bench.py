@@ -561,23 +561,43 @@ def diff_bench(api, torch, steps=10, warmup=3):
 def e2e_run(api, torch, sc, g, ctx, cam, F, A, steps, world, compact):
     """End to end through the public API with host buffers: every step
     copies the source views from pinned host memory, lifts them, renders,
-    and copies F and A back.  Steps are pipelined over three streams with
+    and copies F and A back.  The host side keeps a step's maps in one
+    pinned arena and receives F and A into another, so each direction is one
+    copy per step.  Steps are pipelined over three streams with
     double-buffered device inputs and outputs: the copies of one step overlap
     the lifting and rendering of another.  compact: the maps carry only the
     foreground pixels' rows (TSPLAT_SRC_COMPACT), as a producer that knows
     the mask writes them."""
     up = api.upload_scene(sc, feat_dtype=sc.feat_dtype, compact=compact)
-    pin = [{k: t.cpu().pin_memory() for k, t in v.items() if k != "cam"} for v in up["views"]]
-    dev_sets = [[{k: torch.empty_like(t) for k, t in v.items() if k != "cam"} for v in up["views"]] for _ in range(2)]
-    view_sets = [[api.source_view(d["depth"], d["mask"], d["scale"], d["quat"], d["opacity"], d["feat"], v["cam"],
-                                  compact=compact)
-                  for d, v in zip(ds, up["views"])] for ds in dev_sets]
+    # the step's input arena: every map of every view at a 256-byte aligned offset
+    pieces, off = [], 0
+    for vi, v in enumerate(up["views"]):
+        for key, t in v.items():
+            if key == "cam":
+                continue
+            n = t.numel() * t.element_size()
+            pieces.append((vi, key, t.dtype, tuple(t.shape), off, n))
+            off += (n + 255) // 256 * 256
+    host_in = torch.empty(off, dtype=torch.uint8, pin_memory=True)
+    for vi, key, _, _, o, n in pieces:
+        host_in[o:o + n].copy_(up["views"][vi][key].contiguous().view(-1).view(torch.uint8).cpu())
+    dev_in = [torch.empty(off, dtype=torch.uint8, device="cuda") for _ in range(2)]
+
+    def views_of(buf):
+        maps = [dict() for _ in up["views"]]
+        for vi, key, dt, shape, o, n in pieces:
+            maps[vi][key] = buf[o:o + n].view(dt).view(shape)
+        return [api.source_view(m["depth"], m["mask"], m["scale"], m["quat"], m["opacity"], m["feat"], v["cam"],
+                                compact=compact) for m, v in zip(maps, up["views"])]
+    view_sets = [views_of(b) for b in dev_in]
     del up
-    outs = [(torch.empty_like(F), torch.empty_like(A)) for _ in range(2)]
-    Fh = [torch.empty(F.shape, dtype=F.dtype, pin_memory=True) for _ in range(2)]
-    Ah = [torch.empty(A.shape, dtype=A.dtype, pin_memory=True) for _ in range(2)]
-    h2d = sum(t.numel() * t.element_size() for v in pin for t in v.values())
-    d2h = F.numel() * 4 + A.numel() * 4
+    # F and A of a step contiguous on the device and in one pinned arena
+    nF, nA = F.numel(), A.numel()
+    dev_out = [torch.empty(nF + nA, device="cuda") for _ in range(2)]
+    outs = [(d[:nF].view(F.shape), d[nF:].view(A.shape)) for d in dev_out]
+    host_out = [torch.empty(nF + nA, pin_memory=True) for _ in range(2)]
+    h2d = sum(n for *_, n in pieces)
+    d2h = (nF + nA) * 4
     cs, ks, ds = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
     ev_in = [torch.cuda.Event() for _ in range(2)]
     ev_free = [torch.cuda.Event() for _ in range(2)]
@@ -590,9 +610,7 @@ def e2e_run(api, torch, sc, g, ctx, cam, F, A, steps, world, compact):
         b = k & 1
         with torch.cuda.stream(cs):
             cs.wait_event(ev_free[b])
-            for d, p in zip(dev_sets[b], pin):
-                for key, t in p.items():
-                    d[key].copy_(t, non_blocking=True)
+            dev_in[b].copy_(host_in, non_blocking=True)
             ev_in[b].record(cs)
         ks.wait_event(ev_in[b])
         g.build_into(view_sets[b], stream=ks)
@@ -602,8 +620,7 @@ def e2e_run(api, torch, sc, g, ctx, cam, F, A, steps, world, compact):
         ev_out[b].record(ks)
         with torch.cuda.stream(ds):
             ds.wait_event(ev_out[b])
-            Fh[b].copy_(outs[b][0], non_blocking=True)
-            Ah[b].copy_(outs[b][1], non_blocking=True)
+            host_out[b].copy_(dev_out[b], non_blocking=True)
             ev_read[b].record(ds)
 
     for k in range(2):
@@ -634,7 +651,8 @@ def e2e_run(api, torch, sc, g, ctx, cam, F, A, steps, world, compact):
     maps = "foreground rows only (TSPLAT_SRC_COMPACT) + full masks" if compact else "full H x W maps"
     return {"value": world * 1e3 / e2e_ms, "unit": "views/s", "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms,
-            "pipeline": "host-to-device, compute and device-to-host streams; double-buffered inputs and outputs",
+            "pipeline": "host-to-device, compute and device-to-host streams; double-buffered inputs and outputs; "
+                        "one pinned arena per direction (one copy each way per step)",
             "inputs": f"{len(sc.views)} source views, {maps}: depth, scale, quaternion, opacity f32, mask u8, "
                       f"features {'BF16' if sc.feat_dtype == api.BF16 else 'FP32'}",
             "h2d_gbs_one_buffer": 4 * big.numel() / (c0.elapsed_time(c1) * 1e-3) / 1e9}

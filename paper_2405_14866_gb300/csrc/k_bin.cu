@@ -464,13 +464,7 @@ __device__ __forceinline__ void block_minmax(BinSortSmem &S, uint32_t kmn, uint3
     __syncthreads();
 }
 
-// Entries in shared memory ((key, id) pairs) or in global memory (two arrays).
-struct SmemEntries {
-    uint2 *kv;
-    __device__ uint32_t key(uint32_t j) const { return kv[j].x; }
-    __device__ uint32_t id(uint32_t j) const { return kv[j].y; }
-    __device__ void set_id(uint32_t j, uint32_t v) const { kv[j].y = v; }
-};
+// Entries in global memory (two arrays).
 struct GlobalEntries {
     const uint32_t *k;
     uint32_t *v;
@@ -514,8 +508,45 @@ __device__ bool fix_ties(BinSortSmem &S, const E &e, uint32_t n) {
     return longrun;
 }
 
+// Puts each run of entries with equal key >> lo (entries [0, n) in shared
+// memory, sorted by key >> lo) in (key, id) order, in place, when the run
+// holds at most BS_RUN_MAX entries (one thread per run, insertion); returns
+// true (block-uniform) when a longer run exists, leaving it as it was.
+__device__ bool fix_runs(BinSortSmem &S, uint2 *kv, uint32_t n, int lo) {
+    const int tid = threadIdx.x;
+    if (tid == 0) S.flag = 0u;
+    __syncthreads();
+    for (uint32_t j = tid; j + 1 < n; j += BS_THREADS) {
+        const uint32_t hj = kv[j].x >> lo;
+        if ((j == 0 || (kv[j - 1].x >> lo) != hj) && (kv[j + 1].x >> lo) == hj) {
+            uint32_t end = j + 1;
+            while (end < n && (kv[end].x >> lo) == hj && end - j <= (uint32_t)BS_RUN_MAX) ++end;
+            if (end - j > (uint32_t)BS_RUN_MAX) {
+                atomicOr(&S.flag, 1u);
+            } else {
+                for (uint32_t x = j + 1; x < end; ++x) {
+                    const uint2 vx = kv[x];
+                    uint32_t y = x;
+                    while (y > j && (kv[y - 1].x > vx.x || (kv[y - 1].x == vx.x && kv[y - 1].y > vx.y))) {
+                        kv[y] = kv[y - 1];
+                        --y;
+                    }
+                    kv[y] = vx;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const bool longrun = S.flag != 0u;
+    __syncthreads();
+    return longrun;
+}
+
 // Sorts n <= BS_MAX entries (keys k, ids v in global memory) by (key, id)
-// in shared memory and writes the ids to out (which may alias v).
+// in shared memory and writes the ids to out (which may alias v).  The radix
+// passes cover the highest 8 * npass significant key bits (npass = 2 up to
+// 24 significant bits, else 3); runs of entries that agree on those bits are
+// then put in (key, id) order by insertion, which completes the order.
 __device__ void sort_range_smem(BinSortSmem &S, const uint32_t *k, const uint32_t *v, uint32_t n, uint32_t *out) {
     const int tid = threadIdx.x;
     if (n <= 1) {
@@ -548,12 +579,14 @@ __device__ void sort_range_smem(BinSortSmem &S, const uint32_t *k, const uint32_
     }
     __syncthreads();
     int src = 0;
-    for (int sh = 0; sh < kb; sh += 8) {
+    const int npass = kb <= 16 ? (kb + 7) / 8 : (kb <= 24 ? 2 : 3);
+    const int lo = max(0, kb - 8 * npass);  // key bits below the passes
+    for (int sh = lo; sh < kb; sh += 8) {
         smem_pass_any(S, src, m, false, vmin, sh);
         src ^= 1;
     }
-    // runs of equal depth keys: ids in order (short runs in place)
-    if (fix_ties(S, SmemEntries{S.kv[src]}, n)) {  // a long run: the full (depth key, id) order
+    // runs that agree on the passes' bits: (key, id) order (short runs in place)
+    if (fix_runs(S, S.kv[src], n, lo)) {  // a long run: the full (depth key, id) order
         for (int sh = 0; sh < vb; sh += 8) {
             smem_pass_any(S, src, m, true, vmin, sh);
             src ^= 1;
