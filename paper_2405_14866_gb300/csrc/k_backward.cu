@@ -174,6 +174,15 @@ __device__ __forceinline__ void flush_geo_grads(BwdGroup<CP> &B, int warp, int l
 // lane's terms of the NB Gaussians, which are independent of one another;
 // then the two recurrences that are not (the transmittance T and the
 // suffix <S, g>), one multiply and one FMA per Gaussian.
+// Staged feature rows keep their 16-byte chunks XOR-permuted by the row, so
+// that the eight rows one ldmatrix phase reads (a batch's survivors, mostly
+// consecutive entries) fall into distinct bank groups whatever the row
+// length: chunk c of row r sits at chunk c ^ row_swz<NCH>(r).
+template <int NCH>
+__device__ __forceinline__ int row_swz(int r) {
+    return NCH >= 8 ? (r & 7) : ((r / (8 / NCH)) & (NCH - 1));
+}
+
 // 1 / x with the hardware approximation (rcp.approx, relative error ~2^-23)
 __device__ __forceinline__ float rcp_approx(float x) {
     float y;
@@ -186,6 +195,7 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
     constexpr bool F32 = std::is_same<FT, float>::value;
     constexpr int GP = BwdGroup<CP>::GP;
     constexpr int RW = (F32 ? 2 : 1) * GP;  // bf16 per staged feature row: hi (then lo)
+    constexpr int NCH = RW / 8;             // its 16-byte chunks
     extern __shared__ __align__(16) unsigned char smem[];
     Header *s_hdr = reinterpret_cast<Header *>(smem);
     __nv_bfloat16 *s_row = reinterpret_cast<__nv_bfloat16 *>(smem + CT * sizeof(Header));
@@ -267,15 +277,15 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
                 const uint4 *src = reinterpret_cast<const uint4 *>(reinterpret_cast<const __nv_bfloat16 *>(a.fsplit) +
                                                                    (size_t)gid * 2 * GP);
 #pragma unroll
-                for (int i = 0; i < 2 * GP / 8; ++i) reinterpret_cast<uint4 *>(dst)[i] = __ldg(src + i);
+                for (int i = 0; i < 2 * GP / 8; ++i) reinterpret_cast<uint4 *>(dst)[i ^ row_swz<NCH>(lane)] = __ldg(src + i);
             } else if (bvec) {
                 const uint4 *src = reinterpret_cast<const uint4 *>(reinterpret_cast<const __nv_bfloat16 *>(a.feat) +
                                                                    (size_t)gid * GP);
 #pragma unroll
-                for (int i = 0; i < GP / 8; ++i) reinterpret_cast<uint4 *>(dst)[i] = __ldg(src + i);
+                for (int i = 0; i < GP / 8; ++i) reinterpret_cast<uint4 *>(dst)[i ^ row_swz<NCH>(lane)] = __ldg(src + i);
             } else {
                 const __nv_bfloat16 *src = reinterpret_cast<const __nv_bfloat16 *>(a.feat) + (size_t)gid * a.C;
-                for (int c = 0; c < a.C; ++c) dst[c] = src[c];
+                for (int c = 0; c < a.C; ++c) dst[8 * ((c >> 3) ^ row_swz<NCH>(lane)) + (c & 7)] = src[c];
             }
         }
         __syncwarp();
@@ -310,8 +320,10 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
 #pragma unroll
                 for (int ks = 0; ks < GP / 16; ++ks) {
                     uint32_t bh0, bh1, bl0 = 0u, bl1 = 0u;
-                    const __nv_bfloat16 *rowp = w_row + (size_t)jr * RW + ks * 16 + ((lane >> 3) & 1) * 8;
-                    if (F32) ldsm_x4(bh0, bh1, bl0, bl1, rowp + (lane >> 4) * GP);  // hi k 0-7, 8-15; lo k 0-7, 8-15
+                    // chunk of this lane's row: hi k 0-7, 8-15 (lanes 0-15), lo k 0-7, 8-15 (lanes 16-31)
+                    const int ch = 2 * ks + ((lane >> 3) & 1) + (F32 ? (lane >> 4) * (GP / 8) : 0);
+                    const __nv_bfloat16 *rowp = w_row + (size_t)jr * RW + 8 * (ch ^ row_swz<NCH>(jr));
+                    if (F32) ldsm_x4(bh0, bh1, bl0, bl1, rowp);
                     else ldsm_x2(bh0, bh1, rowp);
 #pragma unroll
                     for (int mt = 0; mt < 2; ++mt) {

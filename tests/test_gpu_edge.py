@@ -125,6 +125,35 @@ def test_limits_are_rejected():
     assert e.value.status == 1
 
 
+def test_runs_below_the_sorted_bits():
+    """The shared-memory sort passes over the highest 16 significant bits of
+    a tile's depth keys (here about 22), then orders each run of keys that
+    agree on them by (key, id): clusters of 2 to 200 Gaussians whose depths
+    lie within 100 ulps of each other (duplicates included) make runs both
+    short enough for the in-place insertion and longer than 32 (the fallback
+    to full passes).  Pairs and ranges bit-exact."""
+    rng = np.random.default_rng(91)
+    sizes = np.resize([2, 5, 20, 32, 33, 60, 200], 60)
+    base = rng.uniform(1.0, 1.5, sizes.size).astype(np.float32).view(np.uint32)
+    zb = np.concatenate([base[k] + rng.integers(0, 100, m).astype(np.uint32) for k, m in enumerate(sizes)])
+    z = zb.view(np.float32)
+    n = z.size
+    perm = rng.permutation(n)                # cluster members spread over the id range
+    z = z[perm]
+    xy = rng.uniform(-0.05, 0.05, size=(n, 2)) * z[:, None]
+    mean = np.concatenate([xy, z[:, None]], 1).astype(np.float32)
+    cov = np.zeros((n, 6), np.float32)
+    cov[:, 0] = cov[:, 3] = cov[:, 5] = (0.003 * z) ** 2
+    opac = rng.uniform(0.02, 0.3, n).astype(np.float32)
+    feat = rng.standard_normal((n, 2)).astype(np.float32)
+    cam = gen.make_camera(300.0, 64, 48, (0, 0, 0), np.eye(3), cx=32.0, cy=24.0)
+    bins = _check_bins_and_maps(O.Gaussians(mean, cov, opac, feat), cam)
+    counts = bins.ranges[:, 1].astype(np.int64) - bins.ranges[:, 0]
+    assert 1000 < counts.max() <= 3840     # the shared-memory path
+    keys = bins.keys.astype(np.int64)
+    assert (keys[1:] == keys[:-1]).sum() > 100   # duplicate keys: ties broken by id
+
+
 @pytest.mark.parametrize("mix", ["spread", "one_slab_heavy", "all_equal"])
 def test_buckets_beyond_shared_memory(mix):
     """15 K Gaussians on a few tiles: buckets larger than the shared-memory
