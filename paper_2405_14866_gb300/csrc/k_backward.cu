@@ -44,6 +44,7 @@ constexpr int CT = 256;
 constexpr int NB = 8;      // survivors per batch of the reverse walk (the n of one MMA)
 constexpr int WTROW = 40;  // bf16 per W^T row (32 used; 80-byte stride spreads ldmatrix rows over the banks)
 constexpr int MSTRIDE = 36;  // floats per moment column (32 used)
+constexpr int FGSTRIDE = 36; // floats per <f, g> row (32 used; the stride keeps the D fragment stores free of bank conflicts)
 template <int CP>
 struct BwdGroup {
     static constexpr int GP = CP < 16 ? 16 : CP;  // channels padded to whole k16 / n16 blocks
@@ -55,7 +56,7 @@ struct BwdGroup {
     uint32_t gid[CT / 32][16];
     float mom[CT / 32][6 * MB][MSTRIDE];  // per moment term of the pending batch: its 32 pixels
     float4 mrec[CT / 32][MB];              // the batch's Gaussians: conic (a, b, c) and id (bits)
-    float fg[CT / 32][32][NB];             // <f_j, g_p> of a survivor batch: pixel rows
+    float fg[CT / 32][NB][FGSTRIDE];       // <f_j, g_p> of a survivor batch: a row of 32 pixels per survivor
 };
 
 template <int CP>
@@ -335,13 +336,15 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
                         if (F32) mma_bf16(d[mt], ah[0], ah[1], ah[2], ah[3], bl0, bl1);
                     }
                 }
-                // D fragment: pixel rows 16 mt + lane/4 (+8), survivor columns 2(lane%4) (+1)
+                // D fragment: pixel rows 16 mt + lane/4 (+8), survivor columns 2(lane%4) (+1),
+                // stored survivor-major so that each survivor's step reads its row by lane
 #pragma unroll
                 for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
                     for (int hh = 0; hh < 2; ++hh)
-                        *reinterpret_cast<float2 *>(&BG.fg[warp][mt * 16 + hh * 8 + (lane >> 2)][2 * (lane & 3)]) =
-                            make_float2(d[mt][2 * hh], d[mt][2 * hh + 1]);
+#pragma unroll
+                        for (int e = 0; e < 2; ++e)
+                            BG.fg[warp][2 * (lane & 3) + e][mt * 16 + hh * 8 + (lane >> 2)] = d[mt][2 * hh + e];
                 __syncwarp();
             }
             for (int s = 0; mb; ++s) {
@@ -362,7 +365,7 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
                 // a lane that does not blend this Gaussian has al = 0: inv = 1 and
                 // wgt = 0, so its T and sg stay as they are
                 const float inv = rcp_approx(1.0f - al);
-                const float fg = BG.fg[warp][lane][s];
+                const float fg = BG.fg[warp][s][lane];
                 const float Tj = T * inv;
                 const float wgt = al * Tj;
                 const float dal = Tj * fg - sg * inv + gA * Tfin * inv;
