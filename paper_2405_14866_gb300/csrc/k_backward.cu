@@ -198,7 +198,9 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
     constexpr int RW = (F32 ? 2 : 1) * GP;  // bf16 per staged feature row: hi (then lo)
     constexpr int NCH = RW / 8;             // its 16-byte chunks
     extern __shared__ __align__(16) unsigned char smem[];
-    Header *s_hdr = reinterpret_cast<Header *>(smem);
+    // records staged as two arrays of 16-byte halves (h0, h1): a warp's
+    // per-lane reads and writes of one half then cover consecutive words
+    float4 *s_h0 = reinterpret_cast<float4 *>(smem), *s_h1 = s_h0 + CT;
     __nv_bfloat16 *s_row = reinterpret_cast<__nv_bfloat16 *>(smem + CT * sizeof(Header));
     BwdGroup<CP> &BG = *reinterpret_cast<BwdGroup<CP> *>(smem + CT * sizeof(Header) + (size_t)CT * RW * 2);
     __shared__ uint32_t s_id[CT];
@@ -238,13 +240,21 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
         lastk = a.last[pix];
         gA = a.dA ? a.dA[pix] : 0.0f;
     }
-    // this pixel's row of G = dL/dF (hi + lo), the operand of both products
+    // this pixel's row of G = dL/dF (hi + lo), the operand of both products,
+    // written eight channels per 16-byte store
 #pragma unroll
-    for (int c = 0; c < GP; ++c) {
-        const float v = (inside && c < a.C) ? a.dF[c * HW + pix] : 0.0f;
-        const __nv_bfloat16 h = __float2bfloat16_rn(v);
-        BG.gh[warp][lane][c] = h;
-        BG.gl[warp][lane][c] = __float2bfloat16_rn(v - __bfloat162float(h));
+    for (int c8 = 0; c8 < GP / 8; ++c8) {
+        uint32_t hw[4], lw[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int c = 8 * c8 + 2 * e;
+            const float v0 = (inside && c < a.C) ? a.dF[c * HW + pix] : 0.0f;
+            const float v1 = (inside && c + 1 < a.C) ? a.dF[(c + 1) * HW + pix] : 0.0f;
+            hw[e] = pack_bf16x2(v0, v1);
+            lw[e] = pack_bf16x2(v0 - bf16_lo_f(hw[e]), v1 - bf16_hi_f(hw[e]));
+        }
+        *reinterpret_cast<uint4 *>(&BG.gh[warp][lane][8 * c8]) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        *reinterpret_cast<uint4 *>(&BG.gl[warp][lane][8 * c8]) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
     }
     const unsigned long long fp2 = f2pack(fpx, fpy);
     int gs = 0;  // contributing Gaussians collected in this warp's current feature group
@@ -254,7 +264,7 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
     // Each warp walks its own list range [0, wmax) back to front in chunks of
     // 32, staged into its own slice of shared memory: no block-wide barrier,
     // so a warp whose pixels stopped early does not wait for the others.
-    Header *w_hdr = s_hdr + warp * 32;
+    float4 *w_h0 = s_h0 + warp * 32, *w_h1 = s_h1 + warp * 32;
     __nv_bfloat16 *w_row = s_row + (size_t)warp * 32 * RW;
     uint32_t *w_id = s_id + warp * 32;
     uint32_t nid = 0;  // ids of the next chunk, loaded one chunk ahead
@@ -272,7 +282,9 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
         __syncwarp();
         if (c0 + lane < c1) {
             w_id[lane] = gid;
-            w_hdr[lane] = a.hdr[gid];
+            const Header hg = a.hdr[gid];
+            w_h0[lane] = hg.h0;
+            w_h1[lane] = hg.h1;
             __nv_bfloat16 *dst = w_row + (size_t)lane * RW;
             if (F32) {
                 const uint4 *src = reinterpret_cast<const uint4 *>(reinterpret_cast<const __nv_bfloat16 *>(a.fsplit) +
@@ -292,9 +304,8 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
         __syncwarp();
         bool rel = false;
         if (c0 + lane < c1) {
-            const Header h = w_hdr[lane];
-            rel = (h.h0.x + h.h1.z >= fbx0) && (h.h0.x - h.h1.z <= fbx1) && (h.h0.y + h.h1.w >= fby0) &&
-                  (h.h0.y - h.h1.w <= fby1);
+            const float4 h0 = w_h0[lane], h1 = w_h1[lane];
+            rel = (h0.x + h1.z >= fbx0) && (h0.x - h1.z <= fbx1) && (h0.y + h1.w >= fby0) && (h0.y - h1.w <= fby1);
         }
         uint32_t m = __ballot_sync(FULL, rel);
         while (m) {
@@ -351,8 +362,8 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
                 const int j = 31 - __clz(mb);  // highest first: back to front
                 mb &= ~(1u << j);
                 const uint32_t k = (uint32_t)(c0 + j);
-                const float4 h0 = w_hdr[j].h0;
-                const float4 h1 = w_hdr[j].h1;
+                const float4 h0 = w_h0[j];
+                const float4 h1 = w_h1[j];
                 float dx, dy;
                 f2unpack(f2sub(fp2, f2pack(h0.x, h0.y)), dx, dy);
                 const float q = gauss_q(dx, dy, h0.z, h0.w, h1.x);
