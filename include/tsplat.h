@@ -419,6 +419,10 @@ tsplat_status tsplat_zbuffer(const tsplat_gaussians *g, const tsplat_camera *cam
  *   d_mean2d N*2, d_conic N*3, d_opac N, d_feat N*C: device f32 outputs,
  *   overwritten, indexed by Gaussian id.  Any output may be NULL.
  * Accumulation order across pixels is not deterministic (FP32 atomics).
+ * Single precision: the sums over a warp's pixels <f_j, g> and dL/df_j are
+ * tensor-core products on bf16 hi + lo parts (relative error about 2^-16);
+ * the division uses the hardware reciprocal.  FP32 features are read from
+ * the split rows the render used.
  * ---------------------------------------------------------------------- */
 tsplat_status tsplat_backward(tsplat_ctx *ctx, const float *dL_dfeat, const float *dL_dalpha,
                               float *d_mean2d, float *d_conic, float *d_opac, float *d_feat,
