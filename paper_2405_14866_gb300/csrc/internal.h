@@ -184,6 +184,7 @@ struct BinArgs {
     uint4 *tile_info_out;        // [n_slots] per position of that order: (tile, first, end, 0)
     uint32_t *tile_ctr;          // persistent-sort tile counter
     uint32_t *status;            // TSPLAT_ERR_CAPACITY when P > p_cap
+    int sort_wide;               // bucket sort with twelve-warp blocks (buckets near the shared-memory size)
 };
 // Ranges, fill cursors and P from the per-tile counts the projection made.
 void launch_bin_scan(const BinArgs &a, cudaStream_t s);

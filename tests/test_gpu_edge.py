@@ -181,6 +181,49 @@ def test_buckets_beyond_shared_memory(mix):
     assert counts.max() > 6144
 
 
+@pytest.mark.parametrize("mix,n", [("spread", 60000), ("one_slab_heavy", 60000), ("clusters", 60000),
+                                   ("spread", 12000), ("clusters", 12000)])
+def test_wide_bucket_sort(mix, n):
+    """More than 3000 instances of store capacity per tile slot (a store of
+    capacity 60 K on the 16 tiles of a 64x64 view) select the bucket sort
+    with twelve-warp blocks: with 60 K Gaussians every bucket exceeds shared
+    memory (depth slabs, a slab of one depth, clusters of depths within 100
+    ulps); with 12 K they are sorted in shared memory (runs below the sorted
+    bits, in place and past the fallback).  Pairs and ranges bit-exact."""
+    rng = np.random.default_rng(95)
+    if mix == "spread":
+        z = rng.uniform(1.0, 2.0, n).astype(np.float32)
+    elif mix == "one_slab_heavy":
+        z = np.where(np.arange(n) % 3 == 0, rng.uniform(1.0, 2.0, n), 1.5).astype(np.float32)
+    else:
+        base = rng.uniform(1.0, 1.5, n // 40).astype(np.float32).view(np.uint32)
+        z = (np.repeat(base, 40) + rng.integers(0, 100, n).astype(np.uint32)).view(np.float32)
+        z = z[rng.permutation(n)]
+    xy = rng.uniform(-0.25, 0.25, size=(n, 2)) * z[:, None]
+    mean = np.concatenate([xy, z[:, None]], 1).astype(np.float32)
+    cov = np.zeros((n, 6), np.float32)
+    cov[:, 0] = cov[:, 3] = cov[:, 5] = (0.002 * z) ** 2
+    opac = rng.uniform(0.02, 0.2, n).astype(np.float32)
+    feat = rng.standard_normal((n, 2)).astype(np.float32)
+    g32 = O.Gaussians(mean, cov, opac, feat)
+    cam = gen.make_camera(128.0, 64, 64, (0, 0, 0), np.eye(3))
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x, np.float32)).cuda()
+    g = api.Gaussians.create(60000, 2)
+    g.set(t(mean), t(cov), t(opac), t(feat))
+    ctx = api.Context()
+    F, A = ctx.render(g, cam)
+    torch.cuda.synchronize()
+    pr = O.project_f32(g32, cam, PAR)
+    bins = O.bin_gaussians(pr, cam.width, cam.height)
+    assert ctx.stats()["n_pairs"] == bins.P
+    assert np.array_equal(ctx.export("pairs").cpu().numpy().view(np.uint32), bins.ids)
+    assert np.array_equal(ctx.export("ranges").cpu().numpy().view(np.uint32), bins.ranges)
+    P.compare_render(F, A, O.render(g32, cam, PAR), g32, cam, PAR, P.TOL_F32)
+    counts = bins.ranges[:, 1].astype(np.int64) - bins.ranges[:, 0]
+    assert (counts > 0).sum() == 16
+    assert (counts.min() > 3840) if n == 60000 else (counts.max() <= 3840)
+
+
 @pytest.mark.parametrize("res", [(64, 48), (1000, 776), (2048, 2048)])
 def test_tile_order_is_longest_first_permutation(res):
     """One chunk of the scan (12 tiles, all with pairs, one of 18 K pairs),
