@@ -509,10 +509,10 @@ static tsplat_status render_tail(tsplat_ctx *c, int64_t n_cap, const uint32_t *n
     launch_bin_fill(bn, s);
     TRY(mark(c, prof, 3, s));
     // instances per tile slot, from the store's capacity: about 4 K for a
-    // 512x512 view of a 4 Mi-pixel frame, whose buckets then hold about
-    // 3.7 K pairs each and sort faster with more warps per tile; 1 K at
-    // 1024x1024, where more tiles in flight per SM pay more
-    bn.sort_wide = (double)inst_cap > 3000.0 * (double)std::max(n_tiles, 1);
+    // 512x512 and 1.8 K for a 768x768 view of a 4 Mi-pixel frame, whose
+    // buckets sort faster with more warps per tile; 1 K at 1024x1024, where
+    // more tiles in flight per SM pay more
+    bn.sort_wide = (double)inst_cap > 1500.0 * (double)std::max(n_tiles, 1);
     launch_bin_sort(bn, s);
     TRY(check_launch("render: bins"));
     TRY(mark(c, prof, 4, s));

@@ -184,7 +184,7 @@ def test_buckets_beyond_shared_memory(mix):
 @pytest.mark.parametrize("mix,n", [("spread", 60000), ("one_slab_heavy", 60000), ("clusters", 60000),
                                    ("spread", 12000), ("clusters", 12000)])
 def test_wide_bucket_sort(mix, n):
-    """More than 3000 instances of store capacity per tile slot (a store of
+    """More than 1500 instances of store capacity per tile slot (a store of
     capacity 60 K on the 16 tiles of a 64x64 view) select the bucket sort
     with twelve-warp blocks: with 60 K Gaussians every bucket exceeds shared
     memory (depth slabs, a slab of one depth, clusters of depths within 100
