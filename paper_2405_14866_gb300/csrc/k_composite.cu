@@ -5,7 +5,8 @@
 // Persistent CTAs take tiles from a counter.  Per tile: 8 consumer warps,
 // each owning an 8x4 pixel block, and 1 producer warp.  The producer
 // streams the tile's depth-ordered
-// Gaussians through a ring of shared-memory slots (64 Gaussians each),
+// Gaussians through a ring of shared-memory slots (128 Gaussians each with
+// BF16 features, 64 with FP32),
 // gathering each Gaussian's 32-byte projected record and feature row with
 // 16-byte asynchronous copies (cp.async) whose completion arrives on the
 // slot's mbarrier; consumer warps advance at their own pace and release
@@ -14,7 +15,7 @@
 // row, and tensor-map gathers of four rows per instruction alike.)  The ids
 // of the next two slots are loaded ahead.
 //
-// Per slot a warp tests the 64 records against its block with each
+// Per slot a warp tests the slot's records against its block with each
 // Gaussian's alpha_min box (exact: outside it alpha < alpha_min, so skipping
 // is what the per-pixel test would do) and walks the survivors in order.
 // Each lane runs the per-pixel recurrence (alpha, T, stop) and produces the
@@ -40,14 +41,23 @@ constexpr float LOG2E = 1.4426950408889634f;
 
 constexpr int NCW = 8;               // consumer warps
 constexpr int NTHR = (NCW + 1) * 32; // + 1 producer warp
-constexpr int SB = 64;               // Gaussians per ring slot
+// Gaussians per ring slot: 128 with BF16 rows (fewer slots per tile, so
+// less per-slot work and less padding of the survivor groups; 0.334 ->
+// 0.309 ms on the 1024x1024 headline against 64), 64 with FP32 features,
+// whose split rows take twice the space (a ring of two 128-slots measured
+// slower than six 64-slots)
+template <bool F32F>
+struct Slot {
+    static constexpr int SB = F32F ? 64 : 128;
+    static constexpr int NQ = SB / 32;  // entries per lane in the producer's and the box test's loops
+};
 constexpr int WROW = 24;             // bf16 per W row (16 used; 48-byte stride avoids bank conflicts)
 
 // Ring slots: as deep as two CTAs per SM allow (the ring is the slack that
 // lets a warp with little work in a slot run ahead of the slowest one).
 template <int CP, bool F32F>
 struct Ring {
-    static constexpr int N = CP <= 16 ? 8 : (CP <= 32 ? (F32F ? 6 : 8) : (F32F ? 3 : 4));
+    static constexpr int N = F32F ? (CP <= 16 ? 8 : (CP <= 32 ? 6 : 3)) : (CP <= 32 ? 4 : 2);
 };
 
 constexpr uint32_t FINAL_TILE = 0xffffffffu;  // slot tile id of the last slot a CTA produces
@@ -62,6 +72,7 @@ struct RecPair {
 template <int CP, bool F32F>
 struct CompSmem {
     static constexpr int RING = Ring<CP, F32F>::N;
+    static constexpr int SB = Slot<F32F>::SB;
     Header hdr[RING][SB + 1];  // entry SB of each slot: an empty record (alpha = 0 everywhere)
     __nv_bfloat16 fhi[RING][SB][CP + 8];  // rows padded by 16 B: spreads ldmatrix row reads over the banks
     __nv_bfloat16 flo[F32F ? RING : 1][F32F ? SB : 1][CP + 8];
@@ -134,6 +145,7 @@ __device__ __forceinline__ void produce_one(CompSmem<CP, F32F> &S, const Composi
 template <int CP, bool F32F>
 __device__ void producer(CompSmem<CP, F32F> &S, const CompositeArgs &a, int lane) {
     constexpr int RING = CompSmem<CP, F32F>::RING;
+    constexpr int SB = Slot<F32F>::SB, NQ = Slot<F32F>::NQ;
     // the tile count comes from the view table in device memory, so a replayed
     // graph may render a different mix of view sizes
     const RenderView &lastv = S.views[a.n_views - 1];
@@ -150,11 +162,13 @@ __device__ void producer(CompSmem<CP, F32F> &S, const CompositeArgs &a, int lane
         const uint4 info = last_tile ? make_uint4(0u, 0u, 0u, 0u) : a.tile_info[tk];
         const uint32_t t = info.x, first = info.y;
         const int n = (int)(info.z - info.y);
-        // ids of the next two slots' Gaussians (two per lane each), loaded ahead
-        uint32_t nid0 = lane < n ? a.ids[first + lane] : 0u;
-        uint32_t nid1 = lane + 32 < n ? a.ids[first + lane + 32] : 0u;
-        uint32_t mid0 = SB + lane < n ? a.ids[first + SB + lane] : 0u;
-        uint32_t mid1 = SB + lane + 32 < n ? a.ids[first + SB + lane + 32] : 0u;
+        // ids of the next two slots' Gaussians (NQ per lane each), loaded ahead
+        uint32_t nid[NQ], mid[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            nid[q] = lane + 32 * q < n ? a.ids[first + lane + 32 * q] : 0u;
+            mid[q] = SB + lane + 32 * q < n ? a.ids[first + SB + lane + 32 * q] : 0u;
+        }
         for (int b = 0;; b += SB, ++i) {
             const int slot = (int)(i % RING);
             if (!mbar_wait(&S.empty[slot], ((i / RING) & 1) ^ 1, a.status)) {
@@ -167,14 +181,17 @@ __device__ void producer(CompSmem<CP, F32F> &S, const CompositeArgs &a, int lane
             const bool end = last_tile || b >= n || all_done;
             const int cnt = end ? 0 : min(SB, n - b);
             if (!end) {
-                const uint32_t id0 = nid0, id1 = nid1;
-                nid0 = mid0;
-                nid1 = mid1;
+                uint32_t id[NQ];
                 const int nb = b + 2 * SB;
-                mid0 = nb + lane < n ? a.ids[first + nb + lane] : 0u;
-                mid1 = nb + lane + 32 < n ? a.ids[first + nb + lane + 32] : 0u;
-                if (lane < cnt) produce_one<CP, F32F>(S, a, slot, lane, id0, ns);
-                if (lane + 32 < cnt) produce_one<CP, F32F>(S, a, slot, lane + 32, id1, ns);
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    id[q] = nid[q];
+                    nid[q] = mid[q];
+                    mid[q] = nb + lane + 32 * q < n ? a.ids[first + nb + lane + 32 * q] : 0u;
+                }
+#pragma unroll
+                for (int q = 0; q < NQ; ++q)
+                    if (lane + 32 * q < cnt) produce_one<CP, F32F>(S, a, slot, lane + 32 * q, id[q], ns);
             }
             // every lane, every slot: counts against the barrier's expected
             // arrivals (.noinc) and fires once this lane's copies have landed
@@ -220,6 +237,7 @@ __global__ __launch_bounds__(NTHR, 2) void k_composite(CompositeArgs a) {
     CompSmem<CP, F32F> &S = *reinterpret_cast<CompSmem<CP, F32F> *>(smem_raw);
     constexpr int NT8 = CP / 8;  // n8 tiles of the MMA
     constexpr int RING = CompSmem<CP, F32F>::RING;
+    constexpr int SB = Slot<F32F>::SB, NQ = Slot<F32F>::NQ;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
@@ -335,12 +353,14 @@ __global__ __launch_bounds__(NTHR, 2) void k_composite(CompositeArgs a) {
             const uint32_t cols = (live | (live >> 8) | (live >> 16) | (live >> 24)) & 0xffu;
             const float fbx0 = (float)(bx0 + __ffs(cols) - 1), fbx1 = (float)(bx0 + 31 - __clz(cols));
             const float fby0 = (float)(by0 + __ffs(rows) - 1), fby1 = (float)(by0 + 31 - __clz(rows));
-            const bool r0 = lane < cnt && box_hit(S.hdr[slot], lane, fbx0, fbx1, fby0, fby1);
-            const bool r1 = lane + 32 < cnt && box_hit(S.hdr[slot], lane + 32, fbx0, fbx1, fby0, fby1);
-            const uint32_t m0 = __ballot_sync(FULL, r0), m1 = __ballot_sync(FULL, r1);
-            const int c0 = __popc(m0), nrel = c0 + __popc(m1);
-            if (r0) S.list[warp][__popc(m0 & lt)] = (uint8_t)lane;
-            if (r1) S.list[warp][c0 + __popc(m1 & lt)] = (uint8_t)(lane + 32);
+            int nrel = 0;
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const bool rq = lane + 32 * q < cnt && box_hit(S.hdr[slot], lane + 32 * q, fbx0, fbx1, fby0, fby1);
+                const uint32_t mq = __ballot_sync(FULL, rq);
+                if (rq) S.list[warp][nrel + __popc(mq & lt)] = (uint8_t)(lane + 32 * q);
+                nrel += __popc(mq);
+            }
             // pad the list to a multiple of 16 with the empty record
             if (lane < 16 && nrel + lane < ((nrel + 15) & ~15)) S.list[warp][nrel + lane] = (uint8_t)SB;
             __syncwarp();
