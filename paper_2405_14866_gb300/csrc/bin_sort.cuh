@@ -113,6 +113,46 @@ __device__ __forceinline__ void smem_pass_any(BinSortSmem &S, int src, int m, bo
     else smem_pass<BS_ROUNDS>(S, src, m, by_id, vmin, shift);
 }
 
+// The lowest pass over the chunk, unstable: each entry's place within its
+// digit comes from a returning shared-memory atomic (thread-strided entries),
+// in place of the stable pass's ballot ranking and per-warp digit counts.
+template <int R>
+__device__ __forceinline__ void smem_pass_unstable(BinSortSmem &S, int src, int m, int shift) {
+    const int tid = threadIdx.x;
+    if (OWNS(tid)) S.dbase[tid] = 0u;
+    __syncthreads();
+    uint32_t pos[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int j = tid + r * BS_THREADS;
+        pos[r] = 0u;
+        if (j < m) pos[r] = atomicAdd(&S.dbase[(S.kv[src][j].x >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    uint32_t tot;
+    const uint32_t base = block_excl_scan<BS_WARPS>(OWNS(tid) ? S.dbase[tid] : 0u, S.sw, tot);
+    if (OWNS(tid)) S.dbase[tid] = base;
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int j = tid + r * BS_THREADS;
+        if (j < m) {
+            const uint2 e = S.kv[src][j];
+            S.kv[src ^ 1][S.dbase[(e.x >> shift) & 255u] + pos[r]] = e;
+        }
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void smem_pass_unstable_any(BinSortSmem &S, int src, int m, int shift) {
+    const int rounds = (m + BS_THREADS - 1) / BS_THREADS;
+    if (rounds <= 1) smem_pass_unstable<1>(S, src, m, shift);
+    else if (rounds <= 2) smem_pass_unstable<2>(S, src, m, shift);
+    else if (rounds <= 4) smem_pass_unstable<4>(S, src, m, shift);
+    else if (rounds <= 8) smem_pass_unstable<8>(S, src, m, shift);
+    else smem_pass_unstable<BS_ROUNDS>(S, src, m, shift);
+}
+
 constexpr int LD_BATCH = 8;  // global loads per thread issued together in the streaming loops
 
 // (k - kmin, v) of entries [0, m), m <= BS_MAX, into dst: all loads of a
@@ -207,6 +247,69 @@ __device__ void global_pass(BinSortSmem &S, const uint32_t *ka, const uint32_t *
         if (OWNS(tid)) S.run[tid] += count;
         __syncthreads();
     }
+}
+
+// The slab split of a bucket beyond shared memory: (ka, va)[0, n) scattered
+// to (kb, vb) by the digit `shift` of key - kmin, in no particular order
+// within a digit (each slab is sorted afterwards, so the split need not be
+// stable): the lanes of a warp with one digit reserve their places with one
+// atomic.  S.run[d] ends as the end of slab d.
+__device__ void global_split(BinSortSmem &S, const uint32_t *ka, const uint32_t *va, uint32_t *kb, uint32_t *vb,
+                             uint32_t n, uint32_t kmin, int shift) {
+    const int tid = threadIdx.x, lane = tid & 31;
+    const uint32_t lt = lanemask_lt();
+    if (OWNS(tid)) S.dbase[tid] = 0u;
+    __syncthreads();
+    for (uint32_t j0 = 0; j0 < n; j0 += LD_BATCH * BS_THREADS) {
+        uint32_t d[LD_BATCH];
+#pragma unroll
+        for (int r = 0; r < LD_BATCH; ++r) {
+            const uint32_t j = j0 + tid + r * BS_THREADS;
+            d[r] = j < n ? ((ka[j] - kmin) >> shift) & 255u : 256u;
+        }
+#pragma unroll
+        for (int r = 0; r < LD_BATCH; ++r)
+            if (d[r] < 256u) atomicAdd(&S.dbase[d[r]], 1u);
+    }
+    __syncthreads();
+    {
+        uint32_t tot;
+        const uint32_t e = block_excl_scan<BS_WARPS>(OWNS(tid) ? S.dbase[tid] : 0u, S.sw, tot);
+        if (OWNS(tid)) S.run[tid] = e;
+    }
+    __syncthreads();
+    for (uint32_t j0 = 0; j0 < n; j0 += LD_BATCH * BS_THREADS) {
+        uint32_t kr[LD_BATCH], vr[LD_BATCH];
+#pragma unroll
+        for (int r = 0; r < LD_BATCH; ++r) {
+            const uint32_t j = j0 + tid + r * BS_THREADS;
+            kr[r] = j < n ? ka[j] : 0u;
+            vr[r] = j < n ? va[j] : 0u;
+        }
+#pragma unroll
+        for (int r = 0; r < LD_BATCH; ++r) {
+            const bool valid = j0 + tid + r * BS_THREADS < n;
+            uint32_t peers = __ballot_sync(FULL, valid);
+            if (peers) {  // warp-uniform
+                const uint32_t d = ((kr[r] - kmin) >> shift) & 255u;
+#pragma unroll
+                for (int b = 0; b < 8; ++b) {
+                    const uint32_t bal = __ballot_sync(FULL, (d >> b) & 1u);
+                    peers &= ((d >> b) & 1u) ? bal : ~bal;
+                }
+                const int leader = peers ? __ffs(peers) - 1 : lane;
+                uint32_t base = 0;
+                if (valid && lane == leader) base = atomicAdd(&S.run[d], (uint32_t)__popc(peers));
+                base = __shfl_sync(FULL, base, leader);
+                if (valid) {
+                    const uint32_t pos = base + (uint32_t)__popc(peers & lt);
+                    kb[pos] = kr[r];
+                    vb[pos] = vr[r];
+                }
+            }
+        }
+    }
+    __syncthreads();
 }
 
 __device__ __forceinline__ int sig_bits(uint32_t lo, uint32_t hi) { return hi > lo ? 32 - __clz(hi - lo) : 0; }
@@ -315,7 +418,10 @@ __device__ bool fix_runs(BinSortSmem &S, uint2 *kv, uint32_t n, int lo) {
 // in shared memory and writes the ids to out (which may alias v).  The radix
 // passes cover the highest 8 * npass significant key bits (npass = 2 up to
 // 24 significant bits, else 3); runs of entries that agree on those bits are
-// then put in (key, id) order by insertion, which completes the order.
+// then put in (key, id) order by insertion, which completes the order.  The
+// lowest pass need not be stable: the order it leaves among entries of one
+// digit survives the stable passes above it only within such runs, which
+// the insertion re-sorts.
 __device__ void sort_range_smem(BinSortSmem &S, const uint32_t *k, const uint32_t *v, uint32_t n, uint32_t *out) {
     const int tid = threadIdx.x;
     if (n <= 1) {
@@ -351,7 +457,8 @@ __device__ void sort_range_smem(BinSortSmem &S, const uint32_t *k, const uint32_
     const int npass = kb <= 16 ? (kb + 7) / 8 : (kb <= 24 ? 2 : 3);
     const int lo = max(0, kb - 8 * npass);  // key bits below the passes
     for (int sh = lo; sh < kb; sh += 8) {
-        smem_pass_any(S, src, m, false, vmin, sh);
+        if (sh == lo) smem_pass_unstable_any(S, src, m, sh);
+        else smem_pass_any(S, src, m, false, vmin, sh);
         src ^= 1;
     }
     // runs that agree on the passes' bits: (key, id) order (short runs in place)
@@ -435,8 +542,8 @@ __global__ __launch_bounds__(BS_THREADS, BS_OCC) void k_bin_sort(BinArgs a) {
             sort_range_smem(S, bk, bi, n, out);
             continue;
         }
-        // A bucket beyond shared memory: one pass over global memory on the
-        // highest significant digit splits it into depth slabs; runs of
+        // A bucket beyond shared memory: one unstable pass over global memory
+        // on the highest significant digit splits it into depth slabs; runs of
         // consecutive slabs of at most BS_MAX entries are then sorted in
         // shared memory, and a slab larger than that by global passes.
         uint32_t kmn, kmx, vmn, vmx;
@@ -448,7 +555,7 @@ __global__ __launch_bounds__(BS_THREADS, BS_OCC) void k_bin_sort(BinArgs a) {
             sort_range_global(S, bk, bi, tk, ti, n, out);
             continue;
         }
-        global_pass(S, bk, bi, tk, ti, n, false, kmin, 0u, ((kb - 1) / 8) * 8);
+        global_split(S, bk, bi, tk, ti, n, kmin, ((kb - 1) / 8) * 8);
         if (OWNS(tid)) S.slab[tid] = S.run[tid];  // end of each slab (the passes below reuse S.run)
         __syncthreads();
         uint32_t c0 = 0;  // start of the pending run of slabs (the same in every thread)

@@ -280,26 +280,32 @@ __global__ __launch_bounds__(CT, 2) void k_backward(BackwardArgs a) {
             nid = n0 + lane < c0 ? a.ids[rg.x + n0 + lane] : 0u;
         }
         __syncwarp();
-        if (c0 + lane < c1) {
-            w_id[lane] = gid;
-            const Header hg = a.hdr[gid];
-            w_h0[lane] = hg.h0;
-            w_h1[lane] = hg.h1;
-            __nv_bfloat16 *dst = w_row + (size_t)lane * RW;
-            if (F32) {
-                const uint4 *src = reinterpret_cast<const uint4 *>(reinterpret_cast<const __nv_bfloat16 *>(a.fsplit) +
-                                                                   (size_t)gid * 2 * GP);
+        if (c0 + lane < c1) w_id[lane] = gid;
+        // records: two lanes per record (its 16-byte halves), so that the two
+        // halves of a 32-byte sector are requested by one load
 #pragma unroll
-                for (int i = 0; i < 2 * GP / 8; ++i) reinterpret_cast<uint4 *>(dst)[i ^ row_swz<NCH>(lane)] = __ldg(src + i);
-            } else if (bvec) {
-                const uint4 *src = reinterpret_cast<const uint4 *>(reinterpret_cast<const __nv_bfloat16 *>(a.feat) +
-                                                                   (size_t)gid * GP);
+        for (int r = 0; r < 2; ++r) {
+            const int j = 16 * r + (lane >> 1), h = lane & 1;
+            const uint32_t gj = __shfl_sync(FULL, gid, j);
+            if (c0 + j < c1) (h ? w_h1 : w_h0)[j] = __ldg(reinterpret_cast<const float4 *>(a.hdr + gj) + h);
+        }
+        // rows: NCH lanes per row, 32 / NCH rows per load (a warp's load then
+        // touches 32 / NCH rows, not 32)
+        if (F32 || bvec) {
+            constexpr int GPI = 32 / NCH;
+            const __nv_bfloat16 *rows = reinterpret_cast<const __nv_bfloat16 *>(F32 ? a.fsplit : a.feat);
 #pragma unroll
-                for (int i = 0; i < GP / 8; ++i) reinterpret_cast<uint4 *>(dst)[i ^ row_swz<NCH>(lane)] = __ldg(src + i);
-            } else {
-                const __nv_bfloat16 *src = reinterpret_cast<const __nv_bfloat16 *>(a.feat) + (size_t)gid * a.C;
-                for (int c = 0; c < a.C; ++c) dst[8 * ((c >> 3) ^ row_swz<NCH>(lane)) + (c & 7)] = src[c];
+            for (int r = 0; r < NCH; ++r) {
+                const int j = GPI * r + lane / NCH, i = lane % NCH;
+                const uint32_t gj = __shfl_sync(FULL, gid, j);
+                if (c0 + j < c1)
+                    reinterpret_cast<uint4 *>(w_row + (size_t)j * RW)[i ^ row_swz<NCH>(j)] =
+                        __ldg(reinterpret_cast<const uint4 *>(rows + (size_t)gj * RW) + i);
             }
+        } else if (c0 + lane < c1) {  // BF16 rows of fewer than GP channels: one lane per row
+            __nv_bfloat16 *dst = w_row + (size_t)lane * RW;
+            const __nv_bfloat16 *src = reinterpret_cast<const __nv_bfloat16 *>(a.feat) + (size_t)gid * a.C;
+            for (int c = 0; c < a.C; ++c) dst[8 * ((c >> 3) ^ row_swz<NCH>(lane)) + (c & 7)] = src[c];
         }
         __syncwarp();
         bool rel = false;

@@ -14,13 +14,15 @@
 //                         of its tile's bucket with one atomic and writes
 //                         (depth key, instance id) into it;
 //   4. k_bin_sort         persistent blocks take tiles in that order and sort
-//                         each bucket by (depth key, id): an LSD radix sort
-//                         with 8-bit digits over the bits in which the tile's
-//                         depth keys differ, then runs of equal depth keys
-//                         put in id order (runs longer than 32: id digits,
-//                         then depth digits again); in shared memory, or for
-//                         buckets larger than it, by the same passes over
-//                         global memory.
+//                         each bucket by (depth key, id): in shared memory,
+//                         an LSD radix sort with 8-bit digits over the
+//                         highest 16 (or 24) bits in which the tile's depth
+//                         keys differ (its lowest pass unstable), then runs
+//                         that agree on those bits put in (key, id) order
+//                         (runs longer than 32: id digits, then depth digits
+//                         again); buckets larger than shared memory are
+//                         first split into depth slabs by a pass over global
+//                         memory.
 // A bucket's order after step 3 depends on the atomics; after step 5 it does
 // not: (depth key, id) is unique within a tile.
 #include <algorithm>

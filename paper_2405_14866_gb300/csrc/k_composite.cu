@@ -8,9 +8,10 @@
 // Gaussians through a ring of shared-memory slots (128 Gaussians each with
 // BF16 features, 64 with FP32),
 // gathering each Gaussian's 32-byte projected record and feature row with
-// 16-byte asynchronous copies (cp.async) whose completion arrives on the
-// slot's mbarrier; consumer warps advance at their own pace and release
-// slots, so no CTA-wide barrier couples them.  (Gathers through the TMA
+// 16-byte asynchronous copies (cp.async; adjacent lanes copy adjacent chunks
+// of one record or row) whose completion arrives on the slot's mbarrier;
+// consumer warps advance at their own pace and release slots, so no CTA-wide
+// barrier couples them.  (Gathers through the TMA
 // engine measured slower for these 32- and 64-byte rows: one bulk copy per
 // row, and tensor-map gathers of four rows per instruction alike.)  The ids
 // of the next two slots are loaded ahead.
@@ -106,32 +107,56 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
 
-// Producer side of one Gaussian of a slot: its record (2 x 16 B) and its
-// feature row by 16-byte asynchronous copies -- BF16 rows of exactly CP
-// channels as stored, FP32 rows as their pre-split bf16 (hi, lo) rows of CP
-// columns each (zero-padded); BF16 rows of fewer channels are loaded and
-// zero-padded by the producer lane itself.
+// Producer side of one Gaussian of a slot with BF16 rows of fewer than CP
+// channels: its record by two 16-byte asynchronous copies, its feature row
+// loaded and zero-padded by the producer lane itself.
 template <int CP, bool F32F>
-__device__ __forceinline__ void produce_one(CompSmem<CP, F32F> &S, const CompositeArgs &a, int slot, int k,
-                                            uint32_t id, uint32_t ns) {
+__device__ __forceinline__ void produce_one_padded(CompSmem<CP, F32F> &S, const CompositeArgs &a, int slot, int k,
+                                                   uint32_t id, uint32_t ns) {
     const uint4 *hs = reinterpret_cast<const uint4 *>(a.hdr + id);
     cp_async16(hdr_h0(S.hdr[slot], k), hs);
     cp_async16(hdr_h1(S.hdr[slot], k), hs + 1);
     const size_t gi = id % ns;  // features are stored once per Gaussian, records per (view, Gaussian)
-    if (F32F) {
-        const uint4 *fs = reinterpret_cast<const uint4 *>(reinterpret_cast<const __nv_bfloat16 *>(a.fsplit) + gi * 2 * CP);
+    const __nv_bfloat16 *src = reinterpret_cast<const __nv_bfloat16 *>(a.feat) + gi * a.C;
+    for (int c = 0; c < CP; ++c) S.fhi[slot][k][c] = c < a.C ? src[c] : __float2bfloat16_rn(0.0f);
+}
+
+// Producer side of 32 Gaussians of a slot (entries k0 .. k0 + 31, id of
+// entry k0 + j held by lane j): records and feature rows -- BF16 rows of
+// exactly CP channels as stored, FP32 rows as their pre-split bf16 (hi, lo)
+// rows of CP columns each (zero-padded) -- by 16-byte asynchronous copies,
+// made chunk-cooperatively: two lanes per record (its two halves) and RC
+// lanes per row, so that the lanes of one copy instruction that share a
+// 32-byte sector request it once (one lane per Gaussian measured 1 % slower
+// on BF16 rows and 4 % on FP32 rows).
+template <int CP, bool F32F>
+__device__ __forceinline__ void produce_group(CompSmem<CP, F32F> &S, const CompositeArgs &a, int slot, int k0,
+                                              int cnt, uint32_t id, uint32_t ns, int lane) {
+    const uint32_t gi = id % ns;  // features are stored once per Gaussian, records per (view, Gaussian)
 #pragma unroll
-        for (int c = 0; c < CP / 8; ++c) {
-            cp_async16(&S.fhi[slot][k][8 * c], fs + c);
-            cp_async16(&S.flo[F32F ? slot : 0][F32F ? k : 0][8 * c], fs + CP / 8 + c);
+    for (int r = 0; r < 2; ++r) {
+        const int j = 16 * r + (lane >> 1), h = lane & 1;
+        const uint32_t idj = __shfl_sync(FULL, id, j);
+        const int k = k0 + j;
+        if (k < cnt)
+            cp_async16(h ? hdr_h1(S.hdr[slot], k) : hdr_h0(S.hdr[slot], k),
+                       reinterpret_cast<const uint4 *>(a.hdr + idj) + h);
+    }
+    constexpr int NC = CP / 8;
+    constexpr int RC = (F32F ? 2 : 1) * NC;
+    constexpr int GPI = 32 / RC;
+    const __nv_bfloat16 *rows = reinterpret_cast<const __nv_bfloat16 *>(F32F ? a.fsplit : a.feat);
+#pragma unroll
+    for (int r = 0; r < RC; ++r) {
+        const int j = GPI * r + lane / RC, c = lane % RC;
+        const uint32_t gj = __shfl_sync(FULL, gi, j);
+        const int k = k0 + j;
+        if (k < cnt) {
+            const uint4 *fs = reinterpret_cast<const uint4 *>(rows + (size_t)gj * (RC * 8));
+            __nv_bfloat16 *dst = (!F32F || c < NC) ? &S.fhi[slot][k][8 * c]
+                                                   : &S.flo[F32F ? slot : 0][F32F ? k : 0][8 * (c - NC)];
+            cp_async16(dst, fs + c);
         }
-    } else if (a.C == CP) {
-        const uint4 *fs = reinterpret_cast<const uint4 *>(reinterpret_cast<const __nv_bfloat16 *>(a.feat) + gi * CP);
-#pragma unroll
-        for (int c = 0; c < CP / 8; ++c) cp_async16(&S.fhi[slot][k][8 * c], fs + c);
-    } else {
-        const __nv_bfloat16 *src = reinterpret_cast<const __nv_bfloat16 *>(a.feat) + gi * a.C;
-        for (int c = 0; c < CP; ++c) S.fhi[slot][k][c] = c < a.C ? src[c] : __float2bfloat16_rn(0.0f);
     }
 }
 
@@ -189,9 +214,14 @@ __device__ void producer(CompSmem<CP, F32F> &S, const CompositeArgs &a, int lane
                     nid[q] = mid[q];
                     mid[q] = nb + lane + 32 * q < n ? a.ids[first + nb + lane + 32 * q] : 0u;
                 }
+                if (F32F || a.C == CP) {  // rows of exactly CP columns: chunk-cooperative copies
 #pragma unroll
-                for (int q = 0; q < NQ; ++q)
-                    if (lane + 32 * q < cnt) produce_one<CP, F32F>(S, a, slot, lane + 32 * q, id[q], ns);
+                    for (int q = 0; q < NQ; ++q) produce_group<CP, F32F>(S, a, slot, 32 * q, cnt, id[q], ns, lane);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < NQ; ++q)
+                        if (lane + 32 * q < cnt) produce_one_padded<CP, F32F>(S, a, slot, lane + 32 * q, id[q], ns);
+                }
             }
             // every lane, every slot: counts against the barrier's expected
             // arrivals (.noinc) and fires once this lane's copies have landed
